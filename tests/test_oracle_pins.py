@@ -1,0 +1,311 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+* dense LU brute force (numpy.linalg.solve / matmul) on tiny lines, for the Thomas,
+  periodic (Sherman-Morrison) Thomas and transposed solves;
+* the closed-form modified wavenumbers of the periodic schemes on Fourier modes;
+* Taylor exactness of every scheme row on monomials (which fixes the interior
+  coefficients uniquely and the order of each closure), and exactness of the whole
+  closed line on low-degree polynomials;
+* sixth-order convergence on a smooth periodic function (Sec. 4.2, order-of-accuracy
+  study);
+* adjoint identities: <D f, g> = <f, D^T g>, and D1^T = -D1, D2^T = D2 on periodic lines;
+* the coefficients printed in Eq. cfds and a hand-enumerated layout example
+  (``tests/golden``).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def dense(o, n, order, bc, h):
+    """Dense A and B assembled from the oracle's bands (wrap-around on cyclic lines)."""
+    a, b, c, B7 = o.bands(n, order, bc, h)
+    A = np.zeros((n, n)); B = np.zeros((n, n))
+    per = bc == "periodic"
+    for i in range(n):
+        A[i, i] = b[i]
+        if i > 0: A[i, i - 1] = a[i]
+        elif per: A[i, n - 1] += a[i]
+        if i < n - 1: A[i, i + 1] = c[i]
+        elif per: A[i, 0] += c[i]
+        for t in range(7):
+            j = i + t - 3
+            if B7[i, t] == 0.0: continue
+            if per: j %= n
+            assert 0 <= j < n
+            B[i, j] += B7[i, t]
+    return A, B
+
+
+# ----------------------------------------------------------------- golden coefficients
+
+def test_first_derivative_coefficients_match_paper(oracle_mod):
+    vals = {}
+    with open(os.path.join(GOLDEN, "compact_first_derivative.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                name, num, den = line.split()
+                vals[name] = int(num) / int(den)
+    n, h = 32, 0.1
+    a, b, c, B7 = oracle_mod.bands(n, 1, "periodic", h)
+    for i in range(n):
+        assert a[i] == pytest.approx(vals["alpha"], rel=1e-15)
+        assert c[i] == pytest.approx(vals["alpha"], rel=1e-15)
+        assert b[i] == 1.0
+        np.testing.assert_allclose(
+            B7[i], [0, -vals["b"] / (4 * h), -vals["a"] / (2 * h), 0,
+                    vals["a"] / (2 * h), vals["b"] / (4 * h), 0], rtol=1e-15)
+
+
+# ------------------------------------------------------------------ dense brute force
+
+@pytest.mark.parametrize("n", [8, 12, 16, 32])
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+def test_deriv_matches_dense_lu(oracle_mod, n, order, bc):
+    rng = np.random.default_rng(100 + n + 7 * order)
+    h = oracle_mod.grid_spacing(n, bc)
+    A, B = dense(oracle_mod, n, order, bc, h)
+    f = rng.uniform(-1, 1, size=(5, n))
+    ref = np.linalg.solve(A, B @ f.T).T
+    got = oracle_mod.deriv_lines(f, order, bc, h)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # the right-hand side alone
+    np.testing.assert_allclose(oracle_mod.rhs_lines(f, order, bc, h), (B @ f.T).T,
+                               rtol=0, atol=1e-14 * np.max(np.abs(B @ f.T)))
+
+
+@pytest.mark.parametrize("n", [8, 12, 16, 32])
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+def test_adjoint_matches_dense_lu(oracle_mod, n, order, bc):
+    rng = np.random.default_rng(200 + n + 7 * order)
+    h = oracle_mod.grid_spacing(n, bc)
+    A, B = dense(oracle_mod, n, order, bc, h)
+    g = rng.normal(size=(5, n))
+    ref = (B.T @ np.linalg.solve(A.T, g.T)).T
+    got = oracle_mod.deriv_adjoint_lines(g, order, bc, h)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("n", [3, 4, 7, 50])
+def test_tridiagonal_solver_random_dominant(oracle_mod, periodic, n):
+    rng = np.random.default_rng(n + 10 * periodic)
+    a = rng.uniform(-1, 1, n); c = rng.uniform(-1, 1, n)
+    b = 2.5 + rng.uniform(0, 1, n)
+    d = rng.normal(size=n)
+    M = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+    if periodic:
+        M[0, n - 1] += a[0]; M[n - 1, 0] += c[n - 1]
+    ref = np.linalg.solve(M, d)
+    got = oracle_mod.tridiag_solve(a, b, c, d, periodic)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.max(np.abs(ref)))
+
+
+# ------------------------------------------------------- closed form: modified wavenumber
+
+def mod_wavenumber(order, k, h):
+    """Fourier symbol of the periodic interior scheme (derived from the stencil)."""
+    if order == 1:
+        al, a, b = 1 / 3, 14 / 9, 1 / 9
+        return (a * np.sin(k * h) + 0.5 * b * np.sin(2 * k * h)) / (h * (1 + 2 * al * np.cos(k * h)))
+    al, a, b = 2 / 11, 12 / 11, 3 / 11
+    return ((2 * a * (1 - np.cos(k * h)) + 0.5 * b * (1 - np.cos(2 * k * h)))
+            / (h * h * (1 + 2 * al * np.cos(k * h))))
+
+
+@pytest.mark.parametrize("n", [16, 64, 256])
+@pytest.mark.parametrize("order", [1, 2])
+def test_modified_wavenumber_closed_form(oracle_mod, n, order):
+    h = 2 * np.pi / n
+    x = np.arange(n) * h
+    rng = np.random.default_rng(n + order)
+    for k in [1, 2, 3, n // 4, n // 2 - 1]:
+        phi = rng.uniform(0, 2 * np.pi)
+        f = np.cos(k * x + phi)
+        got = oracle_mod.deriv_lines(f[None, :], order, "periodic", h)[0]
+        kk = mod_wavenumber(order, k, h)
+        ref = -kk * np.sin(k * x + phi) if order == 1 else -kk * np.cos(k * x + phi)
+        # rounding scales with the operator norm (the largest symbol over all modes),
+        # not with the (possibly small) symbol of this one mode
+        kmax = np.max(np.abs(mod_wavenumber(order, np.arange(n // 2 + 1), h)))
+        assert np.max(np.abs(got - ref)) <= 1e-13 * kmax
+
+
+def test_modified_wavenumber_multidirection_field(oracle_mod):
+    """A mode cos(kx x + ky y + kz z + phi) differentiated along each direction."""
+    nz, ny, nx = 16, 32, 64
+    kx, ky, kz, phi = 5, 3, 2, 0.7
+    X = np.arange(nx) * 2 * np.pi / nx
+    Y = np.arange(ny) * 2 * np.pi / ny
+    Z = np.arange(nz) * 2 * np.pi / nz
+    arg = kx * X[None, None, :] + ky * Y[None, :, None] + kz * Z[:, None, None] + phi
+    f = np.cos(arg)
+    for d, k, n in (("x", kx, nx), ("y", ky, ny), ("z", kz, nz)):
+        got = oracle_mod.deriv(f, d, 1, "periodic")
+        ref = -mod_wavenumber(1, k, 2 * np.pi / n) * np.sin(arg)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+        got2 = oracle_mod.deriv(f, d, 2, "periodic")
+        ref2 = -mod_wavenumber(2, k, 2 * np.pi / n) * np.cos(arg)
+        assert np.max(np.abs(got2 - ref2)) <= 1e-12 * np.max(np.abs(ref2))
+
+
+# ----------------------------------------------------------- Taylor / polynomial exactness
+
+def _row_residual(o, n, order, bc, h, i, p, x0):
+    """Residual of row i of A u' = B f for f = (x - x0)^p, in exact rational arithmetic
+    on the coefficients returned by the oracle."""
+    a, b, c, B7 = o.bands(n, order, bc, h)
+    def f(j): return Fraction(j * 1) ** p if p > 0 else Fraction(1)
+    # derivative of x^p at grid index j (x_j = j*h, x0 = 0): order 1 or 2
+    def df(j):
+        if order == 1:
+            return Fraction(p) * Fraction(j) ** (p - 1) if p >= 1 else Fraction(0)
+        return Fraction(p * (p - 1)) * Fraction(j) ** (p - 2) if p >= 2 else Fraction(0)
+    # work in units h = 1 with exact rationals: scale B by h^order
+    hs = Fraction(h) ** order
+    lhs = Fraction(b[i]) * df(i - x0)
+    if i > 0: lhs += Fraction(a[i]) * df(i - 1 - x0)
+    if i < n - 1: lhs += Fraction(c[i]) * df(i + 1 - x0)
+    rhs = Fraction(0)
+    for t in range(7):
+        j = i + t - 3
+        if B7[i, t] != 0.0:
+            rhs += Fraction(B7[i, t]) * hs * f(j - x0)
+    return float(lhs - rhs), float(abs(lhs) + 1)
+
+
+# (row, exact-through degree) for each scheme's rows; the interior row is exact through
+# degree 6 (first derivative) and 7 (second derivative): that alone fixes alpha, a, b.
+ROWS = {1: [(0, 3), (1, 4), ("mid", 6), (-2, 4), (-1, 3)],
+        2: [(0, 4), (1, 5), ("mid", 7), (-2, 5), (-1, 4)]}
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_rows_taylor_exact_to_stated_degree(oracle_mod, order):
+    n = 16
+    h = 1.0  # power of two: the coefficients are then exact rationals of the scheme
+    for row, deg in ROWS[order]:
+        i = n // 2 if row == "mid" else (row % n)
+        x0 = i  # expand around the row's own node
+        for p in range(0, deg + 1):
+            r, s = _row_residual(oracle_mod, n, order, "closed", h, i, p, x0)
+            assert abs(r) <= 1e-12 * s, (order, row, p, r)
+        # and not exact one degree higher (pins the stated order of each closure);
+        # odd/even symmetry makes the centred rows exact one more degree
+        p = deg + 1
+        r, s = _row_residual(oracle_mod, n, order, "closed", h, i, p, x0)
+        if row in (0, -1):
+            assert abs(r) > 1e-6, (order, row, p)
+        else:
+            r2, s2 = _row_residual(oracle_mod, n, order, "closed", h, i, p + 1, x0)
+            assert abs(r) > 1e-6 or abs(r2) > 1e-6, (order, row, p)
+
+
+@pytest.mark.parametrize("order,maxdeg", [(1, 3), (2, 4)])
+def test_closed_line_exact_on_polynomials(oracle_mod, order, maxdeg):
+    n = 40
+    h = 2.0 / (n - 1)
+    x = -1.0 + np.arange(n) * h
+    for p in range(0, maxdeg + 1):
+        f = x ** p
+        if order == 1:
+            ref = p * x ** (p - 1) if p else np.zeros(n)
+        else:
+            ref = p * (p - 1) * x ** (p - 2) if p >= 2 else np.zeros(n)
+        got = oracle_mod.deriv_lines(f[None, :], order, "closed", h)[0]
+        # rounding scale: largest absolute row sum of B times max|f|
+        _, _, _, B7 = oracle_mod.bands(n, order, "closed", h)
+        scale = np.max(np.sum(np.abs(B7), axis=1)) * max(1.0, np.max(np.abs(f)))
+        assert np.max(np.abs(got - ref)) <= 1e-13 * scale, p
+    # one degree higher is no longer exact at the boundary
+    f = x ** (maxdeg + 1)
+    got = oracle_mod.deriv_lines(f[None, :], order, "closed", h)[0]
+    ref = ((maxdeg + 1) * x ** maxdeg if order == 1
+           else (maxdeg + 1) * maxdeg * x ** (maxdeg - 1))
+    assert np.max(np.abs(got - ref)) > 1e-6
+
+
+def test_sixth_order_convergence_periodic(oracle_mod):
+    """Error against the analytic derivative falls as h^6 (order-of-accuracy study of
+    Sec. 4.2 for n = 32..256)."""
+    for order in (1, 2):
+        errs = []
+        ns = [32, 64, 128]
+        for n in ns:
+            h = 2 * np.pi / n
+            x = np.arange(n) * h
+            f = np.sin(x) + 0.5 * np.cos(2 * x + 0.3)
+            ex = (np.cos(x) - np.sin(2 * x + 0.3)) if order == 1 else \
+                 (-np.sin(x) - 2.0 * np.cos(2 * x + 0.3))
+            got = oracle_mod.deriv_lines(f[None, :], order, "periodic", h)[0]
+            errs.append(np.max(np.abs(got - ex)))
+        rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+        for r in rates:
+            assert 5.7 < r < 6.3, (order, errs, rates)
+
+
+# ------------------------------------------------------------------- adjoint identities
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+@pytest.mark.parametrize("n", [16, 64, 257])
+def test_adjoint_dot_product(oracle_mod, order, bc, n):
+    rng = np.random.default_rng(n * order)
+    h = oracle_mod.grid_spacing(n, bc)
+    f = rng.uniform(-1, 1, (3, n)); g = rng.normal(size=(3, n))
+    Df = oracle_mod.deriv_lines(f, order, bc, h)
+    DTg = oracle_mod.deriv_adjoint_lines(g, order, bc, h)
+    lhs = np.sum(Df * g, axis=1); rhs = np.sum(f * DTg, axis=1)
+    scale = np.sum(np.abs(Df * g), axis=1)
+    assert np.all(np.abs(lhs - rhs) <= 1e-13 * scale)
+
+
+@pytest.mark.parametrize("n", [16, 96])
+def test_periodic_adjoint_symmetry(oracle_mod, n):
+    rng = np.random.default_rng(n)
+    h = 2 * np.pi / n
+    g = rng.normal(size=(4, n))
+    d1 = oracle_mod.deriv_lines(g, 1, "periodic", h)
+    d1t = oracle_mod.deriv_adjoint_lines(g, 1, "periodic", h)
+    np.testing.assert_allclose(d1t, -d1, rtol=0, atol=1e-13 * np.max(np.abs(d1)))
+    d2 = oracle_mod.deriv_lines(g, 2, "periodic", h)
+    d2t = oracle_mod.deriv_adjoint_lines(g, 2, "periodic", h)
+    np.testing.assert_allclose(d2t, d2, rtol=0, atol=1e-13 * np.max(np.abs(d2)))
+
+
+# ----------------------------------------------------------------------------- layouts
+
+def test_layout_hand_enumerated_example(oracle_mod):
+    shape = (2, 2, 3)  # (nz, ny, nx)
+    cart = np.arange(12, dtype=np.float64).reshape(shape)  # v = x + 3y + 6z
+    want = {}
+    with open(os.path.join(GOLDEN, "layout_tiny.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                parts = line.split()
+                want[parts[0]] = [float(v) for v in parts[1:]]
+    for d in "xyz":
+        lay = oracle_mod.to_layout(cart, d, 2)
+        assert lay.tolist() == want[d], d
+        back = oracle_mod.from_layout(lay, d, shape, 2)
+        assert np.array_equal(back, cart)
+
+
+def test_layout_round_trip_and_derivative_consistency(oracle_mod):
+    rng = np.random.default_rng(3)
+    shape = (8, 16, 32)
+    cart = rng.uniform(-1, 1, shape)
+    for d in "xyz":
+        lay = oracle_mod.to_layout(cart, d, 8)
+        assert np.array_equal(oracle_mod.from_layout(lay, d, shape, 8), cart)
+    # derivative along y via lines equals the same derivative along x of the transposed field
+    dy = oracle_mod.deriv(cart, "y", 1, "periodic")
+    dx_t = oracle_mod.deriv(np.ascontiguousarray(cart.transpose(0, 2, 1)), "x", 1, "periodic")
+    assert np.array_equal(dy, dx_t.transpose(0, 2, 1))
