@@ -1,0 +1,457 @@
+"""Benchmark of the compact-derivative hot path on one or more GPUs (one process per GPU).
+
+Workload (default): a 512^3 periodic field, sum of 4 Fourier modes (k <= 100) plus N(0, 0.1)
+noise, P = 8 chunks per line.  One step is one pass of the whole path, in FP64 and then in
+FP32 storage:
+    x layout:  D1 u, D2 u, D1^T u          (first, second derivative, adjoint of the first)
+    reorder x -> y;  the same three along y
+    reorder y -> z;  the same three along z
+i.e. 18 directional operators of 512^3 points and 4 reorders.  ``value`` is directional-
+derivative points per second (Gpoints/s) over all ranks, with the field resident in HBM;
+every field is 0.5-1 GiB, larger than L2, so no flush is needed between steps.
+
+``e2e`` repeats the step through host buffers: the x-layout field comes from pinned host
+memory each step (``tds_deriv_host`` copies it in for the first operator) and every one of
+the 18 results is copied back to pinned host memory.
+
+``--impl reference`` times the FP64 CPU oracle (plain C, one core) on a bounded sample of the
+same workload (slabs of lines along each direction), with the same metric.
+
+Multi-GPU (torchrun): every rank runs the same workload on its own field (independent
+problems: weak scaling, no data exchange); timing is max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gpoints/s and % of HBM roofline per directional derivative, FP64 vs FP32"
+UNIT = "Gpoints/s"
+KERNEL_SRC = os.path.join(ROOT, "paper_2411_13532_gb300", "csrc", "tds_kernels.cu")
+
+# FP64 pipe operations per point of each directional operator as the kernels issue them
+# (interior rows): stencil (antisymmetric 4, symmetric 5), forward pass 2, backward pass 1,
+# substitution 2; the adjoint applies the transposed stencil after the substitution.
+FP64_OPS_PER_POINT = {"d1": 9, "d2": 10, "d1t": 9}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--P", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def file_hash(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:12]
+
+
+def traffic_from_profiles(kernel_key):
+    """DRAM bytes per launch from profiles/traffic.txt: lines '<key> <bytes> <src-hash>'.
+    None if absent or if the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        cur = file_hash(KERNEL_SRC)
+        with open(path) as fh:
+            for line in fh:
+                parts = line.split()
+                if len(parts) == 3 and not line.startswith("#") and parts[0] == kernel_key:
+                    return float(parts[1]) if parts[2] == cur else None
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            p = [v.strip() for v in line.split(",")]
+            if len(p) >= 9:
+                try:
+                    rows.append((float(p[1]), float(p[2]), p[5:9]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_13532_gb300 as tds
+    from paper_2411_13532_gb300 import inputs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    S, P = args.size, args.P
+    shape = (S, S, S)
+    npts = S ** 3
+    f, _ = inputs.fourier_field(shape, seed=2 + rank, kmax=100, noise=0.1, noise_kind="normal",
+                                device=dev)
+    dtypes = [("f64", torch.float64), ("f32", torch.float32)]
+    data = {}
+    for name, dt in dtypes:
+        cart = f.to(dt)
+        ux = tds.reorder(cart, shape, "cart", "x")
+        del cart
+        d = {"ux": ux, "uy": torch.empty_like(ux), "uz": torch.empty_like(ux),
+             "o": [torch.empty_like(ux) for _ in range(3)], "plans": {}}
+        for direc in "xyz":
+            for order in (1, 2):
+                d["plans"][(direc, order)] = tds.Plan(shape, direc, order, "periodic", P=P, dtype=dt)
+        d["ws"] = {k: p.workspace() for k, p in d["plans"].items()}
+        data[name] = d
+    del f
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+
+    # per-operator CUDA events on the launching stream
+    timing = {}
+
+    def timed(key, fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        timing.setdefault(key, []).append((e0, e1))
+
+    launches = [0]
+
+    def step(record):
+        for name, _ in dtypes:
+            d = data[name]
+            src = d["ux"]
+            for direc, nxt in (("x", "uy"), ("y", "uz"), ("z", None)):
+                p1, p2 = d["plans"][(direc, 1)], d["plans"][(direc, 2)]
+                w1, w2 = d["ws"][(direc, 1)], d["ws"][(direc, 2)]
+                ops = [("d1", lambda: p1.deriv(src, d["o"][0], w1)),
+                       ("d2", lambda: p2.deriv(src, d["o"][1], w2)),
+                       ("d1t", lambda: p1.adjoint(src, d["o"][2], w1))]
+                for key, fn in ops:
+                    if record:
+                        timed((name, key, p1.variant if key != "d2" else p2.variant), fn)
+                    else:
+                        fn()
+                    launches[0] += 1 if p1.variant == "resident" else 3
+                if nxt is not None:
+                    rfn = (lambda s=src, t=d[nxt], a=direc, b={"uy": "y", "uz": "z"}[nxt]:
+                           tds.reorder(s, shape, a, b, out=t))
+                    if record:
+                        timed((name, "reorder"), rfn)
+                    else:
+                        rfn()
+                    launches[0] += 1
+                    src = d[nxt]
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches[0] = 0
+    timing.clear()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    gpu_launches = launches[0]
+    if world > 1:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ops_per_step = 18
+    value = world * ops_per_step * npts * args.steps / (ms * 1e-3) / 1e9
+
+    # per-kernel averages
+    per = {}
+    for key, evs in timing.items():
+        per[key] = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    breakdown = {}
+    for key, avg_ms in sorted(per.items()):
+        name = key[0]
+        es = 8 if name == "f64" else 4
+        gpts = npts / (avg_ms * 1e-3) / 1e9
+        gbs = 2 * es * npts / (avg_ms * 1e-3) / 1e9
+        ent = {"ms": round(avg_ms, 4), "gpoints_s": round(gpts, 2), "alg_GB_s": round(gbs, 1),
+               "hbm_frac": round(gbs / hbm, 4)}
+        breakdown["/".join(str(k) for k in key)] = ent
+    # dominant kernel by total time
+    totals = {k: per[k] * len(timing[k]) for k in per}
+    dom = max(totals, key=totals.get)
+    dom_ms = per[dom]
+    es = 8 if dom[0] == "f64" else 4
+    clocks = clk.summary()
+    roofline = None
+    if dom[0] == "f64" and dom[1] != "reorder":
+        # FP64 pipe bound: ops per point issued by the kernel vs the FP64 pipe's peak rate,
+        # 2 FP64 instructions per clock per SM x 152 SMs x sampled SM clock
+        sm_mhz = clocks["sm_mhz"] or 2070.0
+        peak = 2 * 152 * sm_mhz * 1e6 / 1e9
+        ach = FP64_OPS_PER_POINT[dom[1]] * npts / (dom_ms * 1e-3) / 1e9
+        roofline = {"kernel": "/".join(str(k) for k in dom), "bound": "alu", "achieved": round(ach, 1),
+                    "peak": round(peak, 1), "unit": "Gop/s (FP64 pipe)", "frac": round(ach / peak, 4),
+                    "peak_source": "derived: 2 FP64 ops/clk/SM x 152 SMs x median SM clock",
+                    "hbm_frac": round(2 * es * npts / (dom_ms * 1e-3) / 1e9 / hbm, 4)}
+    else:
+        ach = 2 * es * npts / (dom_ms * 1e-3) / 1e9
+        roofline = {"kernel": "/".join(str(k) for k in dom), "bound": "hbm", "achieved": round(ach, 1),
+                    "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+                    "peak_source": peak_kind}
+    kkey = "%s_%s_%s_%d" % (dom[0], dom[1], dom[2] if len(dom) > 2 else "", S)
+    roofline["traffic"] = traffic_from_profiles(kkey)
+    # the FP32 derivative kernels against HBM (the 70 % target)
+    f32 = [v for k, v in breakdown.items() if k.startswith("f32/d")]
+    roofline["f32_deriv_hbm_frac_min"] = min(e["hbm_frac"] for e in f32) if f32 else None
+
+    # ------------------------------------------------------------------ end to end
+    e2e = None
+    if args.e2e_steps > 0:
+        host = {}
+        for name, dt in dtypes:
+            d = data[name]
+            host[name] = {"in": torch.empty(d["ux"].numel(), dtype=dt, pin_memory=True),
+                          "out": [torch.empty(d["ux"].numel(), dtype=dt, pin_memory=True)
+                                  for _ in range(9)]}
+            host[name]["in"].copy_(d["ux"])
+        h2d = sum(host[n]["in"].numel() * host[n]["in"].element_size() for n in host)
+        d2h = sum(o.numel() * o.element_size() for n in host for o in host[n]["out"])
+
+        def e2e_step():
+            for name, _ in dtypes:
+                d, hb = data[name], host[name]
+                i = 0
+                src = d["ux"]
+                for direc, nxt in (("x", "uy"), ("y", "uz"), ("z", None)):
+                    p1, p2 = d["plans"][(direc, 1)], d["plans"][(direc, 2)]
+                    w1, w2 = d["ws"][(direc, 1)], d["ws"][(direc, 2)]
+                    if direc == "x":
+                        # host field in, first result out, through the host-buffer entry point
+                        p1.deriv_host(hb["in"], hb["out"][i], src, d["o"][0], w1)
+                    else:
+                        p1.deriv(src, d["o"][0], w1)
+                        hb["out"][i].copy_(d["o"][0], non_blocking=True)
+                    p2.deriv(src, d["o"][1], w2)
+                    hb["out"][i + 1].copy_(d["o"][1], non_blocking=True)
+                    p1.adjoint(src, d["o"][2], w1)
+                    hb["out"][i + 2].copy_(d["o"][2], non_blocking=True)
+                    i += 3
+                    if nxt is not None:
+                        b = {"uy": "y", "uz": "z"}[nxt]
+                        tds.reorder(src, shape, direc, b, out=d[nxt])
+                        src = d[nxt]
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(b)
+        if world > 1:
+            tt = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ems = float(tt.item())
+        e2e = {"value": round(world * ops_per_step * npts * args.e2e_steps / (ems * 1e-3) / 1e9, 3),
+               "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": round(ems / args.e2e_steps, 3)}
+
+    status = tds.device_status()
+    if status != 0:
+        raise RuntimeError("device status %d after the timed region" % status)
+    return {"value": value, "ms": ms, "roofline": roofline, "breakdown": breakdown,
+            "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches}
+
+
+# ------------------------------------------------------------------------ CPU oracle arm
+
+def oracle_sample_step(S, lines_per_dir, rng_seed=0):
+    """One bounded sample of the step on the CPU oracle: for each direction, a slab of
+    ``lines_per_dir`` whole lines of S points taken from a Cartesian field, the three
+    operators, in FP64 and again on the FP32-rounded field.  Returns points processed."""
+    import numpy as np
+    import oracle
+    side = int(math.sqrt(lines_per_dir))
+    rng = np.random.default_rng(rng_seed)
+    pts = 0
+    for prec in ("f64", "f32"):
+        for direc in "xyz":
+            shp = {"x": (side, side, S), "y": (side, S, side), "z": (S, side, side)}[direc]
+            cart = rng.normal(size=shp)
+            if prec == "f32":
+                cart = cart.astype(np.float32).astype(np.float64)
+            oracle.deriv(cart, direc, 1, "periodic")
+            oracle.deriv(cart, direc, 2, "periodic")
+            oracle.deriv_adjoint(cart, direc, 1, "periodic")
+            pts += 3 * cart.size
+    return pts
+
+
+def time_oracle(S, seconds_target=10.0):
+    import oracle
+    oracle.build()
+    lines = 1024
+    t = time.perf_counter()
+    pts = oracle_sample_step(S, lines)
+    dt = time.perf_counter() - t
+    # grow the sample to roughly the target duration
+    reps = max(1, int(seconds_target / max(dt, 1e-3)))
+    t = time.perf_counter()
+    tot = 0
+    for r in range(reps):
+        tot += oracle_sample_step(S, lines, rng_seed=r + 1)
+    dt = time.perf_counter() - t
+    return tot / dt / 1e9, "%d x (18 operators on %d lines of %d points each, 3 directions, " \
+        "FP64 and FP32-rounded input), %.1f s" % (reps, lines, S, dt)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    S = args.size
+    lines = 4096
+    for _ in range(args.warmup):
+        oracle_sample_step(S, lines, 0)
+    t = time.perf_counter()
+    pts = 0
+    for k in range(args.steps):
+        pts += oracle_sample_step(S, lines, k + 1)
+    dt = time.perf_counter() - t
+    value = pts / dt / 1e9
+    sample = ("per step: 18 operators (D1, D2, D1^T along x, y, z; FP64 and FP32-rounded input) "
+              "on %d whole lines of %d points per direction" % (lines, S))
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "compact derivatives %d^3 periodic, sampled lines (CPU oracle)" % S,
+                       "P": args.P, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            v, sample = time_oracle(args.size)
+            cpu = {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        S = args.size
+        line = {
+            "metric": METRIC, "value": round(res["value"], 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(res["ms"] / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic (seeded Fourier modes k<=100 + N(0,0.1) noise)",
+            "config": {"workload": "compact derivatives %d^3 periodic, P=%d, D1/D2/D1^T along x,y,z "
+                                   "in FP64 and FP32 + 4 reorders per step" % (S, args.P),
+                       "grid": [S, S, S], "P": args.P, "operators_per_step": 18,
+                       "l2": "inputs larger than L2 (%.2f GiB per FP64 field)" % (S ** 3 * 8 / 2 ** 30)},
+            "clocks": res["clocks"], "e2e": res["e2e"], "gpu_launches": res["gpu_launches"],
+            "roofline": res["roofline"], "breakdown": res["breakdown"], "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

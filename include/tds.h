@@ -1,0 +1,188 @@
+/*
+ * tds.h -- C ABI of the GB300 compact finite-difference derivative library (libtds.so).
+ *
+ * The library computes batched sixth-order compact finite-difference derivatives along one
+ * direction of a 3D field with the DistD2 algorithm (Sec. 4.2 of Akkurt et al., "A
+ * Distributed-memory Tridiagonal Solver Based on a Specialised Data Structure Optimised for
+ * CPU and GPU Architectures"): the stencil right-hand side (Eq. cfds) is fused into a
+ * modified-Thomas decoupling sweep over P chunks per line (Algorithm 5), a reduced system
+ * couples the chunk ends, and a substitution finishes each line (Algorithm 6).  The P chunks
+ * stand in for the paper's ranks; all of them live on one GPU.
+ *
+ * Conventions shared by every call:
+ *  - Data pointers are DEVICE pointers unless a name says "host".  The caller owns them.
+ *  - Fields use the interleaved group data structure of Sec. 4.1: for derivative direction
+ *    d with n points per line and N lines, element (s, j, g) of the direction-d layout is at
+ *    flat offset s + SZ*(j + n*g), for line l = g*SZ + s.  Lines are numbered
+ *        x lines: l = y + ny*z   (n = nx)
+ *        y lines: l = x + nx*z   (n = ny)
+ *        z lines: l = x + nx*y   (n = nz)
+ *    The Cartesian layout is x + nx*(y + ny*z).  Only SZ = 32 is supported.
+ *  - Element type: TDS_F64 = IEEE double, TDS_F32 = IEEE float.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default stream).  All
+ *    work is asynchronous on that stream.  Argument and shape errors are returned before any
+ *    launch; launch failures come back as TDS_ERR_CUDA.  No C++ exception crosses the ABI.
+ *  - The hot calls (tds_deriv, tds_deriv_adjoint, tds_reorder) allocate nothing.  Device
+ *    memory is allocated only by tds_plan_create and freed by tds_plan_destroy.
+ *  - A plan is immutable after creation and may be used from several streams at once,
+ *    each with its own workspace.
+ */
+#ifndef TDS_H
+#define TDS_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define TDS_API __attribute__((visibility("default")))
+#else
+#define TDS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TDS_OK = 0,
+    TDS_ERR_ARG = 1,        /* invalid argument (null pointer, unknown enum, bad h or SZ)  */
+    TDS_ERR_SHAPE = 2,      /* shape rule violated (see tds_plan_create)                    */
+    TDS_ERR_ALIAS = 3,      /* input and output buffers overlap                             */
+    TDS_ERR_WORKSPACE = 4,  /* workspace missing or smaller than tds_workspace_bytes        */
+    TDS_ERR_CUDA = 5,       /* a CUDA runtime call or kernel launch failed                  */
+    TDS_ERR_TIMEOUT = 6,    /* a device-side bounded wait gave up (see tds_device_status)   */
+    TDS_ERR_NOMEM = 7       /* device or host allocation failed in tds_plan_create          */
+} tds_status;
+
+typedef enum { TDS_DIR_X = 0, TDS_DIR_Y = 1, TDS_DIR_Z = 2 } tds_dir;
+typedef enum { TDS_LAYOUT_CART = 0, TDS_LAYOUT_X = 1, TDS_LAYOUT_Y = 2, TDS_LAYOUT_Z = 3 } tds_layout;
+typedef enum { TDS_BC_PERIODIC = 0, TDS_BC_CLOSED = 1 } tds_bc;
+typedef enum { TDS_F64 = 0, TDS_F32 = 1 } tds_dtype;
+typedef enum { TDS_REDUCED_EXACT = 0, TDS_REDUCED_PAPER_DROP = 1 } tds_reduced;
+
+/* Kernel pipeline a plan uses; TDS_VARIANT_AUTO lets the plan choose. */
+typedef enum {
+    TDS_VARIANT_AUTO = 0,
+    TDS_VARIANT_RESIDENT = 1,   /* one CTA holds a whole group of SZ lines on chip          */
+    TDS_VARIANT_STREAMING = 2   /* decouple / reduced / substitute as three kernels         */
+} tds_variant;
+
+typedef struct tds_plan tds_plan;
+
+/*
+ * tds_plan_create -- operator preprocessing (Algorithm 4, Sec. 4.2), in FP64 on the host,
+ * "carried out only once for each distinct operation".
+ *   out   : receives the new plan (set to NULL on error).
+ *   nx, ny, nz : Cartesian grid; the line length n is the extent along dir, the number of
+ *           lines N is the product of the two others.
+ *   dir   : derivative direction.
+ *   order : 1 (first derivative, Eq. cfds: alpha=1/3, a=14/9, b=1/9) or 2 (second
+ *           derivative: alpha=2/11, a=12/11, b=3/11).
+ *   bc    : TDS_BC_PERIODIC (cyclic lines) or TDS_BC_CLOSED (one-sided closures:
+ *           first derivative f'0 + 2f'1 = (-5f0 + 4f1 + f2)/2h, f'0/4 + f'1 + f'2/4 =
+ *           (3/2)(f2 - f0)/2h; second derivative f''0 + 11f''1 = (13f0 - 27f1 + 15f2 - f3)/h^2,
+ *           f''0/10 + f''1 + f''2/10 = (6/5)(f0 - 2f1 + f2)/h^2; mirrored at the far end).
+ *   P     : chunks per line (the emulated ranks); n % P == 0, m = n/P >= 4.
+ *   h     : grid spacing (> 0).
+ *   dtype : storage and sweep precision.  TDS_F32 keeps the reduced chunk-end system and the
+ *           Sherman-Morrison correction in FP64.
+ *   sz    : group size SZ; must be 32.
+ *   mode  : TDS_REDUCED_EXACT solves the full 2P-unknown chunk-end system;
+ *           TDS_REDUCED_PAPER_DROP drops the two sub-machine-epsilon couplings per chunk
+ *           (Fig. alg), leaving independent 2x2 systems across chunk boundaries.
+ * Shape rules (TDS_ERR_SHAPE): n >= 8, n % P == 0, n / P >= 4, N % 32 == 0.
+ */
+TDS_API tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_dir dir, int order,
+                           tds_bc bc, int P, double h, tds_dtype dtype, int sz,
+                           tds_reduced mode);
+
+/* Choose the kernel pipeline of a plan (tuning and test hook; call before first use, not
+ * concurrently with a call that uses the plan).  TDS_ERR_ARG if the plan cannot run the
+ * requested variant (a resident group larger than one CTA's shared memory). */
+TDS_API tds_status tds_plan_set_variant(tds_plan *plan, tds_variant variant);
+
+/* Describe a plan: line length n, lines N, chunks P, the variant it will run, and the
+ * dynamic shared memory per CTA of its resident kernel (0 if streaming).  Any output
+ * pointer may be NULL. */
+TDS_API tds_status tds_plan_info(const tds_plan *plan, int *n, int *nlines, int *P, int *variant,
+                         int *smem_bytes);
+
+/* Bytes of device workspace tds_deriv / tds_deriv_adjoint need with this plan (0 is
+ * possible).  The workspace must be 256-byte aligned; its contents need no initialisation
+ * and are garbage afterwards. */
+TDS_API tds_status tds_workspace_bytes(const tds_plan *plan, size_t *bytes);
+
+/*
+ * tds_deriv -- out = A^{-1} B in along the plan's direction (Algorithms 5 and 6 with the
+ * reduced chunk-end system in between).
+ *   in, out : device arrays of N*n elements of the plan's dtype, both in the direction
+ *             layout of the plan; they must not overlap (TDS_ERR_ALIAS).  16-byte aligned.
+ *   ws, ws_bytes : device workspace of at least tds_workspace_bytes (may be NULL if that
+ *             is 0), TDS_ERR_WORKSPACE otherwise.
+ */
+TDS_API tds_status tds_deriv(const tds_plan *plan, const void *in, void *out, void *ws,
+                     size_t ws_bytes, void *stream);
+
+/*
+ * tds_deriv_adjoint -- out = B^T A^{-T} g, the transpose of tds_deriv's operator (not in
+ * the paper: used to back-propagate through a derivative).  Same arguments and rules as
+ * tds_deriv; the transposed tridiagonal solve runs through the same DistD2 pipeline on
+ * A^T, followed by the transposed stencil.
+ */
+TDS_API tds_status tds_deriv_adjoint(const tds_plan *plan, const void *g, void *out, void *ws,
+                             size_t ws_bytes, void *stream);
+
+/*
+ * tds_deriv_host -- tds_deriv on HOST buffers: copies host_in to d_in, runs tds_deriv into
+ * d_out and copies d_out back to host_out, all on stream (the caller synchronises).  Pinned
+ * host memory makes the copies asynchronous.  d_in, d_out, ws are caller-owned device
+ * buffers as in tds_deriv.
+ */
+TDS_API tds_status tds_deriv_host(const tds_plan *plan, const void *host_in, void *host_out,
+                          void *d_in, void *d_out, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * tds_reorder -- permute a field between the Cartesian layout and the x, y, z direction
+ * layouts (Sec. 4.1: "the data layout is specific to a direction in the domain, and it
+ * requires reordering"); a pure permutation, bit-exact.
+ *   in, out : device arrays of nx*ny*nz elements, non-overlapping (TDS_ERR_ALIAS), 16-byte
+ *             aligned.
+ * Shape rules (TDS_ERR_SHAPE): nx % 32 == 0 and ny % 32 == 0 (so that every layout's SZ-row
+ * is a run of 32 consecutive x or y), ny <= 65535, nz <= 65535; from == to is a plain copy.
+ */
+TDS_API tds_status tds_reorder(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
+                       tds_layout to, tds_dtype dtype, int sz, void *stream);
+
+/* Free a plan and its device arrays (NULL is a no-op).  Not stream-ordered: the caller makes
+ * sure no work that uses the plan is still running. */
+TDS_API void tds_plan_destroy(tds_plan *plan);
+
+/* Static, human-readable name of a status code. */
+TDS_API const char *tds_status_string(tds_status status);
+
+/*
+ * tds_device_status -- read and clear the device-side status word of the current device.
+ * Kernels that wait on an asynchronous copy bound their waits; a wait that gives up sets this
+ * word (TDS_ERR_TIMEOUT), skips its writes and returns.  Synchronises the device.
+ */
+TDS_API tds_status tds_device_status(void);
+
+/*
+ * tds_plan_reduced_coeffs -- copy the plan's reduced chunk-end system to host memory for
+ * inspection: for chunk k, row 2k (first unknown F_k) is sub[2k]*L_{k-1} + F_k + sup[2k]*L_k
+ * and row 2k+1 (last unknown L_k) is sub[2k+1]*F_k + L_k + sup[2k+1]*F_{k+1}; on periodic
+ * lines sub[0] couples to L_{P-1} and sup[2P-1] to F_0.  sub and sup hold 2P doubles each.
+ */
+TDS_API tds_status tds_plan_reduced_coeffs(const tds_plan *plan, double *host_sub, double *host_sup);
+
+/*
+ * tds_reduced_solve -- solve the plan's reduced system for many lines (a test entry point
+ * for the communication phase alone): rhs and x are device arrays of N*2P doubles, line
+ * after line, unknowns ordered F_0, L_0, F_1, L_1, ...
+ */
+TDS_API tds_status tds_reduced_solve(const tds_plan *plan, const double *rhs, double *x, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDS_H */

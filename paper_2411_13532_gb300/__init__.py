@@ -1,0 +1,215 @@
+"""GB300-native batched compact finite-difference derivatives (DistD2, arXiv 2411.13532).
+
+Python layer over the C ABI of libtds.so (``include/tds.h``): PyTorch supplies device memory
+and streams, every step of the computation runs in the library's CUDA kernels.
+
+Shapes are Cartesian ``(nz, ny, nx)`` (a field ``cart[z][y][x]``).  A field handed to a plan
+is in the plan direction's interleaved layout (Sec. 4.1), as a contiguous tensor of
+nx*ny*nz elements; ``reorder`` converts between layouts.
+"""
+import ctypes
+import math
+
+import torch
+
+from . import _lib
+from ._lib import TdsError  # noqa: F401
+
+__all__ = ["Plan", "deriv", "deriv_adjoint", "reorder", "CompactDeriv", "compact_deriv",
+           "device_status", "grid_spacing", "TdsError"]
+
+_TORCH_DTYPES = {torch.float64: "f64", torch.float32: "f32"}
+
+
+def grid_spacing(n, bc):
+    """2*pi/n on periodic lines, 2*pi/(n-1) on closed lines (nodes on both ends)."""
+    return 2.0 * math.pi / n if bc == "periodic" else 2.0 * math.pi / (n - 1)
+
+
+def _stream_ptr(stream, device):
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_tensor(t, dtype, numel, what):
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if t.dtype != dtype:
+        raise ValueError("%s has dtype %s, expected %s" % (what, t.dtype, dtype))
+    if not t.is_contiguous() or t.numel() != numel:
+        raise ValueError("%s must be contiguous with %d elements" % (what, numel))
+
+
+class Plan:
+    """One derivative operator: direction, order (1 or 2), boundary condition, P chunks.
+
+    Creation runs the operator preprocessing (Algorithm 4) on the host and uploads it to the
+    current (or given) CUDA device.
+    """
+
+    def __init__(self, shape, direction, order, bc, P=1, h=None, dtype=torch.float64,
+                 mode="exact", variant="auto", device=None):
+        nz, ny, nx = (int(v) for v in shape)
+        self.shape = (nz, ny, nx)
+        self.direction, self.order, self.bc, self.P = direction, int(order), bc, int(P)
+        self.n = {"x": nx, "y": ny, "z": nz}[direction]
+        self.h = float(grid_spacing(self.n, bc) if h is None else h)
+        self.dtype = dtype
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self._handle = None
+        L = _lib.lib()
+        h_ = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(L.tds_plan_create(ctypes.byref(h_), nx, ny, nz, _lib.DIRS[direction],
+                                         self.order, _lib.BCS[bc], self.P, self.h,
+                                         _lib.DTYPES[_TORCH_DTYPES[dtype]], 32,
+                                         _lib.MODES[mode]), "tds_plan_create")
+        self._handle = h_
+        if variant != "auto":
+            _lib.check(L.tds_plan_set_variant(h_, _lib.VARIANTS[variant]), "tds_plan_set_variant")
+        nbytes = ctypes.c_size_t()
+        _lib.check(L.tds_workspace_bytes(h_, ctypes.byref(nbytes)), "tds_workspace_bytes")
+        self.ws_bytes = nbytes.value
+        n_, nl, p_, var, smem = (ctypes.c_int() for _ in range(5))
+        _lib.check(L.tds_plan_info(h_, ctypes.byref(n_), ctypes.byref(nl), ctypes.byref(p_),
+                                   ctypes.byref(var), ctypes.byref(smem)), "tds_plan_info")
+        self.nlines = nl.value
+        self.variant = {1: "resident", 2: "streaming"}[var.value]
+        self.smem_bytes = smem.value
+        self.numel = nx * ny * nz
+
+    def __del__(self):
+        if getattr(self, "_handle", None) is not None and _lib._lib is not None:
+            _lib._lib.tds_plan_destroy(self._handle)
+            self._handle = None
+
+    def workspace(self):
+        """A fresh workspace tensor for this plan (None if it needs none)."""
+        if not self.ws_bytes:
+            return None
+        return torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+
+    def _run(self, fn, x, out, ws, stream, what):
+        _check_tensor(x, self.dtype, self.numel, "input")
+        if out is None:
+            out = torch.empty_like(x)
+        _check_tensor(out, self.dtype, self.numel, "out")
+        if ws is None:
+            ws = self.workspace()
+        wp = ctypes.c_void_p(ws.data_ptr()) if ws is not None else None
+        wb = ws.numel() if ws is not None else 0
+        with torch.cuda.device(self.device):
+            _lib.check(fn(self._handle, ctypes.c_void_p(x.data_ptr()),
+                          ctypes.c_void_p(out.data_ptr()), wp, wb,
+                          _stream_ptr(stream, self.device)), what)
+        return out
+
+    def deriv(self, x, out=None, ws=None, stream=None):
+        """out = A^{-1} B x (x and out in this plan's direction layout)."""
+        return self._run(_lib.lib().tds_deriv, x, out, ws, stream, "tds_deriv")
+
+    def adjoint(self, g, out=None, ws=None, stream=None):
+        """out = B^T A^{-T} g, the transpose of ``deriv``."""
+        return self._run(_lib.lib().tds_deriv_adjoint, g, out, ws, stream, "tds_deriv_adjoint")
+
+    def deriv_host(self, host_in, host_out, d_in, d_out, ws=None, stream=None):
+        """Host buffers in and out through ``tds_deriv_host`` (copies inside the call)."""
+        for t, nm in ((host_in, "host_in"), (host_out, "host_out")):
+            if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != self.numel:
+                raise ValueError("%s must be a contiguous host tensor of %d %s" % (nm, self.numel, self.dtype))
+        _check_tensor(d_in, self.dtype, self.numel, "d_in")
+        _check_tensor(d_out, self.dtype, self.numel, "d_out")
+        if ws is None:
+            ws = self.workspace()
+        wp = ctypes.c_void_p(ws.data_ptr()) if ws is not None else None
+        wb = ws.numel() if ws is not None else 0
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.lib().tds_deriv_host(
+                self._handle, ctypes.c_void_p(host_in.data_ptr()), ctypes.c_void_p(host_out.data_ptr()),
+                ctypes.c_void_p(d_in.data_ptr()), ctypes.c_void_p(d_out.data_ptr()), wp, wb,
+                _stream_ptr(stream, self.device)), "tds_deriv_host")
+        return host_out
+
+    def reduced_coeffs(self):
+        """(sub, sup) of the reduced chunk-end system, 2P doubles each."""
+        R = 2 * self.P
+        sub = (ctypes.c_double * R)()
+        sup = (ctypes.c_double * R)()
+        _lib.check(_lib.lib().tds_plan_reduced_coeffs(self._handle, sub, sup),
+                   "tds_plan_reduced_coeffs")
+        return list(sub), list(sup)
+
+    def reduced_solve(self, rhs, out=None, stream=None):
+        """Solve the reduced system for every line: rhs is (N, 2P) float64 on the device."""
+        numel = self.nlines * 2 * self.P
+        _check_tensor(rhs, torch.float64, numel, "rhs")
+        if out is None:
+            out = torch.empty_like(rhs)
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.lib().tds_reduced_solve(
+                self._handle, ctypes.c_void_p(rhs.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                _stream_ptr(stream, self.device)), "tds_reduced_solve")
+        return out
+
+
+_PLANS = {}
+
+
+def _plan(shape, direction, order, bc, P, h, dtype, mode, device):
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    key = (tuple(shape), direction, order, bc, P, h, dtype, mode, dev)
+    p = _PLANS.get(key)
+    if p is None:
+        p = _PLANS[key] = Plan(shape, direction, order, bc, P, h, dtype, mode, device=dev)
+    return p
+
+
+def deriv(field, shape, direction, order, bc, P=1, h=None, mode="exact", out=None):
+    """Derivative of ``field`` (in ``direction``'s layout) along ``direction``."""
+    return _plan(shape, direction, order, bc, P, h, field.dtype, mode, field.device).deriv(field, out)
+
+
+def deriv_adjoint(g, shape, direction, order, bc, P=1, h=None, mode="exact", out=None):
+    """Transpose of ``deriv`` applied to ``g``."""
+    return _plan(shape, direction, order, bc, P, h, g.dtype, mode, g.device).adjoint(g, out)
+
+
+def reorder(x, shape, src, dst, out=None, stream=None):
+    """Permute a field between layouts 'cart', 'x', 'y', 'z' (bit-exact)."""
+    nz, ny, nx = (int(v) for v in shape)
+    if x.dtype not in _TORCH_DTYPES:
+        raise ValueError("reorder supports float64 and float32")
+    _check_tensor(x, x.dtype, nx * ny * nz, "input")
+    if out is None:
+        out = torch.empty_like(x)
+    _check_tensor(out, x.dtype, nx * ny * nz, "out")
+    with torch.cuda.device(x.device):
+        _lib.check(_lib.lib().tds_reorder(
+            ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), nx, ny, nz,
+            _lib.LAYOUTS[src], _lib.LAYOUTS[dst], _lib.DTYPES[_TORCH_DTYPES[x.dtype]], 32,
+            _stream_ptr(stream, x.device)), "tds_reorder")
+    return out
+
+
+def device_status():
+    """Read and clear the device-side status word (0 = no bounded wait gave up)."""
+    return _lib.lib().tds_device_status()
+
+
+class CompactDeriv(torch.autograd.Function):
+    """y = D x with D = A^{-1} B; the backward pass applies D^T = B^T A^{-T} with the
+    library's adjoint kernels."""
+
+    @staticmethod
+    def forward(ctx, x, plan):
+        ctx.plan = plan
+        return plan.deriv(x.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad):
+        return ctx.plan.adjoint(grad.contiguous()), None
+
+
+def compact_deriv(x, plan):
+    return CompactDeriv.apply(x, plan)

@@ -1,0 +1,188 @@
+// tds_api.cu -- the extern "C" entry points of libtds (declared and documented in tds.h):
+// argument and shape validation, variant selection, and the launches.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "tds_internal.h"
+
+using namespace tds;
+
+namespace {
+
+int extent(int nx, int ny, int nz, tds_dir d) { return d == TDS_DIR_X ? nx : (d == TDS_DIR_Y ? ny : nz); }
+
+bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + bbytes && y < x + abytes;
+}
+
+bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+size_t elem_size(tds_dtype dt) { return dt == TDS_F64 ? 8 : 4; }
+
+size_t ws_need(const tds_plan *p) {
+    return p->variant == TDS_VARIANT_STREAMING ? streaming_ws_bytes(p) : 0;
+}
+
+tds_status run(const tds_plan *p, int which, const void *in, void *out, void *ws, size_t ws_bytes,
+               void *stream) {
+    if (!p || !in || !out) return TDS_ERR_ARG;
+    if (!aligned(in, 16) || !aligned(out, 16)) return TDS_ERR_ARG;
+    const size_t bytes = (size_t)p->n * p->nlines * elem_size(p->dtype);
+    if (overlaps(in, bytes, out, bytes)) return TDS_ERR_ALIAS;
+    const size_t need = ws_need(p);
+    if (need) {
+        if (!ws || ws_bytes < need || !aligned(ws, 256)) return TDS_ERR_WORKSPACE;
+        if (overlaps(ws, need, in, bytes) || overlaps(ws, need, out, bytes)) return TDS_ERR_ALIAS;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p->variant == TDS_VARIANT_RESIDENT) return launch_resident(p, which, in, out, st);
+    return launch_streaming(p, which, in, out, ws, st);
+}
+
+} // namespace
+
+extern "C" {
+
+const char *tds_status_string(tds_status s) {
+    switch (s) {
+    case TDS_OK: return "ok";
+    case TDS_ERR_ARG: return "invalid argument";
+    case TDS_ERR_SHAPE: return "shape rule violated";
+    case TDS_ERR_ALIAS: return "input and output overlap";
+    case TDS_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case TDS_ERR_CUDA: return "CUDA error";
+    case TDS_ERR_TIMEOUT: return "device-side wait timed out";
+    case TDS_ERR_NOMEM: return "out of memory";
+    }
+    return "unknown status";
+}
+
+tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_dir dir, int order,
+                           tds_bc bc, int P, double h, tds_dtype dtype, int sz, tds_reduced mode) {
+    if (!out) return TDS_ERR_ARG;
+    *out = nullptr;
+    if (dir < TDS_DIR_X || dir > TDS_DIR_Z || (order != 1 && order != 2) ||
+        (bc != TDS_BC_PERIODIC && bc != TDS_BC_CLOSED) || (dtype != TDS_F64 && dtype != TDS_F32) ||
+        (mode != TDS_REDUCED_EXACT && mode != TDS_REDUCED_PAPER_DROP) || sz != kSZ ||
+        !(h > 0.0) || !std::isfinite(h) || P < 1)
+        return TDS_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1) return TDS_ERR_SHAPE;
+    const int n = extent(nx, ny, nz, dir);
+    const long long lines = (long long)nx * ny * nz / n;
+    if (n < 8 || n % P != 0 || n / P < 4 || lines % kSZ != 0 || lines > (1ll << 31) - 1 ||
+        (long long)n * lines > (1ll << 40))
+        return TDS_ERR_SHAPE;
+
+    tds_plan *p = new (std::nothrow) tds_plan;
+    if (!p) return TDS_ERR_NOMEM;
+    std::memset(p, 0, sizeof(*p));
+    p->nx = nx; p->ny = ny; p->nz = nz; p->dir = dir; p->order = order; p->bc = bc; p->P = P;
+    p->h = h; p->dtype = dtype; p->mode = mode;
+    p->n = n; p->m = n / P; p->nlines = (int)lines;
+    tds_status s = build_plan(p);
+    if (s != TDS_OK) { tds_plan_destroy(p); return s; }
+
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        tds_plan_destroy(p);
+        return TDS_ERR_CUDA;
+    }
+    const size_t smem = resident_smem_bytes(n, P, dtype);
+    p->resident_smem = (P <= kMaxResidentP && smem <= (size_t)optin) ? (int)smem : 0;
+    p->variant = p->resident_smem ? TDS_VARIANT_RESIDENT : TDS_VARIANT_STREAMING;
+    *out = p;
+    return TDS_OK;
+}
+
+tds_status tds_plan_set_variant(tds_plan *p, tds_variant v) {
+    if (!p) return TDS_ERR_ARG;
+    if (v == TDS_VARIANT_AUTO) v = p->resident_smem ? TDS_VARIANT_RESIDENT : TDS_VARIANT_STREAMING;
+    if (v == TDS_VARIANT_RESIDENT && !p->resident_smem) return TDS_ERR_ARG;
+    if (v != TDS_VARIANT_RESIDENT && v != TDS_VARIANT_STREAMING) return TDS_ERR_ARG;
+    p->variant = v;
+    return TDS_OK;
+}
+
+tds_status tds_plan_info(const tds_plan *p, int *n, int *nlines, int *P, int *variant, int *smem) {
+    if (!p) return TDS_ERR_ARG;
+    if (n) *n = p->n;
+    if (nlines) *nlines = p->nlines;
+    if (P) *P = p->P;
+    if (variant) *variant = (int)p->variant;
+    if (smem) *smem = p->variant == TDS_VARIANT_RESIDENT ? p->resident_smem : 0;
+    return TDS_OK;
+}
+
+tds_status tds_workspace_bytes(const tds_plan *p, size_t *bytes) {
+    if (!p || !bytes) return TDS_ERR_ARG;
+    *bytes = ws_need(p);
+    return TDS_OK;
+}
+
+tds_status tds_deriv(const tds_plan *p, const void *in, void *out, void *ws, size_t ws_bytes,
+                     void *stream) {
+    return run(p, 0, in, out, ws, ws_bytes, stream);
+}
+
+tds_status tds_deriv_adjoint(const tds_plan *p, const void *g, void *out, void *ws,
+                             size_t ws_bytes, void *stream) {
+    return run(p, 1, g, out, ws, ws_bytes, stream);
+}
+
+tds_status tds_deriv_host(const tds_plan *p, const void *host_in, void *host_out, void *d_in,
+                          void *d_out, void *ws, size_t ws_bytes, void *stream) {
+    if (!p || !host_in || !host_out || !d_in || !d_out) return TDS_ERR_ARG;
+    const size_t bytes = (size_t)p->n * p->nlines * elem_size(p->dtype);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(d_in, host_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return TDS_ERR_CUDA;
+    tds_status s = run(p, 0, d_in, d_out, ws, ws_bytes, stream);
+    if (s != TDS_OK) return s;
+    if (cudaMemcpyAsync(host_out, d_out, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return TDS_ERR_CUDA;
+    return TDS_OK;
+}
+
+tds_status tds_reorder(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
+                       tds_layout to, tds_dtype dtype, int sz, void *stream) {
+    if (!in || !out || sz != kSZ || (dtype != TDS_F64 && dtype != TDS_F32) ||
+        from < TDS_LAYOUT_CART || from > TDS_LAYOUT_Z || to < TDS_LAYOUT_CART || to > TDS_LAYOUT_Z)
+        return TDS_ERR_ARG;
+    if (!aligned(in, 16) || !aligned(out, 16)) return TDS_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || nx % kSZ || ny % kSZ || nz > 65535 || ny > 65535 ||
+        (long long)nx * ny * nz > (1ll << 40))
+        return TDS_ERR_SHAPE;
+    const size_t bytes = (size_t)nx * ny * nz * elem_size(dtype);
+    if (overlaps(in, bytes, out, bytes)) return TDS_ERR_ALIAS;
+    return launch_reorder(in, out, nx, ny, nz, from, to, elem_size(dtype),
+                          static_cast<cudaStream_t>(stream));
+}
+
+void tds_plan_destroy(tds_plan *p) {
+    if (!p) return;
+    if (p->dmem) cudaFree(p->dmem);
+    std::free(p->hmem);
+    delete p;
+}
+
+tds_status tds_device_status(void) { return read_device_status(); }
+
+tds_status tds_plan_reduced_coeffs(const tds_plan *p, double *sub, double *sup) {
+    if (!p || !sub || !sup) return TDS_ERR_ARG;
+    std::memcpy(sub, p->red_sub_host[0], sizeof(double) * 2 * p->P);
+    std::memcpy(sup, p->red_sup_host[0], sizeof(double) * 2 * p->P);
+    return TDS_OK;
+}
+
+tds_status tds_reduced_solve(const tds_plan *p, const double *rhs, double *x, void *stream) {
+    if (!p || !rhs || !x) return TDS_ERR_ARG;
+    const size_t rb = sizeof(double) * 2 * p->P * (size_t)p->nlines;
+    if (overlaps(rhs, rb, x, rb)) return TDS_ERR_ALIAS;
+    return launch_reduced_only(p, rhs, x, static_cast<cudaStream_t>(stream));
+}
+
+} // extern "C"

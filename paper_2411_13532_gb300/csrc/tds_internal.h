@@ -1,0 +1,87 @@
+// tds_internal.h -- types shared by the host planner, the kernels and the C ABI of libtds.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "tds.h"
+
+namespace tds {
+
+constexpr int kSZ = 32;           // lines per group: one warp lane per line (Sec. 4.1, SZ=32)
+constexpr int kTaps = 7;          // stencil offsets -3..3 (closure rows reach 3 points in)
+constexpr int kEdgeRows = 4;      // closed lines: rows 0..3 and n-4..n-1 carry their own taps
+constexpr int kMaxResidentP = 16; // resident kernel: one warp per chunk, at most 16 warps
+
+// Number of per-row coefficient arrays of one operator (Algorithm 4 output, per chunk class):
+//   f  : forward factor, 1/b_j for j <= 1, 1/(b_j - a_j s^c_{j-1}) for j >= 2
+//   r  : sub-diagonal a_j (eliminated in the forward pass, j >= 2)
+//   w  : backward multiplier (j = 1..m-3) and c_0/b_0 for the final row-0 step (j = 0)
+//   sa : coupling of row j to the chunk's first unknown after both passes (s^a)
+//   sc : coupling of row j to the chunk's last unknown after both passes (s^c)
+enum { kF = 0, kR = 1, kW = 2, kSA = 3, kSC = 4, kNumRowArrays = 5 };
+
+// Reduced-system arrays (2P entries each): sub-diagonal, forward factor, backward multiplier
+// of the (Sherman-Morrison-modified if cyclic) tridiagonal factorisation, and q = T'^{-1} u.
+enum { kRedSub = 0, kRedWf = 1, kRedCp = 2, kRedQ = 3, kNumRedArrays = 4 };
+
+// Operator descriptor passed by value to every kernel.
+struct DevOp {
+    int n, m, P, nlines, ngroups;
+    int periodic;   // cyclic lines
+    int adjoint;    // 1: operator is B^T A^{-T} (solve on A^T, then apply the B^T taps)
+    int symmetric;  // interior taps: +1 symmetric (order 2), -1 antisymmetric (order 1)
+    int ncls;       // chunk classes (first / interior / last differ on closed lines)
+    int cls_first, cls_mid, cls_last;
+    const double *row64;  // [kNumRowArrays][ncls*m]
+    const float *row32;   // the same arrays rounded to float (FP32 sweeps)
+    const double *n1;     // [ncls] row-0 normaliser 1/(1 - s^c_1 s^a_2) (Algorithm 4, last lines)
+    const double *red;    // [kNumRedArrays][2P]
+    int red_cyclic;
+    double red_vlast;     // last entry of the Sherman-Morrison v vector
+    double red_den_inv;   // 1/(1 + v.q)
+    double tap[kTaps];                 // interior stencil taps, offsets -3..3
+    double edge[2 * kEdgeRows][kTaps]; // closed lines: rows 0..3 then n-4..n-1
+};
+
+} // namespace tds
+
+struct tds_plan {
+    int nx, ny, nz;
+    tds_dir dir;
+    int order;
+    tds_bc bc;
+    int P;
+    double h;
+    tds_dtype dtype;
+    tds_reduced mode;
+    int n, m, nlines;
+    tds_variant variant;   // resolved: RESIDENT or STREAMING
+    int resident_smem;     // dynamic shared memory of the resident kernel (0 = cannot run)
+    tds::DevOp op[2];      // [0] = A^{-1} B, [1] = B^T A^{-T}
+    double *red_sub_host[2], *red_sup_host[2];
+    void *dmem;            // one device allocation holding every array of both operators
+    void *hmem;            // host copies (reduced coefficients)
+};
+
+namespace tds {
+
+// Planner (host, FP64): fills both operator descriptors; returns TDS_ERR_ARG on a zero pivot.
+tds_status build_plan(tds_plan *p);
+
+// Kernel launchers (tds_kernels.cu).  Each returns TDS_ERR_CUDA on a launch failure.
+size_t resident_smem_bytes(int n, int P, tds_dtype dtype);
+tds_status launch_resident(const tds_plan *p, int which, const void *in, void *out,
+                           cudaStream_t st);
+size_t streaming_ws_bytes(const tds_plan *p);
+tds_status launch_streaming(const tds_plan *p, int which, const void *in, void *out,
+                            void *ws, cudaStream_t st);
+tds_status launch_reduced_only(const tds_plan *p, const double *rhs, double *x,
+                               cudaStream_t st);
+tds_status launch_reorder(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
+                          tds_layout to, size_t elem, cudaStream_t st);
+tds_status read_device_status();
+
+} // namespace tds

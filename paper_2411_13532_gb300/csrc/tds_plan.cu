@@ -1,0 +1,279 @@
+// tds_plan.cu -- host-side operator preprocessing (Algorithm 4, Sec. 4.2), in FP64.
+//
+// For one derivative operator the planner produces
+//   * the tridiagonal band of A and the stencil taps of B (Eq. cfds and its closures),
+//   * per chunk class the Algorithm 4 arrays f, r, w, s^a, s^c and the row-0 normaliser,
+//   * the reduced chunk-end system and its factorisation (cyclic: Sherman-Morrison),
+// for A^{-1} B and for its transpose B^T A^{-T}.  Everything is uploaded once to the device;
+// the kernels only read it.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "tds_internal.h"
+
+namespace tds {
+namespace {
+
+// Band of A over the whole line: row J is a[J] u[J-1] + b[J] u[J] + c[J] u[J+1]; on cyclic
+// lines a[0] multiplies u[n-1] and c[n-1] multiplies u[0].  Stencil of B as taps[J][o+3].
+struct LineOperator {
+    std::vector<double> a, b, c;
+    std::vector<double> taps;  // n * kTaps
+};
+
+void scheme_line(int n, int order, bool periodic, double h, LineOperator &L) {
+    L.a.assign(n, 0.0); L.b.assign(n, 1.0); L.c.assign(n, 0.0);
+    L.taps.assign((size_t)n * kTaps, 0.0);
+    double alpha, t0, t1, t2;
+    if (order == 1) {          // Eq. cfds: alpha = 1/3, a = 14/9 over 2h, b = 1/9 over 4h
+        alpha = 1.0 / 3.0;
+        t1 = (14.0 / 9.0) / (2.0 * h);
+        t2 = (1.0 / 9.0) / (4.0 * h);
+        t0 = 0.0;
+    } else {                   // sixth-order second derivative: 2/11, 12/11 over h^2, 3/11 over 4h^2
+        alpha = 2.0 / 11.0;
+        t1 = (12.0 / 11.0) / (h * h);
+        t2 = (3.0 / 11.0) / (4.0 * h * h);
+        t0 = -2.0 * (t1 + t2);
+    }
+    const double sgn = (order == 1) ? -1.0 : 1.0;  // weight of the mirrored point
+    for (int J = 0; J < n; ++J) {
+        L.a[J] = alpha; L.c[J] = alpha;
+        double *t = &L.taps[(size_t)J * kTaps + 3];
+        t[-2] = sgn * t2; t[-1] = sgn * t1; t[0] = t0; t[1] = t1; t[2] = t2;
+    }
+    if (periodic) return;
+    auto row = [&](int J) {
+        double *t = &L.taps[(size_t)J * kTaps + 3];
+        for (int o = -3; o <= 3; ++o) t[o] = 0.0;
+        return t;
+    };
+    L.a[0] = 0.0; L.c[n - 1] = 0.0;
+    double *r0 = row(0), *r1 = row(1), *rm = row(n - 2), *rl = row(n - 1);
+    if (order == 1) {
+        // f'0 + 2 f'1 = (-5 f0 + 4 f1 + f2)/2h  and  f'0/4 + f'1 + f'2/4 = (3/2)(f2 - f0)/2h
+        L.c[0] = 2.0;
+        r0[0] = -2.5 / h; r0[1] = 2.0 / h; r0[2] = 0.5 / h;
+        L.a[1] = 0.25; L.c[1] = 0.25;
+        r1[-1] = -0.75 / h; r1[1] = 0.75 / h;
+        L.a[n - 2] = 0.25; L.c[n - 2] = 0.25;
+        rm[-1] = -0.75 / h; rm[1] = 0.75 / h;
+        L.a[n - 1] = 2.0;
+        rl[0] = 2.5 / h; rl[-1] = -2.0 / h; rl[-2] = -0.5 / h;
+    } else {
+        // f''0 + 11 f''1 = (13 f0 - 27 f1 + 15 f2 - f3)/h^2 and
+        // f''0/10 + f''1 + f''2/10 = (6/5)(f0 - 2 f1 + f2)/h^2
+        const double ih2 = 1.0 / (h * h);
+        L.c[0] = 11.0;
+        r0[0] = 13.0 * ih2; r0[1] = -27.0 * ih2; r0[2] = 15.0 * ih2; r0[3] = -1.0 * ih2;
+        L.a[1] = 0.1; L.c[1] = 0.1;
+        r1[-1] = 1.2 * ih2; r1[0] = -2.4 * ih2; r1[1] = 1.2 * ih2;
+        L.a[n - 2] = 0.1; L.c[n - 2] = 0.1;
+        rm[-1] = 1.2 * ih2; rm[0] = -2.4 * ih2; rm[1] = 1.2 * ih2;
+        L.a[n - 1] = 11.0;
+        rl[0] = 13.0 * ih2; rl[-1] = -27.0 * ih2; rl[-2] = 15.0 * ih2; rl[-3] = -1.0 * ih2;
+    }
+}
+
+// A^T and B^T of a line operator: (A^T)_{J,J-1} = c[J-1], (A^T)_{J,J+1} = a[J+1], and the tap
+// of B^T at offset o in row J is B's tap at offset -o in row J+o.
+void transpose_line(int n, bool periodic, const LineOperator &L, LineOperator &T) {
+    T.a.assign(n, 0.0); T.b = L.b; T.c.assign(n, 0.0);
+    T.taps.assign((size_t)n * kTaps, 0.0);
+    for (int J = 0; J < n; ++J) {
+        T.a[J] = (J > 0) ? L.c[J - 1] : (periodic ? L.c[n - 1] : 0.0);
+        T.c[J] = (J < n - 1) ? L.a[J + 1] : (periodic ? L.a[0] : 0.0);
+        for (int o = -3; o <= 3; ++o) {
+            int I = J + o;
+            if (periodic) I = ((I % n) + n) % n;
+            else if (I < 0 || I >= n) continue;
+            T.taps[(size_t)J * kTaps + 3 + o] = L.taps[(size_t)I * kTaps + 3 - o];
+        }
+    }
+}
+
+// Algorithm 4 on one chunk of m rows with local band (a, b, c): a[0] couples to the previous
+// chunk's last unknown, c[m-1] to the next chunk's first.  Returns false on a zero pivot.
+bool preprocess_chunk(int m, const double *a, const double *b, const double *c,
+                      double *f, double *r, double *w, double *sa, double *sc, double *n1) {
+    for (int j = 0; j < 2; ++j) {          // rows 1 and 2 of the paper: normalise only
+        if (b[j] == 0.0) return false;
+        sa[j] = a[j] / b[j];
+        sc[j] = c[j] / b[j];
+        w[j] = sc[j];
+        f[j] = 1.0 / b[j];
+        r[j] = 0.0;   // rows 1 and 2 are not eliminated: d_j = f_j (s_j - r_j d_{j-1}) with r_j = 0
+    }
+    for (int j = 2; j < m; ++j) {          // forward elimination against row j-1
+        const double den = b[j] - a[j] * sc[j - 1];
+        if (den == 0.0 || !std::isfinite(den)) return false;
+        f[j] = 1.0 / den;
+        r[j] = a[j];
+        sa[j] = -f[j] * a[j] * sa[j - 1];
+        sc[j] = f[j] * c[j];
+        w[j] = 0.0;
+    }
+    for (int j = m - 3; j >= 1; --j) {     // backward elimination against row j+1
+        sa[j] = sa[j] - sc[j] * sa[j + 1];
+        w[j] = sc[j];
+        sc[j] = -sc[j] * sc[j + 1];
+    }
+    const double den = 1.0 - sc[0] * sa[1];  // row 1 of the paper eliminates u_2
+    if (den == 0.0 || !std::isfinite(den)) return false;
+    *n1 = 1.0 / den;
+    sa[0] = *n1 * sa[0];
+    sc[0] = -*n1 * sc[0] * sc[1];
+    // w[0] keeps c_0/b_0 for the final row-0 step of the sweep
+    return true;
+}
+
+} // namespace
+
+// Build one operator (A^{-1}B if which == 0, B^T A^{-T} if which == 1) into host buffers.
+static tds_status build_operator(const tds_plan *p, const LineOperator &L, int which,
+                                 DevOp &op, std::vector<double> &rows,
+                                 std::vector<double> &n1s, std::vector<double> &red,
+                                 std::vector<double> &sub, std::vector<double> &sup) {
+    const int n = p->n, m = p->m, P = p->P;
+    const bool periodic = (p->bc == TDS_BC_PERIODIC);
+    std::memset(&op, 0, sizeof(op));
+    op.n = n; op.m = m; op.P = P; op.nlines = p->nlines; op.ngroups = p->nlines / kSZ;
+    op.periodic = periodic; op.adjoint = which;
+    op.symmetric = (p->order == 2) ? 1 : -1;
+
+    // chunk classes: cyclic lines have one; closed lines distinguish first / interior / last
+    int reps[3];
+    if (periodic || P == 1) { op.ncls = 1; reps[0] = 0; op.cls_first = op.cls_mid = op.cls_last = 0; }
+    else if (P == 2) { op.ncls = 2; reps[0] = 0; reps[1] = 1; op.cls_first = 0; op.cls_mid = 0; op.cls_last = 1; }
+    else { op.ncls = 3; reps[0] = 0; reps[1] = 1; reps[2] = P - 1; op.cls_first = 0; op.cls_mid = 1; op.cls_last = 2; }
+
+    const int nc = op.ncls;
+    rows.assign((size_t)kNumRowArrays * nc * m, 0.0);
+    n1s.assign(nc, 0.0);
+    for (int cl = 0; cl < nc; ++cl) {
+        const int k = reps[cl];
+        double *f = &rows[((size_t)kF * nc + cl) * m], *r = &rows[((size_t)kR * nc + cl) * m];
+        double *w = &rows[((size_t)kW * nc + cl) * m], *sa = &rows[((size_t)kSA * nc + cl) * m];
+        double *sc = &rows[((size_t)kSC * nc + cl) * m];
+        if (!preprocess_chunk(m, &L.a[(size_t)k * m], &L.b[(size_t)k * m], &L.c[(size_t)k * m],
+                              f, r, w, sa, sc, &n1s[cl]))
+            return TDS_ERR_ARG;
+    }
+
+    // stencil taps: interior row (any row at least 4 from a closed end) and the edge rows
+    const int mid = n / 2;
+    for (int o = 0; o < kTaps; ++o) op.tap[o] = L.taps[(size_t)mid * kTaps + o];
+    if (!periodic) {
+        for (int e = 0; e < kEdgeRows; ++e)
+            for (int o = 0; o < kTaps; ++o) {
+                op.edge[e][o] = L.taps[(size_t)e * kTaps + o];
+                op.edge[kEdgeRows + e][o] = L.taps[(size_t)(n - kEdgeRows + e) * kTaps + o];
+            }
+    }
+
+    // reduced chunk-end system, unknowns F_0, L_0, F_1, L_1, ... (2P)
+    const int R = 2 * P;
+    sub.assign(R, 0.0); sup.assign(R, 0.0);
+    for (int k = 0; k < P; ++k) {
+        const int cl = (k == 0) ? op.cls_first : (k == P - 1 ? op.cls_last : op.cls_mid);
+        const double *sa = &rows[((size_t)kSA * nc + cl) * m];
+        const double *sc = &rows[((size_t)kSC * nc + cl) * m];
+        sub[2 * k] = sa[0];          // row F_k: coupling to L_{k-1}
+        sup[2 * k] = sc[0];          //          coupling to its own L_k
+        sub[2 * k + 1] = sa[m - 1];  // row L_k: coupling to its own F_k
+        sup[2 * k + 1] = sc[m - 1];  //          coupling to F_{k+1}
+        if (p->mode == TDS_REDUCED_PAPER_DROP) { sup[2 * k] = 0.0; sub[2 * k + 1] = 0.0; }
+    }
+    red.assign((size_t)kNumRedArrays * R, 0.0);
+    double *rsub = &red[(size_t)kRedSub * R], *wf = &red[(size_t)kRedWf * R];
+    double *cp = &red[(size_t)kRedCp * R], *q = &red[(size_t)kRedQ * R];
+    std::vector<double> diag(R, 1.0);
+    for (int i = 0; i < R; ++i) rsub[i] = sub[i];
+    op.red_cyclic = periodic;
+    double gamma = -1.0;
+    if (periodic) {   // A = T' + u v^T, u = (gamma, 0.., sup_last), v = (1, 0.., sub_0/gamma)
+        diag[0] = 1.0 - gamma;
+        diag[R - 1] = 1.0 - sub[0] * sup[R - 1] / gamma;
+        rsub[0] = 0.0;
+    }
+    for (int i = 0; i < R; ++i) {
+        const double den = diag[i] - (i > 0 ? rsub[i] * cp[i - 1] : 0.0);
+        if (den == 0.0 || !std::isfinite(den)) return TDS_ERR_ARG;
+        wf[i] = 1.0 / den;
+        cp[i] = (i < R - 1) ? wf[i] * sup[i] : 0.0;
+    }
+    if (periodic) {
+        std::vector<double> u(R, 0.0);
+        u[0] = gamma; u[R - 1] += sup[R - 1];
+        for (int i = 0; i < R; ++i) q[i] = wf[i] * (u[i] - (i > 0 ? rsub[i] * q[i - 1] : 0.0));
+        for (int i = R - 2; i >= 0; --i) q[i] -= cp[i] * q[i + 1];
+        op.red_vlast = sub[0] / gamma;
+        const double den = 1.0 + q[0] + op.red_vlast * q[R - 1];
+        if (den == 0.0 || !std::isfinite(den)) return TDS_ERR_ARG;
+        op.red_den_inv = 1.0 / den;
+    }
+    return TDS_OK;
+}
+
+tds_status build_plan(tds_plan *p) {
+    const bool periodic = (p->bc == TDS_BC_PERIODIC);
+    LineOperator L, LT;
+    scheme_line(p->n, p->order, periodic, p->h, L);
+    transpose_line(p->n, periodic, L, LT);
+
+    std::vector<double> rows[2], n1s[2], red[2], sub[2], sup[2];
+    for (int w = 0; w < 2; ++w) {
+        tds_status s = build_operator(p, w ? LT : L, w, p->op[w], rows[w], n1s[w], red[w],
+                                      sub[w], sup[w]);
+        if (s != TDS_OK) return s;
+    }
+
+    // one device allocation: [rows64 | rows32 | n1 | red] per operator, 256-byte aligned parts
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off[2][4], total = 0;
+    for (int w = 0; w < 2; ++w) {
+        off[w][0] = total; total = align(total + rows[w].size() * sizeof(double));
+        off[w][1] = total; total = align(total + rows[w].size() * sizeof(float));
+        off[w][2] = total; total = align(total + n1s[w].size() * sizeof(double));
+        off[w][3] = total; total = align(total + red[w].size() * sizeof(double));
+    }
+    std::vector<unsigned char> host(total, 0);
+    for (int w = 0; w < 2; ++w) {
+        std::memcpy(&host[off[w][0]], rows[w].data(), rows[w].size() * sizeof(double));
+        float *r32 = reinterpret_cast<float *>(&host[off[w][1]]);
+        for (size_t i = 0; i < rows[w].size(); ++i) r32[i] = (float)rows[w][i];
+        std::memcpy(&host[off[w][2]], n1s[w].data(), n1s[w].size() * sizeof(double));
+        std::memcpy(&host[off[w][3]], red[w].data(), red[w].size() * sizeof(double));
+    }
+    void *d = nullptr;
+    const cudaError_t e = cudaMalloc(&d, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? TDS_ERR_NOMEM : TDS_ERR_CUDA;
+    }
+    if (cudaMemcpy(d, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return TDS_ERR_CUDA;
+    }
+    p->dmem = d;
+    unsigned char *base = static_cast<unsigned char *>(d);
+    const int R = 2 * p->P;
+    double *hm = static_cast<double *>(std::malloc(sizeof(double) * 4 * R));
+    if (!hm) { cudaFree(d); p->dmem = nullptr; return TDS_ERR_NOMEM; }
+    p->hmem = hm;
+    for (int w = 0; w < 2; ++w) {
+        p->op[w].row64 = reinterpret_cast<const double *>(base + off[w][0]);
+        p->op[w].row32 = reinterpret_cast<const float *>(base + off[w][1]);
+        p->op[w].n1 = reinterpret_cast<const double *>(base + off[w][2]);
+        p->op[w].red = reinterpret_cast<const double *>(base + off[w][3]);
+        p->red_sub_host[w] = hm + (size_t)(2 * w) * R;
+        p->red_sup_host[w] = hm + (size_t)(2 * w + 1) * R;
+        std::memcpy(p->red_sub_host[w], sub[w].data(), sizeof(double) * R);
+        std::memcpy(p->red_sup_host[w], sup[w].data(), sizeof(double) * R);
+    }
+    return TDS_OK;
+}
+
+} // namespace tds

@@ -1,0 +1,100 @@
+// tds_reorder.cu -- permutations between the Cartesian layout and the direction layouts of
+// the interleaved group data structure (Sec. 4.1: the layout is specific to the derivative
+// direction and data is reordered when the direction changes; Table transport counts these
+// reorders as one read and one write per point).
+//
+// With nx and ny multiples of 32, every 32-element row of the Cartesian, y and z layouts is a
+// run of 32 consecutive x at fixed (y, z), and every row of the x layout is a run of 32
+// consecutive y at fixed (x, z).  So:
+//   Cartesian <-> y <-> z        : a permutation of whole rows (both sides coalesced);
+//   x <-> {Cartesian, y, z}      : a 32 x 32 (x, y) tile transpose through shared memory.
+#include "tds_internal.h"
+
+namespace tds {
+namespace {
+
+constexpr int R = kSZ;  // row length
+
+// Offset of the row holding x = 32*xb .. 32*xb+31 at (y, z) in a layout whose rows run in x.
+__device__ __forceinline__ size_t xrun_row(tds_layout L, int xb, int y, int z, int nx, int ny,
+                                           int nz) {
+    const size_t xg = (size_t)nx / R;
+    switch (L) {
+    case TDS_LAYOUT_CART: return (size_t)xb * R + (size_t)nx * ((size_t)y + (size_t)ny * z);
+    case TDS_LAYOUT_Y: return (size_t)R * ((size_t)y + (size_t)ny * ((size_t)xb + xg * z));
+    default: /* Z */ return (size_t)R * ((size_t)z + (size_t)nz * ((size_t)xb + xg * y));
+    }
+}
+
+// Offset of the x-layout row holding y = 32*yb .. 32*yb+31 at (x, z).
+__device__ __forceinline__ size_t xlayout_row(int x, int yb, int z, int nx, int ny) {
+    const size_t yg = (size_t)ny / R;
+    return (size_t)R * ((size_t)x + (size_t)nx * ((size_t)yb + yg * z));
+}
+
+// Row permutation between two x-run layouts: one warp per row; grid (ceil(nx/32/8), ny, nz).
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows(const T *__restrict__ in, T *__restrict__ out, int nx,
+                                             int ny, int nz, tds_layout from, tds_layout to) {
+    const int xb = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (xb >= nx / R) return;
+    const int y = blockIdx.y, z = blockIdx.z, t = threadIdx.x & 31;
+    out[xrun_row(to, xb, y, z, nx, ny, nz) + t] = __ldg(in + xrun_row(from, xb, y, z, nx, ny, nz) + t);
+}
+
+// 32 x 32 (x, y) tile transpose between the x layout and an x-run layout at fixed z.
+// grid (nx/32, ny/32, nz), block (32, 8).  to_x selects the direction.
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose(const T *__restrict__ in, T *__restrict__ out,
+                                                  int nx, int ny, int nz, tds_layout other,
+                                                  int to_x) {
+    __shared__ T tile[R][R + 1];
+    const int xb = blockIdx.x, yb = blockIdx.y, z = blockIdx.z;
+    const int t = threadIdx.x, r0 = threadIdx.y;
+    if (to_x) {
+        // read rows y = 32 yb + i of the x-run layout: element t is x = 32 xb + t
+        for (int i = r0; i < R; i += 8)
+            tile[i][t] = __ldg(in + xrun_row(other, xb, yb * R + i, z, nx, ny, nz) + t);
+        __syncthreads();
+        // write rows x = 32 xb + i of the x layout: element t is y = 32 yb + t
+        for (int i = r0; i < R; i += 8)
+            out[xlayout_row(xb * R + i, yb, z, nx, ny) + t] = tile[t][i];
+    } else {
+        for (int i = r0; i < R; i += 8)
+            tile[i][t] = __ldg(in + xlayout_row(xb * R + i, yb, z, nx, ny) + t);
+        __syncthreads();
+        for (int i = r0; i < R; i += 8)
+            out[xrun_row(other, xb, yb * R + i, z, nx, ny, nz) + t] = tile[t][i];
+    }
+}
+
+template <typename T>
+tds_status launch_t(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
+                    tds_layout to, cudaStream_t st) {
+    const T *src = static_cast<const T *>(in);
+    T *dst = static_cast<T *>(out);
+    if (from != TDS_LAYOUT_X && to != TDS_LAYOUT_X) {
+        dim3 grid((unsigned)((nx / R + 7) / 8), (unsigned)ny, (unsigned)nz);
+        k_rows<T><<<grid, 256, 0, st>>>(src, dst, nx, ny, nz, from, to);
+    } else {
+        dim3 grid((unsigned)(nx / R), (unsigned)(ny / R), (unsigned)nz);
+        const int to_x = (to == TDS_LAYOUT_X);
+        k_transpose<T><<<grid, dim3(32, 8), 0, st>>>(src, dst, nx, ny, nz, to_x ? from : to, to_x);
+    }
+    return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
+}
+
+} // namespace
+
+tds_status launch_reorder(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
+                          tds_layout to, size_t elem, cudaStream_t st) {
+    if (from == to) {
+        const size_t bytes = (size_t)nx * ny * nz * elem;
+        return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                   ? TDS_OK : TDS_ERR_CUDA;
+    }
+    return elem == 8 ? launch_t<double>(in, out, nx, ny, nz, from, to, st)
+                     : launch_t<float>(in, out, nx, ny, nz, from, to, st);
+}
+
+} // namespace tds

@@ -1,0 +1,301 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Small grids: every output compared with the oracle, over dtype x variant x direction x order
+x boundary x P, sized to span several groups and chunks with a ragged group count.
+Full sizes (the workloads of the benchmark): sampled whole lines compared one by one with
+the oracle.  Bars: max|d|/max|ref| <= 1e-12 (FP64) and <= 1e-5 (FP32, against the oracle
+on the FP32-rounded input)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2411_13532_gb300 import inputs
+from tests.gpu_util import (TOL, TORCH, from_device_layout, gather_lines, rel_errors,
+                            sample_lines, to_device_layout)
+
+pytestmark = pytest.mark.gpu
+
+tds = pytest.importorskip("paper_2411_13532_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2411_13532_gb300 import build
+    build.build()
+    oracle.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    yield
+    assert tds.device_status() == 0
+
+
+SMALL = (12, 40, 32)   # (nz, ny, nx): x lines 480 (15 groups), y lines 384, z lines 1280
+PS = {"x": [1, 2, 8], "y": [1, 2, 5], "z": [1, 3]}
+
+
+def small_case(direction, order, bc, P, dtype, variant, adjoint, seed):
+    cart = np.random.default_rng(seed).uniform(-1, 1, SMALL)
+    if dtype == "f32":
+        cart = cart.astype(np.float32).astype(np.float64)
+    n = {"x": SMALL[2], "y": SMALL[1], "z": SMALL[0]}[direction]
+    h = oracle.grid_spacing(n, bc)
+    plan = tds.Plan(SMALL, direction, order, bc, P=P, h=h, dtype=TORCH[dtype], variant=variant)
+    x = to_device_layout(cart, direction, dtype)
+    y = plan.adjoint(x) if adjoint else plan.deriv(x)
+    torch.cuda.synchronize()
+    got = from_device_layout(y, direction, SMALL)
+    ref = (oracle.deriv_adjoint if adjoint else oracle.deriv)(cart, direction, order, bc, h)
+    return rel_errors(got, ref)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("variant", ["resident", "streaming"])
+@pytest.mark.parametrize("direction", ["x", "y", "z"])
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_small_grid_every_point(dtype, variant, direction, order, bc, adjoint):
+    for i, P in enumerate(PS[direction]):
+        mx, rms = small_case(direction, order, bc, P, dtype, variant, adjoint, seed=11 + i)
+        assert mx <= TOL[dtype], (P, mx, rms)
+
+
+@pytest.mark.parametrize("variant", ["resident", "streaming"])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+def test_minimum_chunk_and_line(variant, bc):
+    """n = 8 (the smallest line) and m = 4 (the smallest chunk)."""
+    shape = (1, 32, 8)
+    cart = np.random.default_rng(5).uniform(-1, 1, shape)
+    for P in (1, 2):
+        for order in (1, 2):
+            h = oracle.grid_spacing(8, bc)
+            plan = tds.Plan(shape, "x", order, bc, P=P, h=h, variant=variant)
+            y = plan.deriv(to_device_layout(cart, "x", "f64"))
+            got = from_device_layout(y, "x", shape)
+            mx, _ = rel_errors(got, oracle.deriv(cart, "x", order, bc, h))
+            assert mx <= 1e-12, (P, order, mx)
+
+
+@pytest.mark.parametrize("variant", ["resident", "streaming"])
+def test_p_invariance(variant):
+    """Chunking does not change the result (order-of-accuracy study of Sec. 4.2: the
+    partitioned solver matches the single-rank solver)."""
+    shape = (2, 16, 256)
+    cart = np.random.default_rng(9).uniform(-1, 1, shape)
+    x = to_device_layout(cart, "x", "f64")
+    for bc in ("periodic", "closed"):
+        base = tds.Plan(shape, "x", 1, bc, P=1, variant=variant).deriv(x)
+        for P in (2, 4, 8, 16, 32, 64):
+            if variant == "resident" and P > 16:
+                continue
+            y = tds.Plan(shape, "x", 1, bc, P=P, variant=variant).deriv(x)
+            mx, _ = rel_errors(y.cpu().numpy(), base.cpu().numpy())
+            assert mx <= 1e-13, (bc, P, mx)
+
+
+def test_resident_and_streaming_agree():
+    shape = (4, 8, 128)
+    cart = np.random.default_rng(2).uniform(-1, 1, shape)
+    x = to_device_layout(cart, "x", "f64")
+    for order in (1, 2):
+        a = tds.Plan(shape, "x", order, "closed", P=4, variant="resident").deriv(x)
+        b = tds.Plan(shape, "x", order, "closed", P=4, variant="streaming").deriv(x)
+        mx, _ = rel_errors(a.cpu().numpy(), b.cpu().numpy())
+        assert mx <= 1e-14
+
+
+def test_bitwise_deterministic():
+    shape = (4, 8, 256)
+    x = to_device_layout(np.random.default_rng(3).uniform(-1, 1, shape), "x", "f64")
+    for variant in ("resident", "streaming"):
+        plan = tds.Plan(shape, "x", 2, "periodic", P=4, variant=variant)
+        a = plan.deriv(x); b = plan.deriv(x)
+        assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("m", [8, 16, 32])
+def test_paper_drop_mode_error_bound(m):
+    """Dropping the two couplings per chunk (Fig. alg) costs O(|lambda|^m), lambda the
+    decay ratio of A^{-1} (0.382 for alpha = 1/3)."""
+    P = 4; n = P * m
+    shape = (1, 32, n)
+    cart = np.random.default_rng(m).uniform(-1, 1, shape)
+    lam = (1 - math.sqrt(1 - 4 / 9)) / (2 / 3)
+    for variant in ("resident", "streaming"):
+        y = tds.Plan(shape, "x", 1, "periodic", P=P, mode="paper_drop", variant=variant).deriv(
+            to_device_layout(cart, "x", "f64"))
+        mx, _ = rel_errors(from_device_layout(y, "x", shape), oracle.deriv(cart, "x", 1, "periodic"))
+        assert mx <= 8 * lam ** m + 1e-13, (variant, mx, lam ** m)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+@pytest.mark.parametrize("P", [1, 3, 8])
+def test_reduced_system_against_dense_solve(bc, P):
+    shape = (1, 32, 8 * P)
+    plan = tds.Plan(shape, "x", 1, bc, P=P)
+    sub, sup = plan.reduced_coeffs()
+    R = 2 * P
+    M = np.eye(R)
+    for i in range(R):
+        if i > 0: M[i, i - 1] += sub[i]
+        elif bc == "periodic": M[i, R - 1] += sub[i]
+        if i < R - 1: M[i, i + 1] += sup[i]
+        elif bc == "periodic": M[i, 0] += sup[i]
+    rhs = np.random.default_rng(P).normal(size=(plan.nlines, R))
+    x = plan.reduced_solve(torch.from_numpy(rhs).cuda()).cpu().numpy()
+    ref = np.linalg.solve(M, rhs.T).T
+    assert np.max(np.abs(x - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_argument_errors_on_device():
+    shape = (1, 32, 64)
+    plan = tds.Plan(shape, "x", 1, "periodic", P=2, variant="streaming")
+    x = torch.zeros(plan.numel, dtype=torch.float64, device="cuda")
+    with pytest.raises(tds.TdsError) as e:
+        plan.deriv(x, out=x)
+    assert e.value.status == 3  # alias
+    with pytest.raises(tds.TdsError) as e:
+        plan.deriv(x, ws=torch.empty(plan.ws_bytes // 2, dtype=torch.uint8, device="cuda"))
+    assert e.value.status == 4  # workspace too small
+    buf = torch.zeros(plan.numel + 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(tds.TdsError) as e:
+        plan.deriv(buf[1:])
+    assert e.value.status == 1  # misaligned
+
+
+# ------------------------------------------------------------------------------ reorders
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_reorder_bitwise(dtype):
+    shape = (3, 64, 96)
+    cart = np.random.default_rng(4).uniform(-1, 1, shape)
+    t = torch.from_numpy(cart.reshape(-1).copy()).cuda().to(TORCH[dtype])
+    ref_cart = t.cpu().double().numpy().reshape(shape)
+    lay = {"cart": t}
+    for d in "xyz":
+        lay[d] = tds.reorder(t, shape, "cart", d)
+        want = oracle.to_layout(ref_cart, d, 32)
+        assert np.array_equal(lay[d].cpu().double().numpy(), want), d
+    for a in lay:
+        for b in lay:
+            got = tds.reorder(lay[a], shape, a, b)
+            assert torch.equal(got, lay[b]), (a, b)
+    # round trip x -> y -> z -> x
+    rt = tds.reorder(tds.reorder(tds.reorder(lay["x"], shape, "x", "y"), shape, "y", "z"), shape, "z", "x")
+    assert torch.equal(rt, lay["x"])
+
+
+# --------------------------------------------------------------------- full-size workloads
+
+def sampled_check(field_cart_dev, shape, direction, order, bc, P, dtype, adjoint=False,
+                  nsample=48, seed=0, fp64_input=None):
+    """Reorder the device field to the direction layout, run the plan, compare sampled lines
+    with the oracle.  Returns (max-rel, rms-rel) against the oracle on the same input."""
+    t = field_cart_dev.to(TORCH[dtype])
+    x = tds.reorder(t, shape, "cart", direction)
+    del t
+    n = {"x": shape[2], "y": shape[1], "z": shape[0]}[direction]
+    h = oracle.grid_spacing(n, bc)
+    plan = tds.Plan(shape, direction, order, bc, P=P, h=h, dtype=TORCH[dtype])
+    y = plan.adjoint(x) if adjoint else plan.deriv(x)
+    lines = sample_lines(plan.nlines, nsample, seed)
+    fin = gather_lines(x, direction, shape, lines).double().cpu().numpy()
+    fout = gather_lines(y, direction, shape, lines).double().cpu().numpy()
+    del x, y
+    ref = (oracle.deriv_adjoint_lines if adjoint else oracle.deriv_lines)(fin, order, bc, h)
+    return rel_errors(fout, ref)
+
+
+def test_config_64cubed_fourier_x_periodic_p1():
+    shape = (64, 64, 64)
+    f, _ = inputs.fourier_field(shape, seed=0, kmax=20, noise=1e-3, device="cuda")
+    cart = f.cpu().numpy()
+    x = tds.reorder(f, shape, "cart", "x")
+    y = tds.Plan(shape, "x", 1, "periodic", P=1).deriv(x)
+    got = from_device_layout(y, "x", shape)
+    mx, rms = rel_errors(got, oracle.deriv(cart, "x", 1, "periodic"))
+    assert mx <= 1e-12, (mx, rms)
+
+
+@pytest.mark.parametrize("direction", ["x", "y", "z"])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+def test_config_256cubed_orders_dirs_bcs_p1_p4(direction, bc):
+    shape = (256, 256, 256)
+    f = inputs.uniform_field(shape, seed=1, device="cuda")
+    for order in (1, 2):
+        for P in (1, 4):
+            mx, rms = sampled_check(f, shape, direction, order, bc, P, "f64", seed=order * 10 + P)
+            assert mx <= 1e-12, (order, P, mx, rms)
+
+
+@pytest.mark.parametrize("direction", ["x", "y", "z"])
+def test_config_512cubed_fp32_vs_fp64(direction):
+    shape = (512, 512, 512)
+    f, _ = inputs.fourier_field(shape, seed=2, kmax=100, noise=0.1, noise_kind="normal",
+                                device="cuda")
+    for order in (1, 2):
+        mx, rms = sampled_check(f, shape, direction, order, "periodic", 8, "f64", nsample=24)
+        assert mx <= 1e-12, ("f64", order, mx, rms)
+        mx, rms = sampled_check(f, shape, direction, order, "periodic", 8, "f32", nsample=24)
+        assert mx <= 1e-5, ("f32", order, mx, rms)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_config_256cubed_adjoint_z_closed_p4(dtype):
+    shape = (256, 256, 256)
+    g = inputs.normal_field(shape, seed=3, device="cuda")
+    mx, rms = sampled_check(g, shape, "z", 1, "closed", 4, dtype, adjoint=True)
+    assert mx <= TOL[dtype], (mx, rms)
+
+
+def test_config_1d_batch_long_lines_p64():
+    shape = (1, 256, 262144)
+    f = inputs.uniform_field(shape, seed=5, device="cuda")
+    mx, rms = sampled_check(f, shape, "x", 1, "periodic", 64, "f64", nsample=6)
+    assert mx <= 1e-12, (mx, rms)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("P", [8, 2])
+def test_config_1024cubed_three_directions(P):
+    shape = (1024, 1024, 1024)
+    f = inputs.uniform_field(shape, seed=4, device="cuda")
+    for direction in "xyz":
+        mx, rms = sampled_check(f, shape, direction, 1, "periodic", P, "f64", nsample=16)
+        assert mx <= 1e-12, (direction, mx, rms)
+    del f
+    torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------------------- adjoint / autograd
+
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_adjoint_dot_product_on_device(bc, dtype):
+    shape = (8, 16, 64)
+    plan = tds.Plan(shape, "x", 1, bc, P=4, dtype=TORCH[dtype])
+    f = inputs.uniform_field(shape, seed=7, device="cuda", dtype=TORCH[dtype]).reshape(-1)
+    g = inputs.normal_field(shape, seed=8, device="cuda", dtype=TORCH[dtype]).reshape(-1)
+    lhs = torch.dot(plan.deriv(f).double(), g.double())
+    rhs = torch.dot(f.double(), plan.adjoint(g).double())
+    scale = torch.sum(torch.abs(plan.deriv(f).double() * g.double()))
+    assert abs(float(lhs - rhs)) <= (1e-13 if dtype == "f64" else 1e-5) * float(scale)
+
+
+def test_gradcheck_small_full_jacobian():
+    shape = (8, 4, 8)   # z lines: 32, n = 8
+    plan = tds.Plan(shape, "z", 1, "closed", P=2)
+    x = torch.randn(plan.numel, dtype=torch.float64, device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda v: tds.compact_deriv(v, plan), (x,), eps=1e-6,
+                                    atol=1e-8, rtol=1e-6)
+
+
+def test_gradcheck_32cubed_fast_mode():
+    shape = (32, 32, 32)
+    plan = tds.Plan(shape, "z", 1, "closed", P=4)
+    x = torch.randn(plan.numel, dtype=torch.float64, device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda v: tds.compact_deriv(v, plan), (x,), eps=1e-6,
+                                    atol=1e-7, rtol=1e-6, fast_mode=True)
