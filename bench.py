@@ -155,7 +155,7 @@ def run_ours(args, rank, world, local_rank):
     dtypes = [("f64", torch.float64), ("f32", torch.float32)]
     data = {}
     for name, dt in dtypes:
-        cart = f.to(dt)
+        cart = f.to(dt).reshape(-1)
         ux = tds.reorder(cart, shape, "cart", "x")
         del cart
         d = {"ux": ux, "uy": torch.empty_like(ux), "uz": torch.empty_like(ux),
