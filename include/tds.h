@@ -181,6 +181,31 @@ TDS_API tds_status tds_plan_reduced_coeffs(const tds_plan *plan, double *host_su
  */
 TDS_API tds_status tds_reduced_solve(const tds_plan *plan, const double *rhs, double *x, void *stream);
 
+/* Size of the scratch array built into the library for tds_deriv_noalloc (16 MiB). */
+#define TDS_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/*
+ * tds_deriv_noalloc -- tds_deriv for callers that cannot allocate device memory (no
+ * counterpart in the paper).  Some callers cannot call cudaMalloc or an allocator at all: a
+ * host application that owns every device buffer, a real-time loop that must never allocate,
+ * or a plugin that may only touch the buffers it is given.  They cannot supply tds_deriv's
+ * workspace, so this call takes its scratch from an array of TDS_NOALLOC_SCRATCH_BYTES
+ * compiled into the library (held on every GPU that loads the library until the process
+ * exits) and allocates nothing.
+ *   plan    : an existing plan (created beforehand; plan creation itself allocates).
+ *   in, out : as in tds_deriv (device, 16-byte aligned, non-overlapping: TDS_ERR_ALIAS).
+ * Always runs the three-kernel streaming pipeline.  Its chunk ends need 16*N*P bytes; a plan
+ * needing more than TDS_NOALLOC_SCRATCH_BYTES (N*P > 1,048,576 lines x chunks) is rejected
+ * with TDS_ERR_WORKSPACE before any launch.
+ * The first call on each device looks up the array's device address with that device
+ * current (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  All calls share the one array, which keeps the last call's contents (nothing in
+ * it needs to start at zero): calls that overlap on the GPU -- concurrent streams, or
+ * several host threads -- race on it and must be serialised by the caller.
+ */
+TDS_API tds_status tds_deriv_noalloc(const tds_plan *plan, const void *in, void *out,
+                                     void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -131,6 +131,18 @@ class Plan:
                 _stream_ptr(stream, self.device)), "tds_deriv_host")
         return host_out
 
+    def deriv_noalloc(self, x, out, stream=None):
+        """``tds_deriv_noalloc``: like ``deriv`` but with the library's built-in scratch instead
+        of a caller workspace (for callers that cannot allocate; ``out`` must be given)."""
+        _check_tensor(x, self.dtype, self.numel, "input")
+        _check_tensor(out, self.dtype, self.numel, "out")
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.lib().tds_deriv_noalloc(self._handle, ctypes.c_void_p(x.data_ptr()),
+                                                    ctypes.c_void_p(out.data_ptr()),
+                                                    _stream_ptr(stream, self.device)),
+                       "tds_deriv_noalloc")
+        return out
+
     def reduced_coeffs(self):
         """(sub, sup) of the reduced chunk-end system, 2P doubles each."""
         R = 2 * self.P

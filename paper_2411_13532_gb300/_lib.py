@@ -33,6 +33,7 @@ SIGNATURES = [
     ("tds_device_status", _i, []),
     ("tds_plan_reduced_coeffs", _i, [_vp, _vp, _vp]),
     ("tds_reduced_solve", _i, [_vp, _vp, _vp, _vp]),
+    ("tds_deriv_noalloc", _i, [_vp, _vp, _vp, _vp]),
 ]
 
 _lib = None

@@ -1,0 +1,64 @@
+// tds_noalloc.cu -- tds_deriv_noalloc: the derivative for callers that cannot allocate device
+// memory, for example code running where cudaMalloc is not available or not allowed (a host
+// that hands out only pre-registered buffers, a real-time loop that must never allocate, a
+// plugin whose host application owns all device memory).  Such callers cannot provide the
+// workspace that tds_deriv's streaming pipeline needs for the chunk ends, so this entry point
+// takes that scratch from a fixed array compiled into the library instead.
+#include <mutex>
+
+#include "tds_internal.h"
+
+namespace {
+
+// Scratch for the chunk ends (FP64, 16 bytes per line and chunk) of the streaming pipeline.
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TDS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 256;
+void *g_scratch_addr[kMaxDevices];   // device address of the array, per device, set once
+std::mutex g_scratch_mutex;
+
+// Address of the scratch array on the current device.  In host code the array's name is only
+// a host-side stand-in, so the device address is looked up once per device with that device
+// current, and cached.
+tds_status scratch_on_current_device(void **addr) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return TDS_ERR_CUDA; }
+    if (dev < 0 || dev >= kMaxDevices) return TDS_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return TDS_ERR_CUDA;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *addr = g_scratch_addr[dev];
+    return TDS_OK;
+}
+
+bool overlap(const void *a, const void *b, size_t bytes) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + bytes && y < x + bytes;
+}
+
+} // namespace
+
+extern "C" TDS_API tds_status tds_deriv_noalloc(const tds_plan *plan, const void *in, void *out,
+                                                void *stream) {
+    if (!plan || !in || !out) return TDS_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+        return TDS_ERR_ARG;
+    const size_t bytes = (size_t)plan->n * plan->nlines * (plan->dtype == TDS_F64 ? 8 : 4);
+    if (overlap(in, out, bytes)) return TDS_ERR_ALIAS;
+    // chunk ends of the forward streaming pipeline: 2 FP64 values per line and chunk
+    const size_t need = (size_t)plan->nlines * plan->P * 2 * sizeof(double);
+    if (need > (size_t)TDS_NOALLOC_SCRATCH_BYTES) return TDS_ERR_WORKSPACE;
+    void *scratch = nullptr;
+    const tds_status s = scratch_on_current_device(&scratch);
+    if (s != TDS_OK) return s;
+    // every scratch entry the pipeline reads is written earlier in the same call: nothing needs
+    // to start at zero
+    return tds::launch_streaming(plan, 0, in, out, scratch, static_cast<cudaStream_t>(stream));
+}
