@@ -197,7 +197,7 @@ def run_ours(args, rank, world, local_rank):
                         timed((name, key, p1.variant if key != "d2" else p2.variant), fn)
                     else:
                         fn()
-                    launches[0] += 1 if p1.variant == "resident" else 3
+                    launches[0] += 3 if p1.variant == "streaming" else 1
                 if nxt is not None:
                     rfn = (lambda s=src, t=d[nxt], a=direc, b={"uy": "y", "uz": "z"}[nxt]:
                            tds.reorder(s, shape, a, b, out=t))

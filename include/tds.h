@@ -63,7 +63,9 @@ typedef enum { TDS_REDUCED_EXACT = 0, TDS_REDUCED_PAPER_DROP = 1 } tds_reduced;
 typedef enum {
     TDS_VARIANT_AUTO = 0,
     TDS_VARIANT_RESIDENT = 1,   /* one CTA holds a whole group of SZ lines on chip          */
-    TDS_VARIANT_STREAMING = 2   /* decouple / reduced / substitute as three kernels         */
+    TDS_VARIANT_STREAMING = 2,  /* decouple / reduced / substitute as three kernels         */
+    TDS_VARIANT_PIPELINED = 3   /* persistent CTAs, each sweeping many groups through
+                                   several on-chip tile buffers filled ahead by TMA         */
 } tds_variant;
 
 typedef struct tds_plan tds_plan;
@@ -97,7 +99,8 @@ TDS_API tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_d
 
 /* Choose the kernel pipeline of a plan (tuning and test hook; call before first use, not
  * concurrently with a call that uses the plan).  TDS_ERR_ARG if the plan cannot run the
- * requested variant (a resident group larger than one CTA's shared memory). */
+ * requested variant (a resident group larger than one CTA's shared memory).  AUTO picks
+ * RESIDENT when a group fits in one CTA, else STREAMING. */
 TDS_API tds_status tds_plan_set_variant(tds_plan *plan, tds_variant variant);
 
 /* Describe a plan: line length n, lines N, chunks P, the variant it will run, and the

@@ -39,6 +39,7 @@ tds_status run(const tds_plan *p, int which, const void *in, void *out, void *ws
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (p->variant == TDS_VARIANT_RESIDENT) return launch_resident(p, which, in, out, st);
+    if (p->variant == TDS_VARIANT_PIPELINED) return launch_pipelined(p, which, in, out, st);
     return launch_streaming(p, which, in, out, ws, st);
 }
 
@@ -93,7 +94,31 @@ tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_dir dir, 
     }
     const size_t smem = resident_smem_bytes(n, P, dtype);
     p->resident_smem = (P <= kMaxResidentP && smem <= (size_t)optin) ? (int)smem : 0;
-    p->variant = p->resident_smem ? TDS_VARIANT_RESIDENT : TDS_VARIANT_STREAMING;
+    // persistent pipelined kernel: as many tile buffers (up to 4) as one CTA can hold, and as
+    // many such CTAs as fit on every SM
+    int smem_sm = 0, nsm = 0;
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        tds_plan_destroy(p);
+        return TDS_ERR_CUDA;
+    }
+    p->pipe_nbuf = 0;
+    if (p->resident_smem) {
+        for (int nb = 4; nb >= 1; --nb)
+            if (pipe_smem_bytes(n, P, dtype, nb) <= (size_t)optin) { p->pipe_nbuf = nb; break; }
+        if (p->pipe_nbuf) {
+            const size_t per = pipe_smem_bytes(n, P, dtype, p->pipe_nbuf);
+            const int ctas = (int)((size_t)smem_sm / (per + 1024));
+            p->pipe_grid = nsm * (ctas > 0 ? ctas : 1);
+        }
+    }
+    // lines per thread in the resident kernels; TDS_RESIDENT_LANES overrides (tuning)
+    p->lanes = (dtype == TDS_F32) ? 4 : 1;
+    if (const char *e = std::getenv("TDS_RESIDENT_LANES")) {
+        const int v = std::atoi(e);
+        if (v == 1 || v == 2 || (v == 4 && dtype == TDS_F32)) p->lanes = v;
+    }
+    tds_plan_set_variant(p, TDS_VARIANT_AUTO);
     *out = p;
     return TDS_OK;
 }
@@ -102,7 +127,9 @@ tds_status tds_plan_set_variant(tds_plan *p, tds_variant v) {
     if (!p) return TDS_ERR_ARG;
     if (v == TDS_VARIANT_AUTO) v = p->resident_smem ? TDS_VARIANT_RESIDENT : TDS_VARIANT_STREAMING;
     if (v == TDS_VARIANT_RESIDENT && !p->resident_smem) return TDS_ERR_ARG;
-    if (v != TDS_VARIANT_RESIDENT && v != TDS_VARIANT_STREAMING) return TDS_ERR_ARG;
+    if (v == TDS_VARIANT_PIPELINED && !p->pipe_nbuf) return TDS_ERR_ARG;
+    if (v != TDS_VARIANT_RESIDENT && v != TDS_VARIANT_STREAMING && v != TDS_VARIANT_PIPELINED)
+        return TDS_ERR_ARG;
     p->variant = v;
     return TDS_OK;
 }
@@ -113,7 +140,10 @@ tds_status tds_plan_info(const tds_plan *p, int *n, int *nlines, int *P, int *va
     if (nlines) *nlines = p->nlines;
     if (P) *P = p->P;
     if (variant) *variant = (int)p->variant;
-    if (smem) *smem = p->variant == TDS_VARIANT_RESIDENT ? p->resident_smem : 0;
+    if (smem)
+        *smem = p->variant == TDS_VARIANT_RESIDENT ? p->resident_smem
+              : p->variant == TDS_VARIANT_PIPELINED ? (int)pipe_smem_bytes(p->n, p->P, p->dtype, p->pipe_nbuf)
+              : 0;
     return TDS_OK;
 }
 

@@ -24,8 +24,15 @@ constexpr int kMaxResidentP = 16; // resident kernel: one warp per chunk, at mos
 enum { kF = 0, kR = 1, kW = 2, kSA = 3, kSC = 4, kNumRowArrays = 5 };
 
 // Reduced-system arrays (2P entries each): sub-diagonal, forward factor, backward multiplier
-// of the (Sherman-Morrison-modified if cyclic) tridiagonal factorisation, and q = T'^{-1} u.
-enum { kRedSub = 0, kRedWf = 1, kRedCp = 2, kRedQ = 3, kNumRedArrays = 4 };
+// of the (Sherman-Morrison-modified if cyclic) tridiagonal factorisation, q = T'^{-1} u; and,
+// for the decoupled form, per chunk boundary k (between chunk k-1 and k, cyclically) the
+// coupling a_k of F_k to L_{k-1}, c_k of L_{k-1} to F_k, and 1/(1 - a_k c_k).
+enum { kRedSub = 0, kRedWf = 1, kRedCp = 2, kRedQ = 3, kRedBa = 4, kRedBc = 5, kRedBinv = 6,
+       kNumRedArrays = 7 };
+
+// The decoupled form is used when every coupling it ignores is below this magnitude
+// (relative to the unit diagonal): the solution then agrees with the full solve to rounding.
+constexpr double kDecoupleTol = 5.421010862427522e-20;   // 2^-64
 
 // Operator descriptor passed by value to every kernel.
 struct DevOp {
@@ -37,9 +44,20 @@ struct DevOp {
     int cls_first, cls_mid, cls_last;
     const double *row64;  // [kNumRowArrays][ncls*m]
     const float *row32;   // the same arrays rounded to float (FP32 sweeps)
+    // Row records of the resident sweep, [ncls][m] each, FP64 and FP32 copies:
+    //   fwd = {f_j, r_j, pi_j, 0}: forward factor, sub-diagonal, and the weight of the forward
+    //         value d_j in the back-swept row 1 (pi_1 = 1, pi_j = -pi_{j-1} s^c_{j-1}, 0 at
+    //         rows 0 and m-1), so that row 1 after the backward pass is sum_j pi_j d_j;
+    //   bwd = {s^a_j, s^c_j} after the forward pass only (coupling to the chunk's first unknown
+    //         and to the next row), for the back-substitution u_j = d_j - s^a_j F - s^c_j u_{j+1}.
+    const double *fwd64;
+    const float *fwd32;
+    const double *bwd64;
+    const float *bwd32;
     const double *n1;     // [ncls] row-0 normaliser 1/(1 - s^c_1 s^a_2) (Algorithm 4, last lines)
     const double *red;    // [kNumRedArrays][2P]
     int red_cyclic;
+    int red_decoupled;    // 1: the 2P system splits into P independent 2x2 boundary systems
     double red_vlast;     // last entry of the Sherman-Morrison v vector
     double red_den_inv;   // 1/(1 + v.q)
     double tap[kTaps];                 // interior stencil taps, offsets -3..3
@@ -58,8 +76,11 @@ struct tds_plan {
     tds_dtype dtype;
     tds_reduced mode;
     int n, m, nlines;
-    tds_variant variant;   // resolved: RESIDENT or STREAMING
+    tds_variant variant;   // resolved: RESIDENT, PIPELINED or STREAMING
     int resident_smem;     // dynamic shared memory of the resident kernel (0 = cannot run)
+    int pipe_nbuf;         // > 0: run the persistent multi-buffered resident kernel
+    int pipe_grid;         // its grid (resident CTAs the device holds at once)
+    int lanes;             // lines per thread in the resident kernels (FP32: 1, 2, 4; FP64: 1, 2)
     tds::DevOp op[2];      // [0] = A^{-1} B, [1] = B^T A^{-T}
     double *red_sub_host[2], *red_sup_host[2];
     void *dmem;            // one device allocation holding every array of both operators
@@ -73,8 +94,11 @@ tds_status build_plan(tds_plan *p);
 
 // Kernel launchers (tds_kernels.cu).  Each returns TDS_ERR_CUDA on a launch failure.
 size_t resident_smem_bytes(int n, int P, tds_dtype dtype);
+size_t pipe_smem_bytes(int n, int P, tds_dtype dtype, int nbuf);
 tds_status launch_resident(const tds_plan *p, int which, const void *in, void *out,
                            cudaStream_t st);
+tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *out,
+                            cudaStream_t st);
 size_t streaming_ws_bytes(const tds_plan *p);
 tds_status launch_streaming(const tds_plan *p, int which, const void *in, void *out,
                             void *ws, cudaStream_t st);

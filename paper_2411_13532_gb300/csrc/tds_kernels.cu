@@ -155,140 +155,503 @@ __device__ void reduced_solve(const DevOp &op, double *x, int stride) {
 }
 
 // ------------------------------------------------------------------------------------------
-// RESIDENT pipeline: one CTA per group, warp k = chunk k.
-// Shared memory: tile[n][32] (T) | ends[2P][32] (double) | bars[P] (mbarrier).
+// RESIDENT pipeline: one CTA holds a whole group of 32 lines.  Chunk k is swept by 32/V
+// threads; each thread carries V adjacent lines (one 16-byte vector of a row for FP32 V=4),
+// which gives V independent recurrences per thread and spreads the per-row work (plan
+// coefficients, addressing, loop control) over V points.
 // ------------------------------------------------------------------------------------------
-template <typename T, bool ADJ>
-__global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_constant__ DevOp op, const T *__restrict__ in,
-                                                   T *__restrict__ out) {
+template <typename T, int V>
+struct Pack {
+    T v[V];
+};
+
+template <typename T, int V>
+__device__ __forceinline__ Pack<T, V> ldv(const T *p) {
+    Pack<T, V> r;
+    if constexpr (V == 1) {
+        r.v[0] = *p;
+    } else if constexpr (sizeof(T) * V == 16 && sizeof(T) == 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(p);
+        r.v[0] = x.x; r.v[1] = x.y; r.v[2] = x.z; r.v[3] = x.w;
+    } else if constexpr (sizeof(T) * V == 16 && sizeof(T) == 8) {
+        const double2 x = *reinterpret_cast<const double2 *>(p);
+        r.v[0] = x.x; r.v[1] = x.y;
+    } else {
+        const float2 x = *reinterpret_cast<const float2 *>(p);
+        r.v[0] = x.x; r.v[1] = x.y;
+    }
+    return r;
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void stv(T *p, const Pack<T, V> &r) {
+    if constexpr (V == 1) {
+        *p = r.v[0];
+    } else if constexpr (sizeof(T) * V == 16 && sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+    } else if constexpr (sizeof(T) * V == 16 && sizeof(T) == 8) {
+        *reinterpret_cast<double2 *>(p) = make_double2(r.v[0], r.v[1]);
+    } else {
+        *reinterpret_cast<float2 *>(p) = make_float2(r.v[0], r.v[1]);
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ Pack<T, V> zero_pack() {
+    Pack<T, V> r;
+#pragma unroll
+    for (int i = 0; i < V; ++i) r.v[i] = T(0);
+    return r;
+}
+
+template <typename T, int V>
+__device__ __forceinline__ Pack<T, V> pick3v(int i, const Pack<T, V> &a0, const Pack<T, V> &a1,
+                                             const Pack<T, V> &a2) {
+    return (i == 0) ? a0 : (i == 1 ? a1 : a2);
+}
+
+// Plan row records of the resident sweep (see DevOp::fwd64 / bwd64).
+template <typename T>
+struct FwdRec {
+    T f, r, pi;
+};
+
+template <typename T>
+__device__ __forceinline__ FwdRec<T> ld_fwd(const DevOp &op, int cls, int j) {
+    const size_t i = (size_t)cls * op.m + j;
+    if constexpr (sizeof(T) == 4) {
+        const float4 x = __ldg(reinterpret_cast<const float4 *>(op.fwd32) + i);
+        return {x.x, x.y, x.z};
+    } else {
+        const double2 x = __ldg(reinterpret_cast<const double2 *>(op.fwd64) + 2 * i);
+        return {x.x, x.y, __ldg(op.fwd64 + 4 * i + 2)};
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void ld_bwd(const DevOp &op, int cls, int j, T &sa, T &sc) {
+    const size_t i = (size_t)cls * op.m + j;
+    if constexpr (sizeof(T) == 4) {
+        const float2 x = __ldg(reinterpret_cast<const float2 *>(op.bwd32) + i);
+        sa = x.x; sc = x.y;
+    } else {
+        const double2 x = __ldg(reinterpret_cast<const double2 *>(op.bwd64) + i);
+        sa = x.x; sc = x.y;
+    }
+}
+
+// Interior stencil (offsets -2..2) of V lines from the window w[i] = v[J - 2 + i].
+template <typename T, int V, bool SYM>
+__device__ __forceinline__ void istencil(T t0, T t1, T t2, const Pack<T, V> (&w)[5], T (&s)[V]) {
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        if (SYM) s[i] = t0 * w[2].v[i] + t1 * (w[3].v[i] + w[1].v[i]) + t2 * (w[4].v[i] + w[0].v[i]);
+        else s[i] = t1 * (w[3].v[i] - w[1].v[i]) + t2 * (w[4].v[i] - w[0].v[i]);
+    }
+}
+
+// Closure-row stencil (offsets -3..3, closed lines only) from w[i] = v[J - 3 + i]; e indexes
+// the plan's edge rows (0..3 = rows 0..3, 4..7 = rows n-4..n-1).
+template <typename T, int V>
+__device__ __forceinline__ void estencil(const DevOp &op, int e, const Pack<T, V> (&w)[kTaps], T (&s)[V]) {
+#pragma unroll
+    for (int i = 0; i < V; ++i) s[i] = T(0);
+#pragma unroll
+    for (int o = 0; o < kTaps; ++o) {
+        const T c = T(op.edge[e][o]);
+#pragma unroll
+        for (int i = 0; i < V; ++i) s[i] += c * w[o].v[i];
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ Pack<T, V> ld_row(const DevOp &op, const T *tile, int J, int c) {
+    const int r = line_row(op, J);
+    return (r >= 0) ? ldv<T, V>(tile + (size_t)r * kSZ + c) : zero_pack<T, V>();
+}
+
+// Before the sweep (and before the CTA barrier that lets any thread overwrite the tile): the
+// stencil halo of this chunk (2 rows before, 2 after) into registers, and on closed lines the
+// first and last 7 rows of the line into the scratch rows xs[0..6], xs[7..13] (the closure
+// rows reach 3 points in, and the sweep overwrites the tile in place).
+template <typename T, int V>
+__device__ __forceinline__ void read_halo(const DevOp &op, const T *tile, T *xs, int k, int c,
+                                          Pack<T, V> (&hb)[2], Pack<T, V> (&ha)[2]) {
+    const int J0 = k * op.m;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        hb[i] = ld_row<T, V>(op, tile, J0 - 2 + i, c);
+        ha[i] = ld_row<T, V>(op, tile, J0 + op.m + i, c);
+    }
+    if (!op.periodic) {
+        if (k == 0)
+            for (int i = 0; i < kTaps; ++i) stv<T, V>(xs + (size_t)i * kSZ + c, ld_row<T, V>(op, tile, i, c));
+        if (k == op.P - 1)
+            for (int i = 0; i < kTaps; ++i)
+                stv<T, V>(xs + (size_t)(kTaps + i) * kSZ + c, ld_row<T, V>(op, tile, op.n - kTaps + i, c));
+    }
+}
+
+// Forward pass over rows [jb, je) of the chunk with the interior stencil: d_j = f_j (s_j -
+// r_j d_{j-1}), S += pi_j d_j, d_j written over the tile row.  w[0..3] holds v[j-2..j+1] on
+// entry; v[j+2] comes from the tile while inside the chunk, then from the halo after it.
+template <typename T, int V, bool SYM>
+__device__ __forceinline__ void fwd_interior(const DevOp &op, int cls, T *row, int jb, int je,
+                                             Pack<T, V> (&w)[5], const Pack<T, V> (&ha)[2],
+                                             Pack<T, V> &dprev, Pack<T, V> &S) {
+    const int m = op.m;
+    const T t0 = T(op.tap[3]), t1 = T(op.tap[4]), t2 = T(op.tap[5]);
+    const int jm = (je < m - 2) ? je : m - 2;
+#pragma unroll 4
+    for (int j = jb; j < jm; ++j) {
+        w[4] = ldv<T, V>(row + (size_t)(j + 2) * kSZ);
+        T sv[V];
+        istencil<T, V, SYM>(t0, t1, t2, w, sv);
+        const FwdRec<T> q = ld_fwd<T>(op, cls, j);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            dprev.v[i] = q.f * (sv[i] - q.r * dprev.v[i]);
+            S.v[i] = fma(q.pi, dprev.v[i], S.v[i]);
+        }
+        stv<T, V>(row + (size_t)j * kSZ, dprev);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
+    }
+    for (int j = (jb > m - 2 ? jb : m - 2); j < je; ++j) {
+        w[4] = (j + 2 - m == 0) ? ha[0] : ha[1];
+        T sv[V];
+        istencil<T, V, SYM>(t0, t1, t2, w, sv);
+        const FwdRec<T> q = ld_fwd<T>(op, cls, j);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            dprev.v[i] = q.f * (sv[i] - q.r * dprev.v[i]);
+            S.v[i] = fma(q.pi, dprev.v[i], S.v[i]);
+        }
+        stv<T, V>(row + (size_t)j * kSZ, dprev);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
+    }
+}
+
+// Closure rows of the forward pass: local rows j0..j0+3 whose 7-point windows are the scratch
+// rows x[t + o] (t = 0..3, o = 0..6) with x[i] = v[Jx + i]; entries outside the line are zero.
+template <typename T, int V>
+__device__ __forceinline__ void fwd_edge(const DevOp &op, int cls, T *row, int j0, int e0,
+                                         const T *xs, int c, int xlo, int xhi,
+                                         Pack<T, V> &dprev, Pack<T, V> &S) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        Pack<T, V> w7[kTaps];
+#pragma unroll
+        for (int o = 0; o < kTaps; ++o) {
+            const int x = t + o + xlo;   // scratch index, valid in [0, xhi)
+            w7[o] = (x >= 0 && x < xhi) ? ldv<T, V>(xs + (size_t)x * kSZ + c) : zero_pack<T, V>();
+        }
+        T sv[V];
+        estencil<T, V>(op, e0 + t, w7, sv);
+        const int j = j0 + t;
+        const FwdRec<T> q = ld_fwd<T>(op, cls, j);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            dprev.v[i] = q.f * (sv[i] - q.r * dprev.v[i]);
+            S.v[i] = fma(q.pi, dprev.v[i], S.v[i]);
+        }
+        stv<T, V>(row + (size_t)j * kSZ, dprev);
+    }
+}
+
+// x = B^T y over this chunk's rows [jb, je) with the interior taps; the tile holds y for the
+// whole line (read only), results go to `orow`.
+template <typename T, int V, bool SYM>
+__device__ __forceinline__ void bt_interior(const DevOp &op, const T *tile, T *orow, int J0, int jb,
+                                            int je, int c) {
+    const int m = op.m;
+    const T t0 = T(op.tap[3]), t1 = T(op.tap[4]), t2 = T(op.tap[5]);
+    Pack<T, V> w[5];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = ld_row<T, V>(op, tile, J0 + jb - 2 + i, c);
+    const int jm = (je < m - 2) ? je : m - 2;
+#pragma unroll 4
+    for (int j = jb; j < jm; ++j) {
+        w[4] = ldv<T, V>(tile + (size_t)(J0 + j + 2) * kSZ + c);
+        T sv[V];
+        istencil<T, V, SYM>(t0, t1, t2, w, sv);
+        Pack<T, V> x;
+#pragma unroll
+        for (int i = 0; i < V; ++i) x.v[i] = sv[i];
+        stv<T, V>(orow + (size_t)j * kSZ, x);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
+    }
+    for (int j = (jb > m - 2 ? jb : m - 2); j < je; ++j) {
+        w[4] = ld_row<T, V>(op, tile, J0 + j + 2, c);
+        T sv[V];
+        istencil<T, V, SYM>(t0, t1, t2, w, sv);
+        Pack<T, V> x;
+#pragma unroll
+        for (int i = 0; i < V; ++i) x.v[i] = sv[i];
+        stv<T, V>(orow + (size_t)j * kSZ, x);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void bt_edge(const DevOp &op, const T *tile, T *orow, int J0, int j0,
+                                        int e0, int c) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int J = J0 + j0 + t;
+        Pack<T, V> w7[kTaps];
+#pragma unroll
+        for (int o = 0; o < kTaps; ++o) w7[o] = ld_row<T, V>(op, tile, J - 3 + o, c);
+        T sv[V];
+        estencil<T, V>(op, e0 + t, w7, sv);
+        Pack<T, V> x;
+#pragma unroll
+        for (int i = 0; i < V; ++i) x.v[i] = sv[i];
+        stv<T, V>(orow + (size_t)(j0 + t) * kSZ, x);
+    }
+}
+
+// One group, called by every thread of the CTA after the tile has landed and every thread has
+// run read_halo.  The DistD2 phases of Sec. 4.2 with the backward pass fused into the
+// substitution:
+//   forward  : fused stencil + forward elimination (Algorithm 5), accumulating the back-swept
+//              row 1 as S = sum_j pi_j d_j, so that row 0 is decoupled (d0~ = N1 (d_0 - w_0 S))
+//              without a separate backward pass;
+//   reduced  : the chunk-end system in FP64 (decoupled 2x2 boundaries or the full 2P system);
+//   back-substitution: u_{m-1} = L, u_j = d_j - s^a_j F - s^c_j u_{j+1}, u_0 = F -- the
+//              backward pass and Algorithm 6 in one reverse sweep over the forward rows.
+// Results go to `og` (forward operator) or back into the tile for the B^T pass (adjoint).
+template <typename T, int V, bool ADJ>
+__device__ __forceinline__ void group_sweep(const DevOp &op, T *tile, T *xs, double *ends, T *og,
+                                            int k, int c, const Pack<T, V> (&hb)[2],
+                                            const Pack<T, V> (&ha)[2]) {
+    const int m = op.m, P = op.P, n = op.n;
+    const int cls = chunk_class(op, k);
+    const int J0 = k * m;
+    const bool first_edge = !op.periodic && k == 0;
+    const bool last_edge = !op.periodic && k == P - 1;
+    T *row = tile + (size_t)J0 * kSZ + c;
+    Pack<T, V> dprev = zero_pack<T, V>(), S = zero_pack<T, V>();
+
+    // ---- forward pass ----
+    if (!ADJ) {
+        const int jb = first_edge ? 4 : 0, je = last_edge ? m - 4 : m;
+        if (first_edge) fwd_edge<T, V>(op, cls, row, 0, 0, xs, c, -3, kTaps, dprev, S);
+        Pack<T, V> w[5];
+        if (first_edge) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[i] = ldv<T, V>(xs + (size_t)(2 + i) * kSZ + c);
+        } else {
+            w[0] = hb[0]; w[1] = hb[1];
+            w[2] = ldv<T, V>(row); w[3] = ldv<T, V>(row + kSZ);
+        }
+        if (op.symmetric > 0) fwd_interior<T, V, true>(op, cls, row, jb, je, w, ha, dprev, S);
+        else fwd_interior<T, V, false>(op, cls, row, jb, je, w, ha, dprev, S);
+        // last 4 rows of a closed line: scratch rows 7..13 hold v[n-7..n-1]; row n-4+t has
+        // window v[n-7+t .. n-1+t]
+        if (last_edge) fwd_edge<T, V>(op, cls, row, m - 4, kEdgeRows, xs + (size_t)kTaps * kSZ, c, 0, kTaps, dprev, S);
+    } else {
+#pragma unroll 4
+        for (int j = 0; j < m; ++j) {
+            const Pack<T, V> g = ldv<T, V>(row + (size_t)j * kSZ);
+            const FwdRec<T> q = ld_fwd<T>(op, cls, j);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                dprev.v[i] = q.f * (g.v[i] - q.r * dprev.v[i]);
+                S.v[i] = fma(q.pi, dprev.v[i], S.v[i]);
+            }
+            stv<T, V>(row + (size_t)j * kSZ, dprev);
+        }
+    }
+    {
+        // row 0 eliminates the back-swept row 1: d0~ = N1 (d_0 - w_0 S); chunk ends to `ends`
+        const Pack<T, V> d0 = ldv<T, V>(row);
+        T sa0, w0;
+        ld_bwd<T>(op, cls, 0, sa0, w0);
+        const T n1 = T(__ldg(op.n1 + cls));
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            ends[(size_t)(2 * k) * kSZ + c + i] = double(n1 * (d0.v[i] - w0 * S.v[i]));
+            ends[(size_t)(2 * k + 1) * kSZ + c + i] = double(dprev.v[i]);
+        }
+    }
+    __syncthreads();
+
+    // ---- reduced chunk-end system, FP64 ----
+    if (op.red_decoupled) {
+        // boundary k joins L_{k-1} (ends slot 2k-1) and F_k (slot 2k): every thread solves its
+        // own lines' boundary; each slot is read and written by exactly one thread
+        const int R = 2 * P, prev = (k == 0) ? P - 1 : k - 1;
+        const double a = __ldg(op.red + (size_t)kRedBa * R + k);
+        const double cc = __ldg(op.red + (size_t)kRedBc * R + k);
+        const double inv = __ldg(op.red + (size_t)kRedBinv * R + k);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            double *ef = ends + (size_t)(2 * k) * kSZ + c + i;
+            double *el = ends + (size_t)(2 * prev + 1) * kSZ + c + i;
+            const double dl = *el;
+            const double Fk = (*ef - a * dl) * inv;
+            *ef = Fk;
+            *el = dl - cc * Fk;
+        }
+    } else {
+        for (int l = threadIdx.x; l < kSZ; l += blockDim.x) reduced_solve(op, ends + l, kSZ);
+    }
+    __syncthreads();
+
+    // ---- back-substitution: u_{m-1} = L, u_j = d_j - s^a_j F - s^c_j u_{j+1}, u_0 = F ----
+    Pack<T, V> F, u;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        F.v[i] = T(ends[(size_t)(2 * k) * kSZ + c + i]);
+        u.v[i] = T(ends[(size_t)(2 * k + 1) * kSZ + c + i]);
+    }
+    T *orow = og + (size_t)J0 * kSZ + c;
+    T *dst = ADJ ? row : orow;   // adjoint: y stays in the tile for the B^T pass
+    stv<T, V>(dst + (size_t)(m - 1) * kSZ, u);
+#pragma unroll 4
+    for (int j = m - 2; j >= 1; --j) {
+        const Pack<T, V> d = ldv<T, V>(row + (size_t)j * kSZ);
+        T sa, sc;
+        ld_bwd<T>(op, cls, j, sa, sc);
+#pragma unroll
+        for (int i = 0; i < V; ++i) u.v[i] = (d.v[i] - sa * F.v[i]) - sc * u.v[i];
+        stv<T, V>(dst + (size_t)j * kSZ, u);
+    }
+    stv<T, V>(dst, F);
+    if (!ADJ) return;
+
+    // ---- adjoint: x = B^T y ----
+    __syncthreads();
+    const int jb = first_edge ? 4 : 0, je = last_edge ? m - 4 : m;
+    if (first_edge) bt_edge<T, V>(op, tile, orow, J0, 0, 0, c);
+    if (op.symmetric > 0) bt_interior<T, V, true>(op, tile, orow, J0, jb, je, c);
+    else bt_interior<T, V, false>(op, tile, orow, J0, jb, je, c);
+    if (last_edge) bt_edge<T, V>(op, tile, orow, J0, m - 4, kEdgeRows, c);
+    (void)n;
+}
+
+// Shared-memory layout of the resident kernels (per tile buffer, then once per CTA):
+//   tiles[nbuf][n][32] (T) | xs[14][32] (T, closure rows) | ends[2P][32] (double) | bars
+__host__ __device__ inline size_t tile_bytes_of(int n, size_t es) { return (size_t)n * kSZ * es; }
+__host__ __device__ inline size_t xs_bytes_of(size_t es) { return ((size_t)2 * kTaps * kSZ * es + 15) & ~(size_t)15; }
+
+// One CTA per group, P * 32/V threads.  The tile arrives as one TMA bulk copy per chunk; a
+// thread starts as soon as its own chunk and its neighbours' have landed.
+template <typename T, int V, bool ADJ>
+__global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_constant__ DevOp op,
+                                                                 const T *__restrict__ in,
+                                                                 T *__restrict__ out) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int failed;
     const int n = op.n, m = op.m, P = op.P;
-    const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
+    constexpr int tpc = kSZ / V;
+    const int k = threadIdx.x / tpc, c = (threadIdx.x % tpc) * V;
     const size_t gofs = (size_t)blockIdx.x * n * kSZ;
     T *tile = reinterpret_cast<T *>(smem);
-    double *ends = reinterpret_cast<double *>(smem + (((size_t)n * kSZ * sizeof(T) + 15) & ~(size_t)15));
+    T *xs = reinterpret_cast<T *>(smem + tile_bytes_of(n, sizeof(T)));
+    double *ends = reinterpret_cast<double *>(smem + tile_bytes_of(n, sizeof(T)) + xs_bytes_of(sizeof(T)));
     uint64_t *bars = reinterpret_cast<uint64_t *>(ends + (size_t)2 * P * kSZ);
     const uint32_t chunk_bytes = (uint32_t)((size_t)m * kSZ * sizeof(T));
 
     if (threadIdx.x == 0) {
         failed = 0;
-        for (int c = 0; c < P; ++c) mbar_init(&bars[c], 1);
+        for (int q = 0; q < P; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int c = 0; c < P; ++c) {
-            mbar_expect_tx(&bars[c], chunk_bytes);
-            bulk_g2s(tile + (size_t)c * m * kSZ, in + gofs + (size_t)c * m * kSZ, chunk_bytes, &bars[c]);
+        for (int q = 0; q < P; ++q) {
+            mbar_expect_tx(&bars[q], chunk_bytes);
+            bulk_g2s(tile + (size_t)q * m * kSZ, in + gofs + (size_t)q * m * kSZ, chunk_bytes, &bars[q]);
         }
     }
-    // this warp's chunk and, for the stencil halo, its neighbours
     bool ok = mbar_wait(&bars[k], 0);
     if (!ADJ) {
         if (k > 0 || op.periodic) ok = mbar_wait(&bars[(k - 1 + P) % P], 0) && ok;
         if (k < P - 1 || op.periodic) ok = mbar_wait(&bars[(k + 1) % P], 0) && ok;
+        // the closure rows of a closed line may reach into the second / second-to-last chunk
+        if (!op.periodic && (k == 0 || k == P - 1))
+            for (int q = 0; q < P; ++q) ok = mbar_wait(&bars[q], 0) && ok;
     }
-    if (!ok && lane == 0) atomicExch(&failed, 1);
-
-    const int cls = chunk_class(op, k);
-    const int J0 = k * m;
-    T win[kTaps];
-    T halo_after[3];
-    if (!ADJ) {
-        // halo rows of u before anyone overwrites them
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const int rb = line_row(op, J0 - 3 + i);
-            win[i] = (ok && rb >= 0) ? tile[(size_t)rb * kSZ + lane] : T(0);
-            const int ra = line_row(op, J0 + m + i);
-            halo_after[i] = (ok && ra >= 0) ? tile[(size_t)ra * kSZ + lane] : T(0);
-        }
-    }
+    if (!ok) atomicExch(&failed, 1);
+    Pack<T, V> hb[2], ha[2];
+    if (!ADJ && ok) read_halo<T, V>(op, tile, xs, k, c, hb, ha);
     __syncthreads();
     if (failed) {
         // let every bulk copy land before the CTA's shared memory is released
-        if (threadIdx.x < P) mbar_wait(&bars[threadIdx.x], 0);
+        for (int q = threadIdx.x; q < P; q += blockDim.x) mbar_wait(&bars[q], 0);
         if (threadIdx.x == 0) record_timeout();
         return;
     }
+    group_sweep<T, V, ADJ>(op, tile, xs, ends, out + gofs, k, c, hb, ha);
+}
 
-    // ---- decoupling (Algorithm 5): forward pass with the fused right-hand side ----
-    T *row = tile + (size_t)J0 * kSZ + lane;
-    T dprev = T(0);
-    if (!ADJ) {
-#pragma unroll
-        for (int i = 3; i < kTaps; ++i) win[i] = row[(size_t)(i - 3) * kSZ];
-#pragma unroll 4
-        for (int j = 0; j < m; ++j) {
-            const T s = stencil<T>(op, J0 + j, win);
-            const T d = rowc<T>(op, kF, cls, j) * (s - rowc<T>(op, kR, cls, j) * dprev);
-            row[(size_t)j * kSZ] = d;
-            dprev = d;
-#pragma unroll
-            for (int i = 0; i < kTaps - 1; ++i) win[i] = win[i + 1];
-            const int jn = j + 4;
-            win[kTaps - 1] = (jn < m) ? row[(size_t)jn * kSZ]
-                                      : pick3<T>(jn - m, halo_after[0], halo_after[1], halo_after[2]);
+// Persistent variant: each CTA walks groups blockIdx.x, +gridDim.x, ... through `nbuf` tile
+// buffers; the TMA bulk copy of a group is issued `nbuf` groups ahead, so HBM reads stay in
+// flight while the threads sweep.
+template <typename T, int V, bool ADJ>
+__global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_pipe(const __grid_constant__ DevOp op,
+                                                                      const T *__restrict__ in,
+                                                                      T *__restrict__ out, int nbuf) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int failed;
+    const int n = op.n, P = op.P, G = op.ngroups;
+    constexpr int tpc = kSZ / V;
+    const int k = threadIdx.x / tpc, c = (threadIdx.x % tpc) * V;
+    const size_t tile_elems = (size_t)n * kSZ;
+    const uint32_t tile_bytes = (uint32_t)tile_bytes_of(n, sizeof(T));
+    T *tiles = reinterpret_cast<T *>(smem);
+    T *xs = reinterpret_cast<T *>(smem + (size_t)nbuf * tile_bytes);
+    double *ends = reinterpret_cast<double *>(smem + (size_t)nbuf * tile_bytes + xs_bytes_of(sizeof(T)));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ends + (size_t)2 * P * kSZ);
+
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int b = 0; b < nbuf; ++b) mbar_init(&bars[b], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < nbuf; ++b) {
+            const long long g = blockIdx.x + (long long)b * gridDim.x;
+            if (g >= G) break;
+            mbar_expect_tx(&bars[b], tile_bytes);
+            bulk_g2s(tiles + (size_t)b * tile_elems, in + (size_t)g * tile_elems, tile_bytes, &bars[b]);
         }
-    } else {
-#pragma unroll 4
-        for (int j = 0; j < m; ++j) {
-            const T d = rowc<T>(op, kF, cls, j) * (row[(size_t)j * kSZ] - rowc<T>(op, kR, cls, j) * dprev);
-            row[(size_t)j * kSZ] = d;
-            dprev = d;
+    }
+    for (int it = 0;; ++it) {
+        const long long g = blockIdx.x + (long long)it * gridDim.x;
+        if (g >= G) break;
+        const int b = it % nbuf;
+        T *tile = tiles + (size_t)b * tile_elems;
+        const bool ok = mbar_wait(&bars[b], (uint32_t)((it / nbuf) & 1));
+        if (!ok) atomicExch(&failed, 1);
+        Pack<T, V> hb[2], ha[2];
+        if (!ADJ && ok) read_halo<T, V>(op, tile, xs, k, c, hb, ha);
+        __syncthreads();
+        if (failed) {
+            // drain every bulk copy still in flight into this CTA's buffers, then give up
+            for (int d = threadIdx.x; d < nbuf; d += blockDim.x)
+                if (blockIdx.x + (long long)(it + d) * gridDim.x < G)
+                    mbar_wait(&bars[(it + d) % nbuf], (uint32_t)(((it + d) / nbuf) & 1));
+            if (threadIdx.x == 0) record_timeout();
+            return;
         }
-    }
-    // backward pass j = m-3 .. 1, then row 0 eliminates row 1
-    T dnext = row[(size_t)(m - 2) * kSZ];
-#pragma unroll 4
-    for (int j = m - 3; j >= 1; --j) {
-        const T d = row[(size_t)j * kSZ] - rowc<T>(op, kW, cls, j) * dnext;
-        row[(size_t)j * kSZ] = d;
-        dnext = d;
-    }
-    const T d0 = T(__ldg(op.n1 + cls)) * (row[0] - rowc<T>(op, kW, cls, 0) * dnext);
-    row[0] = d0;
-    ends[(size_t)(2 * k) * kSZ + lane] = double(d0);
-    ends[(size_t)(2 * k + 1) * kSZ + lane] = double(row[(size_t)(m - 1) * kSZ]);
-    __syncthreads();
-
-    // ---- reduced chunk-end system, FP64, one lane per line ----
-    if (k == 0) reduced_solve(op, ends + lane, kSZ);
-    __syncthreads();
-
-    // ---- substitution (Algorithm 6) ----
-    const double F64 = ends[(size_t)(2 * k) * kSZ + lane];
-    const double L64 = ends[(size_t)(2 * k + 1) * kSZ + lane];
-    const T F = T(F64), L = T(L64);
-    T *orow = out + gofs + (size_t)J0 * kSZ + lane;
-    if (!ADJ) {
-        orow[0] = F;
-#pragma unroll 4
-        for (int j = 1; j < m - 1; ++j)
-            orow[(size_t)j * kSZ] = row[(size_t)j * kSZ] - rowc<T>(op, kSA, cls, j) * F - rowc<T>(op, kSC, cls, j) * L;
-        orow[(size_t)(m - 1) * kSZ] = L;
-        return;
-    }
-    // adjoint: y in place, then x = B^T y with a rolling window over this chunk
-    row[0] = F;
-#pragma unroll 4
-    for (int j = 1; j < m - 1; ++j)
-        row[(size_t)j * kSZ] = row[(size_t)j * kSZ] - rowc<T>(op, kSA, cls, j) * F - rowc<T>(op, kSC, cls, j) * L;
-    row[(size_t)(m - 1) * kSZ] = L;
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kTaps; ++i) {
-        const int r = line_row(op, J0 - 3 + i);
-        win[i] = (r >= 0) ? tile[(size_t)r * kSZ + lane] : T(0);
-    }
-#pragma unroll 4
-    for (int j = 0; j < m; ++j) {
-        orow[(size_t)j * kSZ] = stencil<T>(op, J0 + j, win);
-#pragma unroll
-        for (int i = 0; i < kTaps - 1; ++i) win[i] = win[i + 1];
-        const int r = line_row(op, J0 + j + 4);
-        win[kTaps - 1] = (r >= 0) ? tile[(size_t)r * kSZ + lane] : T(0);
+        group_sweep<T, V, ADJ>(op, tile, xs, ends, out + (size_t)g * tile_elems, k, c, hb, ha);
+        __syncthreads();   // every thread is done with this tile, the scratch rows and `ends`
+        if (threadIdx.x == 0) {
+            const long long gn = g + (long long)nbuf * gridDim.x;
+            if (gn < G) {
+                // generic-proxy accesses of the buffer are ordered before the async refill
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&bars[b], tile_bytes);
+                bulk_g2s(tile, in + (size_t)gn * tile_elems, tile_bytes, &bars[b]);
+            }
+        }
     }
 }
 
@@ -443,12 +806,22 @@ __global__ void k_reduced_lines(const __grid_constant__ DevOp op, const double *
     reduced_solve(op, xl, 1);
 }
 
-template <typename T, bool ADJ>
+template <typename T, int V, bool ADJ>
 tds_status launch_resident_t(const DevOp &op, const void *in, void *out, int smem, cudaStream_t st) {
-    auto kern = k_resident<T, ADJ>;
+    auto kern = k_resident<T, V, ADJ>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return TDS_ERR_CUDA;
-    kern<<<op.ngroups, op.P * 32, smem, st>>>(op, static_cast<const T *>(in), static_cast<T *>(out));
+    kern<<<op.ngroups, op.P * (kSZ / V), smem, st>>>(op, static_cast<const T *>(in), static_cast<T *>(out));
+    return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
+}
+
+template <typename T, int V, bool ADJ>
+tds_status launch_pipe_t(const DevOp &op, const void *in, void *out, int nbuf, int smem, int grid,
+                         cudaStream_t st) {
+    auto kern = k_resident_pipe<T, V, ADJ>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return TDS_ERR_CUDA;
+    kern<<<grid, op.P * (kSZ / V), smem, st>>>(op, static_cast<const T *>(in), static_cast<T *>(out), nbuf);
     return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
 }
 
@@ -470,16 +843,49 @@ tds_status launch_streaming_t(const DevOp &op, const void *in, void *out, void *
 
 size_t resident_smem_bytes(int n, int P, tds_dtype dtype) {
     const size_t es = (dtype == TDS_F64) ? 8 : 4;
-    return (((size_t)n * kSZ * es + 15) & ~(size_t)15) + (size_t)2 * P * kSZ * 8 + (size_t)P * 8;
+    return tile_bytes_of(n, es) + xs_bytes_of(es) + (size_t)2 * P * kSZ * 8 + (size_t)P * 8;
+}
+
+size_t pipe_smem_bytes(int n, int P, tds_dtype dtype, int nbuf) {
+    const size_t es = (dtype == TDS_F64) ? 8 : 4;
+    return (size_t)nbuf * tile_bytes_of(n, es) + xs_bytes_of(es) + (size_t)2 * P * kSZ * 8 + (size_t)nbuf * 8;
+}
+
+// Lines per thread in the resident kernels (tds_plan::lanes): 1, 2 or 4 for FP32, 1 or 2 for
+// FP64.  More lanes spread the per-row work (plan coefficients, addressing, loop control) over
+// more points and give each thread independent recurrences; fewer lanes give more threads.
+template <typename T, int V>
+tds_status launch_pipelined_v(const tds_plan *p, int which, const void *in, void *out, cudaStream_t st) {
+    const DevOp &op = p->op[which];
+    const int smem = (int)pipe_smem_bytes(p->n, p->P, p->dtype, p->pipe_nbuf);
+    const int grid = op.ngroups < p->pipe_grid ? op.ngroups : p->pipe_grid;
+    return which ? launch_pipe_t<T, V, true>(op, in, out, p->pipe_nbuf, smem, grid, st)
+                 : launch_pipe_t<T, V, false>(op, in, out, p->pipe_nbuf, smem, grid, st);
+}
+
+template <typename T, int V>
+tds_status launch_resident_v(const tds_plan *p, int which, const void *in, void *out, cudaStream_t st) {
+    const DevOp &op = p->op[which];
+    return which ? launch_resident_t<T, V, true>(op, in, out, p->resident_smem, st)
+                 : launch_resident_t<T, V, false>(op, in, out, p->resident_smem, st);
+}
+
+tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *out, cudaStream_t st) {
+    if (p->dtype == TDS_F64)
+        return p->lanes == 2 ? launch_pipelined_v<double, 2>(p, which, in, out, st)
+                             : launch_pipelined_v<double, 1>(p, which, in, out, st);
+    return p->lanes == 4 ? launch_pipelined_v<float, 4>(p, which, in, out, st)
+         : p->lanes == 2 ? launch_pipelined_v<float, 2>(p, which, in, out, st)
+                         : launch_pipelined_v<float, 1>(p, which, in, out, st);
 }
 
 tds_status launch_resident(const tds_plan *p, int which, const void *in, void *out, cudaStream_t st) {
-    const DevOp &op = p->op[which];
     if (p->dtype == TDS_F64)
-        return which ? launch_resident_t<double, true>(op, in, out, p->resident_smem, st)
-                     : launch_resident_t<double, false>(op, in, out, p->resident_smem, st);
-    return which ? launch_resident_t<float, true>(op, in, out, p->resident_smem, st)
-                 : launch_resident_t<float, false>(op, in, out, p->resident_smem, st);
+        return p->lanes == 2 ? launch_resident_v<double, 2>(p, which, in, out, st)
+                             : launch_resident_v<double, 1>(p, which, in, out, st);
+    return p->lanes == 4 ? launch_resident_v<float, 4>(p, which, in, out, st)
+         : p->lanes == 2 ? launch_resident_v<float, 2>(p, which, in, out, st)
+                         : launch_resident_v<float, 1>(p, which, in, out, st);
 }
 
 size_t streaming_ws_bytes(const tds_plan *p) {

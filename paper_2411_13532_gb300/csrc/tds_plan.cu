@@ -97,7 +97,8 @@ void transpose_line(int n, bool periodic, const LineOperator &L, LineOperator &T
 // Algorithm 4 on one chunk of m rows with local band (a, b, c): a[0] couples to the previous
 // chunk's last unknown, c[m-1] to the next chunk's first.  Returns false on a zero pivot.
 bool preprocess_chunk(int m, const double *a, const double *b, const double *c,
-                      double *f, double *r, double *w, double *sa, double *sc, double *n1) {
+                      double *f, double *r, double *w, double *sa, double *sc, double *n1,
+                      double *saf, double *scf, double *pi) {
     for (int j = 0; j < 2; ++j) {          // rows 1 and 2 of the paper: normalise only
         if (b[j] == 0.0) return false;
         sa[j] = a[j] / b[j];
@@ -115,6 +116,10 @@ bool preprocess_chunk(int m, const double *a, const double *b, const double *c,
         sc[j] = f[j] * c[j];
         w[j] = 0.0;
     }
+    // forward-pass couplings, and the weights of the forward values in the back-swept row 1
+    for (int j = 0; j < m; ++j) { saf[j] = sa[j]; scf[j] = sc[j]; pi[j] = 0.0; }
+    pi[1] = 1.0;
+    for (int j = 2; j <= m - 2; ++j) pi[j] = -pi[j - 1] * scf[j - 1];
     for (int j = m - 3; j >= 1; --j) {     // backward elimination against row j+1
         sa[j] = sa[j] - sc[j] * sa[j + 1];
         w[j] = sc[j];
@@ -135,7 +140,8 @@ bool preprocess_chunk(int m, const double *a, const double *b, const double *c,
 static tds_status build_operator(const tds_plan *p, const LineOperator &L, int which,
                                  DevOp &op, std::vector<double> &rows,
                                  std::vector<double> &n1s, std::vector<double> &red,
-                                 std::vector<double> &sub, std::vector<double> &sup) {
+                                 std::vector<double> &sub, std::vector<double> &sup,
+                                 std::vector<double> &fwd, std::vector<double> &bwd) {
     const int n = p->n, m = p->m, P = p->P;
     const bool periodic = (p->bc == TDS_BC_PERIODIC);
     std::memset(&op, 0, sizeof(op));
@@ -152,14 +158,22 @@ static tds_status build_operator(const tds_plan *p, const LineOperator &L, int w
     const int nc = op.ncls;
     rows.assign((size_t)kNumRowArrays * nc * m, 0.0);
     n1s.assign(nc, 0.0);
+    fwd.assign((size_t)nc * m * 4, 0.0);
+    bwd.assign((size_t)nc * m * 2, 0.0);
+    std::vector<double> saf(m), scf(m), pi(m);
     for (int cl = 0; cl < nc; ++cl) {
         const int k = reps[cl];
         double *f = &rows[((size_t)kF * nc + cl) * m], *r = &rows[((size_t)kR * nc + cl) * m];
         double *w = &rows[((size_t)kW * nc + cl) * m], *sa = &rows[((size_t)kSA * nc + cl) * m];
         double *sc = &rows[((size_t)kSC * nc + cl) * m];
         if (!preprocess_chunk(m, &L.a[(size_t)k * m], &L.b[(size_t)k * m], &L.c[(size_t)k * m],
-                              f, r, w, sa, sc, &n1s[cl]))
+                              f, r, w, sa, sc, &n1s[cl], saf.data(), scf.data(), pi.data()))
             return TDS_ERR_ARG;
+        for (int j = 0; j < m; ++j) {
+            double *fw = &fwd[((size_t)cl * m + j) * 4], *bw = &bwd[((size_t)cl * m + j) * 2];
+            fw[0] = f[j]; fw[1] = r[j]; fw[2] = pi[j]; fw[3] = 0.0;
+            bw[0] = saf[j]; bw[1] = scf[j];
+        }
     }
 
     // stencil taps: interior row (any row at least 4 from a closed end) and the edge rows
@@ -204,6 +218,26 @@ static tds_status build_operator(const tds_plan *p, const LineOperator &L, int w
         wf[i] = 1.0 / den;
         cp[i] = (i < R - 1) ? wf[i] * sup[i] : 0.0;
     }
+    // Decoupled form (the communication phase of Sec. 4.2 / Fig. alg): boundary k joins L_{k-1}
+    // and F_k.  It is exact for P = 1 (both couplings of the single chunk's ends are kept, summed)
+    // and for the paper-drop mode; for P >= 2 in exact mode it is used only when the couplings
+    // it ignores (F_k <-> L_k within a chunk) are below kDecoupleTol.
+    {
+        double dropped = 0.0;
+        for (int k = 0; k < P; ++k)
+            dropped = std::fmax(dropped, std::fmax(std::fabs(sup[2 * k]), std::fabs(sub[2 * k + 1])));
+        op.red_decoupled = (P == 1) || p->mode == TDS_REDUCED_PAPER_DROP || dropped <= kDecoupleTol;
+        double *ba = &red[(size_t)kRedBa * R], *bc = &red[(size_t)kRedBc * R];
+        double *binv = &red[(size_t)kRedBinv * R];
+        for (int k = 0; k < P; ++k) {
+            const int prev = (k - 1 + P) % P;
+            double a = sub[2 * k], c = sup[2 * prev + 1];
+            if (P == 1) { a += sup[0]; c += sub[1]; }
+            const double det = 1.0 - a * c;
+            if (op.red_decoupled && (det == 0.0 || !std::isfinite(det))) return TDS_ERR_ARG;
+            ba[k] = a; bc[k] = c; binv[k] = 1.0 / det;
+        }
+    }
     if (periodic) {
         std::vector<double> u(R, 0.0);
         u[0] = gamma; u[R - 1] += sup[R - 1];
@@ -223,29 +257,40 @@ tds_status build_plan(tds_plan *p) {
     scheme_line(p->n, p->order, periodic, p->h, L);
     transpose_line(p->n, periodic, L, LT);
 
-    std::vector<double> rows[2], n1s[2], red[2], sub[2], sup[2];
+    std::vector<double> rows[2], n1s[2], red[2], sub[2], sup[2], fwd[2], bwd[2];
     for (int w = 0; w < 2; ++w) {
         tds_status s = build_operator(p, w ? LT : L, w, p->op[w], rows[w], n1s[w], red[w],
-                                      sub[w], sup[w]);
+                                      sub[w], sup[w], fwd[w], bwd[w]);
         if (s != TDS_OK) return s;
     }
 
-    // one device allocation: [rows64 | rows32 | n1 | red] per operator, 256-byte aligned parts
+    // one device allocation per plan, 256-byte aligned parts per operator:
+    // [rows64 | rows32 | n1 | red | fwd64 | fwd32 | bwd64 | bwd32]
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t off[2][4], total = 0;
+    size_t off[2][8], total = 0;
     for (int w = 0; w < 2; ++w) {
         off[w][0] = total; total = align(total + rows[w].size() * sizeof(double));
         off[w][1] = total; total = align(total + rows[w].size() * sizeof(float));
         off[w][2] = total; total = align(total + n1s[w].size() * sizeof(double));
         off[w][3] = total; total = align(total + red[w].size() * sizeof(double));
+        off[w][4] = total; total = align(total + fwd[w].size() * sizeof(double));
+        off[w][5] = total; total = align(total + fwd[w].size() * sizeof(float));
+        off[w][6] = total; total = align(total + bwd[w].size() * sizeof(double));
+        off[w][7] = total; total = align(total + bwd[w].size() * sizeof(float));
     }
     std::vector<unsigned char> host(total, 0);
+    auto put64 = [&](size_t o, const std::vector<double> &v) {
+        std::memcpy(&host[o], v.data(), v.size() * sizeof(double));
+    };
+    auto put32 = [&](size_t o, const std::vector<double> &v) {
+        float *d = reinterpret_cast<float *>(&host[o]);
+        for (size_t i = 0; i < v.size(); ++i) d[i] = (float)v[i];
+    };
     for (int w = 0; w < 2; ++w) {
-        std::memcpy(&host[off[w][0]], rows[w].data(), rows[w].size() * sizeof(double));
-        float *r32 = reinterpret_cast<float *>(&host[off[w][1]]);
-        for (size_t i = 0; i < rows[w].size(); ++i) r32[i] = (float)rows[w][i];
-        std::memcpy(&host[off[w][2]], n1s[w].data(), n1s[w].size() * sizeof(double));
-        std::memcpy(&host[off[w][3]], red[w].data(), red[w].size() * sizeof(double));
+        put64(off[w][0], rows[w]); put32(off[w][1], rows[w]);
+        put64(off[w][2], n1s[w]); put64(off[w][3], red[w]);
+        put64(off[w][4], fwd[w]); put32(off[w][5], fwd[w]);
+        put64(off[w][6], bwd[w]); put32(off[w][7], bwd[w]);
     }
     void *d = nullptr;
     const cudaError_t e = cudaMalloc(&d, total);
@@ -268,6 +313,10 @@ tds_status build_plan(tds_plan *p) {
         p->op[w].row32 = reinterpret_cast<const float *>(base + off[w][1]);
         p->op[w].n1 = reinterpret_cast<const double *>(base + off[w][2]);
         p->op[w].red = reinterpret_cast<const double *>(base + off[w][3]);
+        p->op[w].fwd64 = reinterpret_cast<const double *>(base + off[w][4]);
+        p->op[w].fwd32 = reinterpret_cast<const float *>(base + off[w][5]);
+        p->op[w].bwd64 = reinterpret_cast<const double *>(base + off[w][6]);
+        p->op[w].bwd32 = reinterpret_cast<const float *>(base + off[w][7]);
         p->red_sub_host[w] = hm + (size_t)(2 * w) * R;
         p->red_sup_host[w] = hm + (size_t)(2 * w + 1) * R;
         std::memcpy(p->red_sub_host[w], sub[w].data(), sizeof(double) * R);
