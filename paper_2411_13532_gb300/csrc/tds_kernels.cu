@@ -69,6 +69,24 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// TMA bulk copy shared -> global (bytes % 16 == 0, 16-byte aligned), tracked by bulk groups.
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                 ::"l"(dst), "r"(smem_u32(src)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Wait until every committed bulk store has finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -210,6 +228,12 @@ __device__ __forceinline__ Pack<T, V> pick3v(int i, const Pack<T, V> &a0, const 
     return (i == 0) ? a0 : (i == 1 ? a1 : a2);
 }
 
+// Whether the resident kernels store a finished tile with one TMA bulk copy (FP32, where the
+// sweep is HBM-bound) or each thread stores its rows directly (FP64, where the sweep is bound by
+// the FP64 pipe and the direct stores overlap it).
+template <typename T>
+constexpr bool kBulkStore = (sizeof(T) == 4);
+
 // Plan row records of the resident sweep (see DevOp::fwd64 / bwd64).
 template <typename T>
 struct FwdRec {
@@ -302,20 +326,28 @@ __device__ __forceinline__ void fwd_interior(const DevOp &op, int cls, T *row, i
     const int m = op.m;
     const T t0 = T(op.tap[3]), t1 = T(op.tap[4]), t2 = T(op.tap[5]);
     const int jm = (je < m - 2) ? je : m - 2;
+    if (jb < jm) {
+        // one row ahead: the next tile row and plan record are in flight during this row
+        Pack<T, V> wn = ldv<T, V>(row + (size_t)(jb + 2) * kSZ);
+        FwdRec<T> qn = ld_fwd<T>(op, cls, jb);
 #pragma unroll 4
-    for (int j = jb; j < jm; ++j) {
-        w[4] = ldv<T, V>(row + (size_t)(j + 2) * kSZ);
-        T sv[V];
-        istencil<T, V, SYM>(t0, t1, t2, w, sv);
-        const FwdRec<T> q = ld_fwd<T>(op, cls, j);
+        for (int j = jb; j < jm; ++j) {
+            w[4] = wn;
+            const FwdRec<T> q = qn;
+            const int jn = (j + 1 < jm) ? j + 1 : j;
+            wn = ldv<T, V>(row + (size_t)(jn + 2) * kSZ);
+            qn = ld_fwd<T>(op, cls, jn);
+            T sv[V];
+            istencil<T, V, SYM>(t0, t1, t2, w, sv);
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            dprev.v[i] = q.f * (sv[i] - q.r * dprev.v[i]);
-            S.v[i] = fma(q.pi, dprev.v[i], S.v[i]);
+            for (int i = 0; i < V; ++i) {
+                dprev.v[i] = q.f * (sv[i] - q.r * dprev.v[i]);
+                S.v[i] = fma(q.pi, dprev.v[i], S.v[i]);
+            }
+            stv<T, V>(row + (size_t)j * kSZ, dprev);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
         }
-        stv<T, V>(row + (size_t)j * kSZ, dprev);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
     }
     for (int j = (jb > m - 2 ? jb : m - 2); j < je; ++j) {
         w[4] = (j + 2 - m == 0) ? ha[0] : ha[1];
@@ -360,57 +392,59 @@ __device__ __forceinline__ void fwd_edge(const DevOp &op, int cls, T *row, int j
     }
 }
 
-// x = B^T y over this chunk's rows [jb, je) with the interior taps; the tile holds y for the
-// whole line (read only), results go to `orow`.
+// In-place x = B^T y over rows [jb, je) of this chunk with the interior taps: w[0..3] holds
+// y[j-2..j+1] on entry; y[j+2] comes from the tile while inside the chunk (rows ahead of the
+// window are not yet overwritten), then from the halo after it.
 template <typename T, int V, bool SYM>
-__device__ __forceinline__ void bt_interior(const DevOp &op, const T *tile, T *orow, int J0, int jb,
-                                            int je, int c) {
+__device__ __forceinline__ void bt_interior_inplace(const DevOp &op, T *row, int jb, int je,
+                                                    Pack<T, V> (&w)[5], const Pack<T, V> (&ha)[2]) {
     const int m = op.m;
     const T t0 = T(op.tap[3]), t1 = T(op.tap[4]), t2 = T(op.tap[5]);
-    Pack<T, V> w[5];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) w[i] = ld_row<T, V>(op, tile, J0 + jb - 2 + i, c);
     const int jm = (je < m - 2) ? je : m - 2;
 #pragma unroll 4
     for (int j = jb; j < jm; ++j) {
-        w[4] = ldv<T, V>(tile + (size_t)(J0 + j + 2) * kSZ + c);
+        w[4] = ldv<T, V>(row + (size_t)(j + 2) * kSZ);
         T sv[V];
         istencil<T, V, SYM>(t0, t1, t2, w, sv);
         Pack<T, V> x;
 #pragma unroll
         for (int i = 0; i < V; ++i) x.v[i] = sv[i];
-        stv<T, V>(orow + (size_t)j * kSZ, x);
+        stv<T, V>(row + (size_t)j * kSZ, x);
 #pragma unroll
         for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
     }
     for (int j = (jb > m - 2 ? jb : m - 2); j < je; ++j) {
-        w[4] = ld_row<T, V>(op, tile, J0 + j + 2, c);
+        w[4] = (j + 2 - m == 0) ? ha[0] : ha[1];
         T sv[V];
         istencil<T, V, SYM>(t0, t1, t2, w, sv);
         Pack<T, V> x;
 #pragma unroll
         for (int i = 0; i < V; ++i) x.v[i] = sv[i];
-        stv<T, V>(orow + (size_t)j * kSZ, x);
+        stv<T, V>(row + (size_t)j * kSZ, x);
 #pragma unroll
         for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
     }
 }
 
+// In-place closure rows of the B^T pass: local rows j0..j0+3 with 7-point windows from the
+// scratch rows (x[i] = y[Jx + i], entries outside the line zero).
 template <typename T, int V>
-__device__ __forceinline__ void bt_edge(const DevOp &op, const T *tile, T *orow, int J0, int j0,
-                                        int e0, int c) {
+__device__ __forceinline__ void bt_edge_inplace(const DevOp &op, T *row, int j0, int e0, const T *xs,
+                                                int c, int xlo, int xhi) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-        const int J = J0 + j0 + t;
         Pack<T, V> w7[kTaps];
 #pragma unroll
-        for (int o = 0; o < kTaps; ++o) w7[o] = ld_row<T, V>(op, tile, J - 3 + o, c);
+        for (int o = 0; o < kTaps; ++o) {
+            const int x = t + o + xlo;
+            w7[o] = (x >= 0 && x < xhi) ? ldv<T, V>(xs + (size_t)x * kSZ + c) : zero_pack<T, V>();
+        }
         T sv[V];
         estencil<T, V>(op, e0 + t, w7, sv);
         Pack<T, V> x;
 #pragma unroll
         for (int i = 0; i < V; ++i) x.v[i] = sv[i];
-        stv<T, V>(orow + (size_t)(j0 + t) * kSZ, x);
+        stv<T, V>(row + (size_t)(j0 + t) * kSZ, x);
     }
 }
 
@@ -510,7 +544,9 @@ __device__ __forceinline__ void group_sweep(const DevOp &op, T *tile, T *xs, dou
         u.v[i] = T(ends[(size_t)(2 * k + 1) * kSZ + c + i]);
     }
     T *orow = og + (size_t)J0 * kSZ + c;
-    T *dst = ADJ ? row : orow;   // adjoint: y stays in the tile for the B^T pass
+    // the result stays in the tile: the kernel stores the whole tile with one TMA bulk copy
+    // (forward operator), or the B^T pass reads it (adjoint)
+    T *dst = row;
     stv<T, V>(dst + (size_t)(m - 1) * kSZ, u);
 #pragma unroll 4
     for (int j = m - 2; j >= 1; --j) {
@@ -522,15 +558,34 @@ __device__ __forceinline__ void group_sweep(const DevOp &op, T *tile, T *xs, dou
         stv<T, V>(dst + (size_t)j * kSZ, u);
     }
     stv<T, V>(dst, F);
-    if (!ADJ) return;
-
-    // ---- adjoint: x = B^T y ----
-    __syncthreads();
-    const int jb = first_edge ? 4 : 0, je = last_edge ? m - 4 : m;
-    if (first_edge) bt_edge<T, V>(op, tile, orow, J0, 0, 0, c);
-    if (op.symmetric > 0) bt_interior<T, V, true>(op, tile, orow, J0, jb, je, c);
-    else bt_interior<T, V, false>(op, tile, orow, J0, jb, je, c);
-    if (last_edge) bt_edge<T, V>(op, tile, orow, J0, m - 4, kEdgeRows, c);
+    if (ADJ) {
+        // ---- adjoint: x = B^T y, in place, with the same halo scheme as the forward stencil ----
+        __syncthreads();
+        Pack<T, V> yb[2], ya[2];
+        read_halo<T, V>(op, tile, xs, k, c, yb, ya);
+        __syncthreads();
+        const int jb = first_edge ? 4 : 0, je = last_edge ? m - 4 : m;
+        if (first_edge) bt_edge_inplace<T, V>(op, row, 0, 0, xs, c, -3, kTaps);
+        Pack<T, V> w[5];
+        if (first_edge) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[i] = ldv<T, V>(xs + (size_t)(2 + i) * kSZ + c);
+        } else {
+            w[0] = yb[0]; w[1] = yb[1];
+            w[2] = ldv<T, V>(row); w[3] = ldv<T, V>(row + kSZ);
+        }
+        if (op.symmetric > 0) bt_interior_inplace<T, V, true>(op, row, jb, je, w, ya);
+        else bt_interior_inplace<T, V, false>(op, row, jb, je, w, ya);
+        if (last_edge) bt_edge_inplace<T, V>(op, row, m - 4, kEdgeRows, xs + (size_t)kTaps * kSZ, c, 0, kTaps);
+    }
+    // the result is in the tile: make this thread's writes visible to the kernel's bulk store,
+    // or store the rows directly
+    if (kBulkStore<T>) {
+        fence_async_smem();
+    } else {
+#pragma unroll 4
+        for (int j = 0; j < m; ++j) stv<T, V>(orow + (size_t)j * kSZ, ldv<T, V>(row + (size_t)j * kSZ));
+    }
     (void)n;
 }
 
@@ -588,6 +643,14 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_co
         return;
     }
     group_sweep<T, V, ADJ>(op, tile, xs, ends, out + gofs, k, c, hb, ha);
+    if (kBulkStore<T>) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            bulk_s2g(out + gofs, tile, (uint32_t)tile_bytes_of(n, sizeof(T)));
+            bulk_commit();
+            bulk_wait_read();   // shared memory must stay valid until the copy has read it
+        }
+    }
 }
 
 // Persistent variant: each CTA walks groups blockIdx.x, +gridDim.x, ... through `nbuf` tile
@@ -644,15 +707,22 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_pipe(const __gr
         group_sweep<T, V, ADJ>(op, tile, xs, ends, out + (size_t)g * tile_elems, k, c, hb, ha);
         __syncthreads();   // every thread is done with this tile, the scratch rows and `ends`
         if (threadIdx.x == 0) {
+            if (kBulkStore<T>) {
+                bulk_s2g(out + (size_t)g * tile_elems, tile, tile_bytes);
+                bulk_commit();
+            }
             const long long gn = g + (long long)nbuf * gridDim.x;
             if (gn < G) {
-                // generic-proxy accesses of the buffer are ordered before the async refill
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                // the buffer is refilled only after the store has read it, and generic-proxy
+                // accesses are ordered before the async refill
+                if (kBulkStore<T>) bulk_wait_read();
+                fence_async_smem();
                 mbar_expect_tx(&bars[b], tile_bytes);
                 bulk_g2s(tile, in + (size_t)gn * tile_elems, tile_bytes, &bars[b]);
             }
         }
     }
+    if (kBulkStore<T> && threadIdx.x == 0) bulk_wait_read();
 }
 
 // ------------------------------------------------------------------------------------------
