@@ -38,10 +38,20 @@ METRIC = "Gpoints/s and % of HBM roofline per directional derivative, FP64 vs FP
 UNIT = "Gpoints/s"
 KERNEL_SRC = os.path.join(ROOT, "paper_2411_13532_gb300", "csrc", "tds_kernels.cu")
 
-# FP64 pipe operations per point of each directional operator as the kernels issue them
-# (interior rows): stencil (antisymmetric 4, symmetric 5), forward pass 2, backward pass 1,
-# substitution 2; the adjoint applies the transposed stencil after the substitution.
-FP64_OPS_PER_POINT = {"d1": 9, "d2": 10, "d1t": 9}
+def fp64_ops_per_point(op, m):
+    """FP64-pipe operations per interior point as the resident kernel issues them.
+
+    Forward row with f folded into the coefficients: 2 adds (the stencil differences or sums)
+    + 1 multiply + 2 FMAs (first derivative) or 3 FMAs (second: the centre tap); the adjoint's
+    forward row (identity right-hand side) is 1 multiply + 1 FMA and its B^T pass 4.  Back-
+    substitution: 1 FMA.  The accumulation S += pi_j d_j and the s^a_j F term of the back-
+    substitution are issued only on the rows before the plan's cut-off, where those weights,
+    decaying like lambda^j (lambda = 0.382 for alpha = 1/3, 0.188 for alpha = 2/11), fall
+    below 2^-60: about 44 and 25 rows."""
+    lam = {"d1": 0.38196601125, "d2": 0.18826230851, "d1t": 0.38196601125}[op]
+    cut = min(m, math.ceil(math.log(2.0 ** -60) / math.log(lam)))
+    extra = 2.0 * cut / m
+    return {"d1": 5.0 + 1.0, "d2": 6.0 + 1.0, "d1t": 2.0 + 1.0 + 4.0}[op] + extra
 
 
 def parse():
@@ -263,7 +273,7 @@ def run_ours(args, rank, world, local_rank):
         # 2 FP64 instructions per clock per SM x 152 SMs x sampled SM clock
         sm_mhz = clocks["sm_mhz"] or 2070.0
         peak = 2 * 152 * sm_mhz * 1e6 / 1e9
-        ach = FP64_OPS_PER_POINT[dom[1]] * npts / (dom_ms * 1e-3) / 1e9
+        ach = fp64_ops_per_point(dom[1], S // args.P) * npts / (dom_ms * 1e-3) / 1e9
         roofline = {"kernel": "/".join(str(k) for k in dom), "bound": "alu", "achieved": round(ach, 1),
                     "peak": round(peak, 1), "unit": "Gop/s (FP64 pipe)", "frac": round(ach / peak, 4),
                     "peak_source": "derived: 2 FP64 ops/clk/SM x 152 SMs x median SM clock",

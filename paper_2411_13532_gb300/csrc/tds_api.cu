@@ -113,7 +113,7 @@ tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_dir dir, 
         }
     }
     // lines per thread in the resident kernels; TDS_RESIDENT_LANES overrides (tuning)
-    p->lanes = (dtype == TDS_F32) ? 2 : 1;
+    p->lanes = 1;
     if (const char *e = std::getenv("TDS_RESIDENT_LANES")) {
         const int v = std::atoi(e);
         if (v == 1 || v == 2 || (v == 4 && dtype == TDS_F32)) p->lanes = v;

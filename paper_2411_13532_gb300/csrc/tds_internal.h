@@ -54,6 +54,14 @@ struct DevOp {
     const float *fwd32;
     const double *bwd64;
     const float *bwd32;
+    // interior rows of the forward pass with f_j folded in: {f t_0, f t_1, f t_2, f r} so that
+    // d_j = c1 (v[j+1] -+ v[j-1]) + c2 (v[j+2] -+ v[j-2]) (+ c0 v[j]) - g d_{j-1}; for the
+    // adjoint (identity right-hand side) {f, 0, 0, f r}.  [ncls][m] records.
+    const double *ifw64;
+    const float *ifw32;
+    // per chunk class: rows j >= jpi carry |pi_j| below the cut-off and rows j >= jsa carry
+    // |s^a_j| below it (2^-60 for FP64 sweeps, 2^-30 for FP32): those terms are not issued
+    int jpi64[3], jsa64[3], jpi32[3], jsa32[3];
     const double *n1;     // [ncls] row-0 normaliser 1/(1 - s^c_1 s^a_2) (Algorithm 4, last lines)
     const double *red;    // [kNumRedArrays][2P]
     int red_cyclic;

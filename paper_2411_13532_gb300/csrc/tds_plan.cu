@@ -141,7 +141,8 @@ static tds_status build_operator(const tds_plan *p, const LineOperator &L, int w
                                  DevOp &op, std::vector<double> &rows,
                                  std::vector<double> &n1s, std::vector<double> &red,
                                  std::vector<double> &sub, std::vector<double> &sup,
-                                 std::vector<double> &fwd, std::vector<double> &bwd) {
+                                 std::vector<double> &fwd, std::vector<double> &bwd,
+                                 std::vector<double> &ifw) {
     const int n = p->n, m = p->m, P = p->P;
     const bool periodic = (p->bc == TDS_BC_PERIODIC);
     std::memset(&op, 0, sizeof(op));
@@ -175,7 +176,6 @@ static tds_status build_operator(const tds_plan *p, const LineOperator &L, int w
             bw[0] = saf[j]; bw[1] = scf[j];
         }
     }
-
     // stencil taps: interior row (any row at least 4 from a closed end) and the edge rows
     const int mid = n / 2;
     for (int o = 0; o < kTaps; ++o) op.tap[o] = L.taps[(size_t)mid * kTaps + o];
@@ -185,6 +185,29 @@ static tds_status build_operator(const tds_plan *p, const LineOperator &L, int w
                 op.edge[e][o] = L.taps[(size_t)e * kTaps + o];
                 op.edge[kEdgeRows + e][o] = L.taps[(size_t)(n - kEdgeRows + e) * kTaps + o];
             }
+    }
+
+    // interior forward records with f folded in, and the cut-off rows of pi and s^a
+    ifw.assign((size_t)nc * m * 4, 0.0);
+    for (int cl = 0; cl < nc; ++cl) {
+        for (int j = 0; j < m; ++j) {
+            const double f = fwd[((size_t)cl * m + j) * 4], r = fwd[((size_t)cl * m + j) * 4 + 1];
+            double *c = &ifw[((size_t)cl * m + j) * 4];
+            if (which == 0) { c[0] = f * op.tap[3]; c[1] = f * op.tap[4]; c[2] = f * op.tap[5]; }
+            else { c[0] = f; c[1] = 0.0; c[2] = 0.0; }
+            c[3] = f * r;
+        }
+        auto cutoff = [&](int idx, double tol) {   // first row after which |x_j| <= tol
+            int j0 = m;
+            while (j0 > 0 && std::fabs(idx == 0 ? fwd[((size_t)cl * m + j0 - 1) * 4 + 2]
+                                                : bwd[((size_t)cl * m + j0 - 1) * 2]) <= tol)
+                --j0;
+            return j0;
+        };
+        op.jpi64[cl] = cutoff(0, std::ldexp(1.0, -60));
+        op.jsa64[cl] = cutoff(1, std::ldexp(1.0, -60));
+        op.jpi32[cl] = cutoff(0, std::ldexp(1.0, -30));
+        op.jsa32[cl] = cutoff(1, std::ldexp(1.0, -30));
     }
 
     // reduced chunk-end system, unknowns F_0, L_0, F_1, L_1, ... (2P)
@@ -257,17 +280,17 @@ tds_status build_plan(tds_plan *p) {
     scheme_line(p->n, p->order, periodic, p->h, L);
     transpose_line(p->n, periodic, L, LT);
 
-    std::vector<double> rows[2], n1s[2], red[2], sub[2], sup[2], fwd[2], bwd[2];
+    std::vector<double> rows[2], n1s[2], red[2], sub[2], sup[2], fwd[2], bwd[2], ifw[2];
     for (int w = 0; w < 2; ++w) {
         tds_status s = build_operator(p, w ? LT : L, w, p->op[w], rows[w], n1s[w], red[w],
-                                      sub[w], sup[w], fwd[w], bwd[w]);
+                                      sub[w], sup[w], fwd[w], bwd[w], ifw[w]);
         if (s != TDS_OK) return s;
     }
 
     // one device allocation per plan, 256-byte aligned parts per operator:
-    // [rows64 | rows32 | n1 | red | fwd64 | fwd32 | bwd64 | bwd32]
+    // [rows64 | rows32 | n1 | red | fwd64 | fwd32 | bwd64 | bwd32 | ifw64 | ifw32]
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t off[2][8], total = 0;
+    size_t off[2][10], total = 0;
     for (int w = 0; w < 2; ++w) {
         off[w][0] = total; total = align(total + rows[w].size() * sizeof(double));
         off[w][1] = total; total = align(total + rows[w].size() * sizeof(float));
@@ -277,6 +300,8 @@ tds_status build_plan(tds_plan *p) {
         off[w][5] = total; total = align(total + fwd[w].size() * sizeof(float));
         off[w][6] = total; total = align(total + bwd[w].size() * sizeof(double));
         off[w][7] = total; total = align(total + bwd[w].size() * sizeof(float));
+        off[w][8] = total; total = align(total + ifw[w].size() * sizeof(double));
+        off[w][9] = total; total = align(total + ifw[w].size() * sizeof(float));
     }
     std::vector<unsigned char> host(total, 0);
     auto put64 = [&](size_t o, const std::vector<double> &v) {
@@ -291,6 +316,7 @@ tds_status build_plan(tds_plan *p) {
         put64(off[w][2], n1s[w]); put64(off[w][3], red[w]);
         put64(off[w][4], fwd[w]); put32(off[w][5], fwd[w]);
         put64(off[w][6], bwd[w]); put32(off[w][7], bwd[w]);
+        put64(off[w][8], ifw[w]); put32(off[w][9], ifw[w]);
     }
     void *d = nullptr;
     const cudaError_t e = cudaMalloc(&d, total);
@@ -317,6 +343,8 @@ tds_status build_plan(tds_plan *p) {
         p->op[w].fwd32 = reinterpret_cast<const float *>(base + off[w][5]);
         p->op[w].bwd64 = reinterpret_cast<const double *>(base + off[w][6]);
         p->op[w].bwd32 = reinterpret_cast<const float *>(base + off[w][7]);
+        p->op[w].ifw64 = reinterpret_cast<const double *>(base + off[w][8]);
+        p->op[w].ifw32 = reinterpret_cast<const float *>(base + off[w][9]);
         p->red_sub_host[w] = hm + (size_t)(2 * w) * R;
         p->red_sup_host[w] = hm + (size_t)(2 * w + 1) * R;
         std::memcpy(p->red_sub_host[w], sub[w].data(), sizeof(double) * R);

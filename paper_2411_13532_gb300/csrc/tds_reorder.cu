@@ -32,39 +32,66 @@ __device__ __forceinline__ size_t xlayout_row(int x, int yb, int z, int nx, int 
     return (size_t)R * ((size_t)x + (size_t)nx * ((size_t)yb + yg * z));
 }
 
-// Row permutation between two x-run layouts: one warp per row; grid (ceil(nx/32/8), ny, nz).
+// Row permutation between two x-run layouts, in 16-byte vectors: a block copies the rows of
+// kRowsY consecutive y at one z; each thread moves kVecPerThread independent vectors (all
+// loads issued before the stores, so several are in flight per thread).
+constexpr int kRowsY = 8;
+constexpr int kVecPerThread = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_rows(const T *__restrict__ in, T *__restrict__ out, int nx,
                                              int ny, int nz, tds_layout from, tds_layout to) {
-    const int xb = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (xb >= nx / R) return;
-    const int y = blockIdx.y, z = blockIdx.z, t = threadIdx.x & 31;
-    out[xrun_row(to, xb, y, z, nx, ny, nz) + t] = __ldg(in + xrun_row(from, xb, y, z, nx, ny, nz) + t);
+    constexpr int vpr = R * sizeof(T) / 16;      // 16-byte vectors per row
+    constexpr int epv = 16 / sizeof(T);          // elements per vector
+    const int xg = nx / R, z = blockIdx.y, y0 = blockIdx.x * kRowsY;
+    const int ylim = (ny - y0 < kRowsY) ? ny - y0 : kRowsY;
+    const int total = ylim * xg * vpr;
+    for (int base = threadIdx.x; base < total; base += 256 * kVecPerThread) {
+        float4 v[kVecPerThread];
+        size_t dst[kVecPerThread];
+#pragma unroll
+        for (int u = 0; u < kVecPerThread; ++u) {
+            const int idx = base + u * 256;
+            dst[u] = (size_t)-1;
+            if (idx < total) {
+                const int vi = idx % vpr, rowi = idx / vpr;
+                const int xb = rowi % xg, y = y0 + rowi / xg;
+                v[u] = __ldg(reinterpret_cast<const float4 *>(in + xrun_row(from, xb, y, z, nx, ny, nz) + vi * epv));
+                dst[u] = xrun_row(to, xb, y, z, nx, ny, nz) + vi * epv;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVecPerThread; ++u)
+            if (dst[u] != (size_t)-1) *reinterpret_cast<float4 *>(out + dst[u]) = v[u];
+    }
 }
 
-// 32 x 32 (x, y) tile transpose between the x layout and an x-run layout at fixed z.
-// grid (nx/32, ny/32, nz), block (32, 8).  to_x selects the direction.
+// 32 x 32 (x, y) tile transposes between the x layout and an x-run layout, kTilesZ
+// consecutive z per block (all loads of a block are issued before its stores).
+// grid (nx/32, ny/32, ceil(nz/kTilesZ)), block (32, 8).  to_x selects the direction.
+constexpr int kTilesZ = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_transpose(const T *__restrict__ in, T *__restrict__ out,
                                                   int nx, int ny, int nz, tds_layout other,
                                                   int to_x) {
-    __shared__ T tile[R][R + 1];
-    const int xb = blockIdx.x, yb = blockIdx.y, z = blockIdx.z;
+    __shared__ T tile[kTilesZ][R][R + 1];
+    const int xb = blockIdx.x, yb = blockIdx.y, z0 = blockIdx.z * kTilesZ;
     const int t = threadIdx.x, r0 = threadIdx.y;
-    if (to_x) {
-        // read rows y = 32 yb + i of the x-run layout: element t is x = 32 xb + t
+    const int nt = (nz - z0 < kTilesZ) ? nz - z0 : kTilesZ;
+    for (int q = 0; q < nt; ++q) {
+        const int z = z0 + q;
         for (int i = r0; i < R; i += 8)
-            tile[i][t] = __ldg(in + xrun_row(other, xb, yb * R + i, z, nx, ny, nz) + t);
-        __syncthreads();
-        // write rows x = 32 xb + i of the x layout: element t is y = 32 yb + t
-        for (int i = r0; i < R; i += 8)
-            out[xlayout_row(xb * R + i, yb, z, nx, ny) + t] = tile[t][i];
-    } else {
-        for (int i = r0; i < R; i += 8)
-            tile[i][t] = __ldg(in + xlayout_row(xb * R + i, yb, z, nx, ny) + t);
-        __syncthreads();
-        for (int i = r0; i < R; i += 8)
-            out[xrun_row(other, xb, yb * R + i, z, nx, ny, nz) + t] = tile[t][i];
+            tile[q][i][t] = to_x ? __ldg(in + xrun_row(other, xb, yb * R + i, z, nx, ny, nz) + t)
+                                 : __ldg(in + xlayout_row(xb * R + i, yb, z, nx, ny) + t);
+    }
+    __syncthreads();
+    for (int q = 0; q < nt; ++q) {
+        const int z = z0 + q;
+        for (int i = r0; i < R; i += 8) {
+            if (to_x) out[xlayout_row(xb * R + i, yb, z, nx, ny) + t] = tile[q][t][i];
+            else out[xrun_row(other, xb, yb * R + i, z, nx, ny, nz) + t] = tile[q][t][i];
+        }
     }
 }
 
@@ -74,10 +101,10 @@ tds_status launch_t(const void *in, void *out, int nx, int ny, int nz, tds_layou
     const T *src = static_cast<const T *>(in);
     T *dst = static_cast<T *>(out);
     if (from != TDS_LAYOUT_X && to != TDS_LAYOUT_X) {
-        dim3 grid((unsigned)((nx / R + 7) / 8), (unsigned)ny, (unsigned)nz);
+        dim3 grid((unsigned)((ny + kRowsY - 1) / kRowsY), (unsigned)nz);
         k_rows<T><<<grid, 256, 0, st>>>(src, dst, nx, ny, nz, from, to);
     } else {
-        dim3 grid((unsigned)(nx / R), (unsigned)(ny / R), (unsigned)nz);
+        dim3 grid((unsigned)(nx / R), (unsigned)(ny / R), (unsigned)((nz + kTilesZ - 1) / kTilesZ));
         const int to_x = (to == TDS_LAYOUT_X);
         k_transpose<T><<<grid, dim3(32, 8), 0, st>>>(src, dst, nx, ny, nz, to_x ? from : to, to_x);
     }

@@ -1,0 +1,700 @@
+// tds_resident.cu -- the resident DistD2 kernels (Sec. 4.2): one CTA holds a whole group of 32
+// lines (all P chunks) in shared memory, so the field is read once and written once.
+//
+// Per group: TMA bulk copies bring the n x 32 tile into shared memory (one mbarrier per chunk,
+// bounded waits); chunk k is swept by 32/V threads, each carrying V adjacent lines; then
+//   forward  : stencil right-hand side fused into the modified-Thomas forward elimination
+//              (Algorithm 5), in place, accumulating the back-swept row 1 as S = sum pi_j d_j
+//              so that row 0 is decoupled without a separate backward pass;
+//   reduced  : the chunk-end system in FP64 (communication phase; decoupled 2x2 boundary
+//              systems when the couplings they ignore are below 2^-64, else the full system);
+//   back-substitution: u_{m-1} = L, u_j = d_j - s^a_j F - s^c_j u_{j+1}, u_0 = F -- the
+//              backward pass and Algorithm 6 in one reverse sweep;
+//   adjoint  : the same on A^T with the identity right-hand side, then x = B^T y in place;
+//   output   : FP32 tiles leave with one TMA bulk store; FP64 tiles with per-thread stores.
+//
+// The sweep is written once over storage/arithmetic traits (FP32, FP64).
+#include "tds_device.cuh"
+
+namespace tds {
+
+// Device-side status word: a bounded wait that gives up records TDS_ERR_TIMEOUT here.
+__device__ int g_device_status = 0;
+
+namespace {
+
+__device__ __forceinline__ void record_timeout() { atomicExch(&g_device_status, (int)TDS_ERR_TIMEOUT); }
+
+// a * b + c
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return ::fma(a, b, c); }
+
+// ------------------------------------------------------------------------------------------
+// Storage / arithmetic traits of the sweep.
+//   S: element type in HBM and in the tile; A: arithmetic type of the sweep.
+//   in  : a raw input row (u, or g for the adjoint) -> A
+//   mid : an intermediate value (d_j, y_j) kept in the tile slot of its row
+//   out : a final value into the tile slot, as S
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct TrNative {
+    using S = T;
+    using A = T;
+    static __device__ __forceinline__ A from_d(double x) { return A(x); }
+    static __device__ __forceinline__ double to_d(A x) { return double(x); }
+    template <int V>
+    static __device__ __forceinline__ Pack<A, V> ld_in(const DevOp &, const S *p, int &) { return ldv<T, V>(p); }
+    template <int V>
+    static __device__ __forceinline__ Pack<A, V> ld_mid(const S *p) { return ldv<T, V>(p); }
+    template <int V>
+    static __device__ __forceinline__ void st_mid(S *p, const Pack<A, V> &v) { stv<T, V>(p, v); }
+    template <int V>
+    static __device__ __forceinline__ void st_out(const DevOp &, S *p, const Pack<A, V> &v) { stv<T, V>(p, v); }
+    static __device__ __forceinline__ A tap(const DevOp &op, int i) { return A(op.tap[i]); }
+    static __device__ __forceinline__ A edge(const DevOp &op, int e, int o) { return A(op.edge[e][o]); }
+    static __device__ __forceinline__ void fwd(const DevOp &op, int cls, int j, A &f, A &r, A &pi) {
+        const size_t i = (size_t)cls * op.m + j;
+        if constexpr (sizeof(T) == 4) {
+            const float4 x = __ldg(reinterpret_cast<const float4 *>(op.fwd32) + i);
+            f = x.x; r = x.y; pi = x.z;
+        } else {
+            const double2 x = __ldg(reinterpret_cast<const double2 *>(op.fwd64) + 2 * i);
+            f = x.x; r = x.y; pi = __ldg(op.fwd64 + 4 * i + 2);
+        }
+    }
+    static __device__ __forceinline__ void bwd(const DevOp &op, int cls, int j, A &sa, A &sc) {
+        const size_t i = (size_t)cls * op.m + j;
+        if constexpr (sizeof(T) == 4) {
+            const float2 x = __ldg(reinterpret_cast<const float2 *>(op.bwd32) + i);
+            sa = x.x; sc = x.y;
+        } else {
+            const double2 x = __ldg(reinterpret_cast<const double2 *>(op.bwd64) + i);
+            sa = x.x; sc = x.y;
+        }
+    }
+    // folded interior record {c0, c1, c2, g} and the weight pi_j
+    static __device__ __forceinline__ void ifw(const DevOp &op, int cls, int j, A &c0, A &c1, A &c2, A &g) {
+        const size_t i = (size_t)cls * op.m + j;
+        if constexpr (sizeof(T) == 4) {
+            const float4 x = __ldg(reinterpret_cast<const float4 *>(op.ifw32) + i);
+            c0 = x.x; c1 = x.y; c2 = x.z; g = x.w;
+        } else {
+            const double2 a = __ldg(reinterpret_cast<const double2 *>(op.ifw64) + 2 * i);
+            const double2 b = __ldg(reinterpret_cast<const double2 *>(op.ifw64) + 2 * i + 1);
+            c0 = a.x; c1 = a.y; c2 = b.x; g = b.y;
+        }
+    }
+    static __device__ __forceinline__ A pi(const DevOp &op, int cls, int j) {
+        const size_t i = (size_t)cls * op.m + j;
+        if constexpr (sizeof(T) == 4) return __ldg(op.fwd32 + 4 * i + 2);
+        else return __ldg(op.fwd64 + 4 * i + 2);
+    }
+    static __device__ __forceinline__ int jpi(const DevOp &op, int cls) {
+        return sizeof(T) == 4 ? op.jpi32[cls] : op.jpi64[cls];
+    }
+    static __device__ __forceinline__ int jsa(const DevOp &op, int cls) {
+        return sizeof(T) == 4 ? op.jsa32[cls] : op.jsa64[cls];
+    }
+};
+
+using TrF32 = TrNative<float>;
+using TrF64 = TrNative<double>;
+
+// Whether a finished tile leaves with one TMA bulk store (FP32: the sweep is HBM-bound) or
+// with per-thread stores that overlap the sweep (FP64 storage).
+template <typename Tr>
+constexpr bool kBulkStore = (sizeof(typename Tr::S) == 4);
+
+template <typename Tr, int V>
+__device__ __forceinline__ Pack<typename Tr::A, V> zero_a() {
+    Pack<typename Tr::A, V> r;
+#pragma unroll
+    for (int i = 0; i < V; ++i) r.v[i] = Tr::from_d(0.0);
+    return r;
+}
+
+// Interior stencil (offsets -2..2) of V lines from the window w[i] = v[J - 2 + i].
+template <typename A, int V, bool SYM>
+__device__ __forceinline__ void istencil(A t0, A t1, A t2, const Pack<A, V> (&w)[5], A (&s)[V]) {
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        if (SYM) s[i] = t0 * w[2].v[i] + t1 * (w[3].v[i] + w[1].v[i]) + t2 * (w[4].v[i] + w[0].v[i]);
+        else s[i] = t1 * (w[3].v[i] - w[1].v[i]) + t2 * (w[4].v[i] - w[0].v[i]);
+    }
+}
+
+// Closure-row stencil (offsets -3..3, closed lines) from w[i] = v[J - 3 + i]; e indexes the
+// plan's edge rows (0..3 = rows 0..3, 4..7 = rows n-4..n-1).
+template <typename Tr, int V>
+__device__ __forceinline__ void estencil(const DevOp &op, int e, const Pack<typename Tr::A, V> (&w)[kTaps],
+                                         typename Tr::A (&s)[V]) {
+    using A = typename Tr::A;
+#pragma unroll
+    for (int i = 0; i < V; ++i) s[i] = Tr::from_d(0.0);
+#pragma unroll
+    for (int o = 0; o < kTaps; ++o) {
+        const A c = Tr::edge(op, e, o);
+#pragma unroll
+        for (int i = 0; i < V; ++i) s[i] = s[i] + c * w[o].v[i];
+    }
+}
+
+// Row J of the line (cyclic wrap; zero outside a closed line) as an input or mid value.
+template <typename Tr, int V, bool MID>
+__device__ __forceinline__ Pack<typename Tr::A, V> ld_row(const DevOp &op, const typename Tr::S *tile,
+                                                          int J, int c, int &unsafe) {
+    const int r = line_row(op, J);
+    if (r < 0) return zero_a<Tr, V>();
+    const typename Tr::S *p = tile + (size_t)r * kSZ + c;
+    return MID ? Tr::template ld_mid<V>(p) : Tr::template ld_in<V>(op, p, unsafe);
+}
+
+// Captured before the CTA barrier that lets any thread overwrite the tile: the stencil halo of
+// this chunk (2 rows before, 2 after) in registers and, on closed lines, the first and last 7
+// rows of the line in the scratch rows xs[0..6], xs[7..13] (closure rows reach 3 points in and
+// the sweep works in place), copied as they are: raw inputs for the forward stencil, mid values
+// (MID) for the adjoint B^T pass.
+template <typename Tr, int V, bool MID>
+__device__ __forceinline__ void read_halo(const DevOp &op, const typename Tr::S *tile, typename Tr::S *xs,
+                                          int k, int c, Pack<typename Tr::A, V> (&hb)[2],
+                                          Pack<typename Tr::A, V> (&ha)[2], int &unsafe) {
+    using S = typename Tr::S;
+    const int J0 = k * op.m;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        hb[i] = ld_row<Tr, V, MID>(op, tile, J0 - 2 + i, c, unsafe);
+        ha[i] = ld_row<Tr, V, MID>(op, tile, J0 + op.m + i, c, unsafe);
+    }
+    if (!op.periodic) {
+        auto copy_row = [&](int src, int dst) {
+            const S *p = tile + (size_t)src * kSZ + c;
+            if (!MID) (void)Tr::template ld_in<V>(op, p, unsafe);   // range check of the input
+            stv<S, V>(xs + (size_t)dst * kSZ + c, ldv<S, V>(p));
+        };
+        if (k == 0)
+            for (int i = 0; i < kTaps; ++i) copy_row(i, i);
+        if (k == op.P - 1)
+            for (int i = 0; i < kTaps; ++i) copy_row(op.n - kTaps + i, kTaps + i);
+    }
+}
+
+// One row of the forward pass: d_j = f_j (s_j - r_j d_{j-1}), S += pi_j d_j, d_j -> tile.
+template <typename Tr, int V>
+__device__ __forceinline__ void fwd_row(const DevOp &op, int cls, int j, typename Tr::S *row,
+                                        const typename Tr::A (&sv)[V], Pack<typename Tr::A, V> &dprev,
+                                        Pack<typename Tr::A, V> &S) {
+    typename Tr::A f, r, pi;
+    Tr::fwd(op, cls, j, f, r, pi);
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        dprev.v[i] = f * (sv[i] - r * dprev.v[i]);
+        S.v[i] = mad(pi, dprev.v[i], S.v[i]);
+    }
+    Tr::template st_mid<V>(row + (size_t)j * kSZ, dprev);
+}
+
+// Interior row of the forward pass with f folded into the coefficients:
+// d_j = c1 (v[j+1] -+ v[j-1]) + c2 (v[j+2] -+ v[j-2]) (+ c0 v[j]) - g d_{j-1}, one FMA on the
+// recurrence; ACC: S += pi_j d_j (rows past the plan's cut-off skip it).
+template <typename Tr, int V, bool SYM, bool ACC>
+__device__ __forceinline__ void fwd_irow(const DevOp &op, int cls, int j, typename Tr::S *row,
+                                         const Pack<typename Tr::A, V> (&w)[5],
+                                         Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S) {
+    using A = typename Tr::A;
+    A c0, c1, c2, g;
+    Tr::ifw(op, cls, j, c0, c1, c2, g);
+    A p = A(0);
+    if (ACC) p = Tr::pi(op, cls, j);
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        A base = SYM ? mad(c0, w[2].v[i], mad(c1, w[3].v[i] + w[1].v[i], c2 * (w[4].v[i] + w[0].v[i])))
+                     : mad(c1, w[3].v[i] - w[1].v[i], c2 * (w[4].v[i] - w[0].v[i]));
+        dprev.v[i] = mad(-g, dprev.v[i], base);
+        if (ACC) S.v[i] = mad(p, dprev.v[i], S.v[i]);
+    }
+    Tr::template st_mid<V>(row + (size_t)j * kSZ, dprev);
+}
+
+// Interior forward rows [jb, je) reading v[j+2] from the tile (inside the chunk).
+template <typename Tr, int V, bool SYM, bool ACC>
+__device__ __forceinline__ void fwd_irows(const DevOp &op, int cls, typename Tr::S *row, int jb, int je,
+                                          Pack<typename Tr::A, V> (&w)[5], Pack<typename Tr::A, V> &dprev,
+                                          Pack<typename Tr::A, V> &S, int &unsafe) {
+#pragma unroll 4
+    for (int j = jb; j < je; ++j) {
+        w[4] = Tr::template ld_in<V>(op, row + (size_t)(j + 2) * kSZ, unsafe);
+        fwd_irow<Tr, V, SYM, ACC>(op, cls, j, row, w, dprev, S);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
+    }
+}
+
+// Interior rows [jb, je) of a stencil sweep over this chunk, in place: w[0..3] holds
+// v[j-2..j+1] on entry; v[j+2] is read from the tile while inside the chunk (rows ahead of the
+// window are not yet overwritten), then from the halo `ha`.  FWD: forward elimination rows
+// (input values); else B^T rows (mid values, result written as output).
+template <typename Tr, int V, bool SYM, bool FWD>
+__device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typename Tr::S *row, int jb, int je,
+                                               Pack<typename Tr::A, V> (&w)[5],
+                                               const Pack<typename Tr::A, V> (&ha)[2],
+                                               Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S,
+                                               int &unsafe) {
+    using A = typename Tr::A;
+    const int m = op.m;
+    const A t0 = Tr::tap(op, 3), t1 = Tr::tap(op, 4), t2 = Tr::tap(op, 5);
+    const int jm = (je < m - 2) ? je : m - 2;
+    if (FWD) {
+        // rows before the pi cut-off accumulate S, the rest do not
+        const int jp = Tr::jpi(op, cls);
+        const int j1 = (jp < jb) ? jb : (jp > jm ? jm : jp);
+        fwd_irows<Tr, V, SYM, true>(op, cls, row, jb, j1, w, dprev, S, unsafe);
+        fwd_irows<Tr, V, SYM, false>(op, cls, row, j1, jm, w, dprev, S, unsafe);
+    } else {
+#pragma unroll 4
+        for (int j = jb; j < jm; ++j) {
+            w[4] = Tr::template ld_mid<V>(row + (size_t)(j + 2) * kSZ);
+            A sv[V];
+            istencil<A, V, SYM>(t0, t1, t2, w, sv);
+            Pack<A, V> x;
+#pragma unroll
+            for (int i = 0; i < V; ++i) x.v[i] = sv[i];
+            Tr::template st_out<V>(op, row + (size_t)j * kSZ, x);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
+        }
+    }
+    for (int j = (jb > m - 2 ? jb : m - 2); j < je; ++j) {
+        w[4] = (j + 2 - m == 0) ? ha[0] : ha[1];
+        if (FWD) {
+            fwd_irow<Tr, V, SYM, true>(op, cls, j, row, w, dprev, S);
+        } else {
+            A sv[V];
+            istencil<A, V, SYM>(t0, t1, t2, w, sv);
+            Pack<A, V> x;
+#pragma unroll
+            for (int i = 0; i < V; ++i) x.v[i] = sv[i];
+            Tr::template st_out<V>(op, row + (size_t)j * kSZ, x);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
+    }
+}
+
+// Closure rows j0..j0+3 of a stencil sweep: 7-point windows from the scratch rows
+// (x[i] = v[Jx + i] at scratch index i - xlo, entries outside [0, xhi) zero).
+template <typename Tr, int V, bool FWD>
+__device__ __forceinline__ void sweep_edge(const DevOp &op, int cls, typename Tr::S *row, int j0, int e0,
+                                           const typename Tr::S *xs, int c, int xlo, int xhi,
+                                           Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S) {
+    using A = typename Tr::A;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        A sv[V];
+        {
+            Pack<A, V> w7[kTaps];
+#pragma unroll
+            for (int o = 0; o < kTaps; ++o) {
+                const int x = t + o + xlo;
+                int dummy = 0;
+                w7[o] = (x >= 0 && x < xhi)
+                            ? (FWD ? Tr::template ld_in<V>(op, xs + (size_t)x * kSZ + c, dummy)
+                                   : Tr::template ld_mid<V>(xs + (size_t)x * kSZ + c))
+                            : zero_a<Tr, V>();
+            }
+            estencil<Tr, V>(op, e0 + t, w7, sv);
+        }
+        if (FWD) {
+            fwd_row<Tr, V>(op, cls, j0 + t, row, sv, dprev, S);
+        } else {
+            Pack<A, V> x;
+#pragma unroll
+            for (int i = 0; i < V; ++i) x.v[i] = sv[i];
+            Tr::template st_out<V>(op, row + (size_t)(j0 + t) * kSZ, x);
+        }
+    }
+}
+
+// A full stencil sweep over this chunk (closure rows peeled on closed lines).
+template <typename Tr, int V, bool FWD>
+__device__ __forceinline__ void stencil_sweep(const DevOp &op, int k, int cls, typename Tr::S *row,
+                                              const typename Tr::S *xs, int c,
+                                              const Pack<typename Tr::A, V> (&hb)[2],
+                                              const Pack<typename Tr::A, V> (&ha)[2],
+                                              Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S,
+                                              int &unsafe) {
+    const int m = op.m;
+    const bool first_edge = !op.periodic && k == 0;
+    const bool last_edge = !op.periodic && k == op.P - 1;
+    const int jb = first_edge ? 4 : 0, je = last_edge ? m - 4 : m;
+    if (first_edge) sweep_edge<Tr, V, FWD>(op, cls, row, 0, 0, xs, c, -3, kTaps, dprev, S);
+    Pack<typename Tr::A, V> w[5];
+    if (first_edge) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            w[i] = FWD ? Tr::template ld_in<V>(op, xs + (size_t)(2 + i) * kSZ + c, unsafe)
+                       : Tr::template ld_mid<V>(xs + (size_t)(2 + i) * kSZ + c);
+    } else {
+        w[0] = hb[0];
+        w[1] = hb[1];
+        w[2] = FWD ? Tr::template ld_in<V>(op, row, unsafe) : Tr::template ld_mid<V>(row);
+        w[3] = FWD ? Tr::template ld_in<V>(op, row + kSZ, unsafe) : Tr::template ld_mid<V>(row + kSZ);
+    }
+    if (op.symmetric > 0) sweep_interior<Tr, V, true, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
+    else sweep_interior<Tr, V, false, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
+    // the last 4 rows of a closed line: scratch rows 7..13 hold v[n-7..n-1]
+    if (last_edge)
+        sweep_edge<Tr, V, FWD>(op, cls, row, m - 4, kEdgeRows, xs + (size_t)kTaps * kSZ, c, 0, kTaps, dprev, S);
+}
+
+// One group.  Called by every thread of the CTA after the tile has landed and every thread
+// has run read_halo; leaves the result in the tile (as S).  Contains __syncthreads().
+template <typename Tr, int V, bool ADJ>
+__device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *tile, typename Tr::S *xs,
+                                            double *ends, int k, int c,
+                                            const Pack<typename Tr::A, V> (&hb)[2],
+                                            const Pack<typename Tr::A, V> (&ha)[2], int &unsafe) {
+    using A = typename Tr::A;
+    using S = typename Tr::S;
+    const int m = op.m, P = op.P;
+    const int cls = chunk_class(op, k);
+    S *row = tile + (size_t)k * m * kSZ + c;
+    Pack<A, V> dprev = zero_a<Tr, V>(), Ssum = zero_a<Tr, V>();
+
+    // ---- forward pass ----
+    if (!ADJ) {
+        stencil_sweep<Tr, V, true>(op, k, cls, row, xs, c, hb, ha, dprev, Ssum, unsafe);
+    } else {
+        // identity right-hand side: d_j = f_j g_j - (f_j r_j) d_{j-1}
+        auto arow = [&](int j, bool acc) {
+            A c0, c1, c2, gg;
+            Tr::ifw(op, cls, j, c0, c1, c2, gg);
+            const Pack<A, V> g = Tr::template ld_in<V>(op, row + (size_t)j * kSZ, unsafe);
+            const A p = acc ? Tr::pi(op, cls, j) : A(0);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                dprev.v[i] = mad(-gg, dprev.v[i], c0 * g.v[i]);
+                if (acc) Ssum.v[i] = mad(p, dprev.v[i], Ssum.v[i]);
+            }
+            Tr::template st_mid<V>(row + (size_t)j * kSZ, dprev);
+        };
+        const int jp = Tr::jpi(op, cls) < m ? Tr::jpi(op, cls) : m;
+#pragma unroll 4
+        for (int j = 0; j < jp; ++j) arow(j, true);
+#pragma unroll 4
+        for (int j = jp; j < m; ++j) arow(j, false);
+    }
+    {
+        // row 0 eliminates the back-swept row 1: d0~ = N1 (d_0 - w_0 S); chunk ends to `ends`
+        const Pack<A, V> d0 = Tr::template ld_mid<V>(row);
+        A sa0, w0;
+        Tr::bwd(op, cls, 0, sa0, w0);
+        const A n1 = Tr::from_d(__ldg(op.n1 + cls));
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            ends[(size_t)(2 * k) * kSZ + c + i] = Tr::to_d(n1 * (d0.v[i] - w0 * Ssum.v[i]));
+            ends[(size_t)(2 * k + 1) * kSZ + c + i] = Tr::to_d(dprev.v[i]);
+        }
+    }
+    __syncthreads();
+
+    // ---- reduced chunk-end system, FP64 ----
+    if (op.red_decoupled) {
+        // boundary k joins L_{k-1} (ends slot 2k-1) and F_k (slot 2k): every thread solves its
+        // own lines' boundary; each slot is read and written by exactly one thread
+        const int R = 2 * P, prev = (k == 0) ? P - 1 : k - 1;
+        const double a = __ldg(op.red + (size_t)kRedBa * R + k);
+        const double cc = __ldg(op.red + (size_t)kRedBc * R + k);
+        const double inv = __ldg(op.red + (size_t)kRedBinv * R + k);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            double *ef = ends + (size_t)(2 * k) * kSZ + c + i;
+            double *el = ends + (size_t)(2 * prev + 1) * kSZ + c + i;
+            const double dl = *el;
+            const double Fk = (*ef - a * dl) * inv;
+            *ef = Fk;
+            *el = dl - cc * Fk;
+        }
+    } else {
+        for (int l = threadIdx.x; l < kSZ; l += blockDim.x) reduced_solve(op, ends + l, kSZ);
+    }
+    __syncthreads();
+
+    // ---- back-substitution: u_{m-1} = L, u_j = d_j - s^a_j F - s^c_j u_{j+1}, u_0 = F ----
+    Pack<A, V> F, u;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        F.v[i] = Tr::from_d(ends[(size_t)(2 * k) * kSZ + c + i]);
+        u.v[i] = Tr::from_d(ends[(size_t)(2 * k + 1) * kSZ + c + i]);
+    }
+    // forward operator: results as output values; adjoint: y as mid values for the B^T pass
+    auto put = [&](int j, const Pack<A, V> &v) {
+        if (ADJ) Tr::template st_mid<V>(row + (size_t)j * kSZ, v);
+        else Tr::template st_out<V>(op, row + (size_t)j * kSZ, v);
+    };
+    put(m - 1, u);
+    // rows at or past the s^a cut-off: u_j = d_j - s^c_j u_{j+1}
+    const int js = Tr::jsa(op, cls) > 1 ? Tr::jsa(op, cls) : 1;
+#pragma unroll 4
+    for (int j = m - 2; j >= js; --j) {
+        const Pack<A, V> d = Tr::template ld_mid<V>(row + (size_t)j * kSZ);
+        A sa, sc;
+        Tr::bwd(op, cls, j, sa, sc);
+#pragma unroll
+        for (int i = 0; i < V; ++i) u.v[i] = mad(-sc, u.v[i], d.v[i]);
+        put(j, u);
+    }
+#pragma unroll 4
+    for (int j = (js < m - 1 ? js : m - 1) - 1; j >= 1; --j) {
+        const Pack<A, V> d = Tr::template ld_mid<V>(row + (size_t)j * kSZ);
+        A sa, sc;
+        Tr::bwd(op, cls, j, sa, sc);
+#pragma unroll
+        for (int i = 0; i < V; ++i) u.v[i] = mad(-sc, u.v[i], mad(-sa, F.v[i], d.v[i]));
+        put(j, u);
+    }
+    put(0, F);
+    if (ADJ) {
+        // ---- adjoint: x = B^T y, in place, with the same halo scheme as the forward stencil ----
+        __syncthreads();
+        Pack<A, V> yb[2], ya[2];
+        read_halo<Tr, V, true>(op, tile, xs, k, c, yb, ya, unsafe);
+        __syncthreads();
+        stencil_sweep<Tr, V, false>(op, k, cls, row, xs, c, yb, ya, dprev, Ssum, unsafe);
+    }
+}
+
+// Shared-memory layout of the resident kernels:
+//   tiles[nbuf][n][32] (S) | xs[14][32] (S, closure rows) | ends[2P][32] (double) | bars
+__host__ __device__ inline size_t tile_bytes_of(int n, size_t es) { return (size_t)n * kSZ * es; }
+__host__ __device__ inline size_t xs_bytes_of(size_t es) { return ((size_t)2 * kTaps * kSZ * es + 15) & ~(size_t)15; }
+
+// The finished tile (in shared memory) to HBM.
+template <typename Tr, int V>
+__device__ __forceinline__ void store_tile(const DevOp &op, const typename Tr::S *tile,
+                                           typename Tr::S *og, int k, int c) {
+    using S = typename Tr::S;
+    if (kBulkStore<Tr>) {
+        fence_async_smem();   // this thread's tile writes are visible to the bulk store
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            bulk_s2g(og, tile, (uint32_t)tile_bytes_of(op.n, sizeof(S)));
+            bulk_commit();
+            bulk_wait_read();   // shared memory must stay valid until the copy has read it
+        }
+    } else {
+        const size_t o = (size_t)k * op.m * kSZ + c;
+#pragma unroll 4
+        for (int j = 0; j < op.m; ++j)
+            stv<S, V>(og + o + (size_t)j * kSZ, ldv<S, V>(tile + o + (size_t)j * kSZ));
+    }
+}
+
+// One CTA per group, P * 32/V threads.  The tile arrives as one TMA bulk copy per chunk; a
+// thread starts as soon as its own chunk and its neighbours' have landed.
+template <typename Tr, int V, bool ADJ>
+__global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_constant__ DevOp op,
+                                                                 const typename Tr::S *__restrict__ in,
+                                                                 typename Tr::S *__restrict__ out) {
+    using S = typename Tr::S;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int failed;
+    const int n = op.n, m = op.m, P = op.P;
+    constexpr int tpc = kSZ / V;
+    const int k = threadIdx.x / tpc, c = (threadIdx.x % tpc) * V;
+    const size_t gofs = (size_t)blockIdx.x * n * kSZ;
+    S *tile = reinterpret_cast<S *>(smem);
+    S *xs = reinterpret_cast<S *>(smem + tile_bytes_of(n, sizeof(S)));
+    double *ends = reinterpret_cast<double *>(smem + tile_bytes_of(n, sizeof(S)) + xs_bytes_of(sizeof(S)));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ends + (size_t)2 * P * kSZ);
+    const uint32_t chunk_bytes = (uint32_t)((size_t)m * kSZ * sizeof(S));
+
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int q = 0; q < P; ++q) mbar_init(&bars[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < P; ++q) {
+            mbar_expect_tx(&bars[q], chunk_bytes);
+            bulk_g2s(tile + (size_t)q * m * kSZ, in + gofs + (size_t)q * m * kSZ, chunk_bytes, &bars[q]);
+        }
+    }
+    bool ok = mbar_wait(&bars[k], 0);
+    if (!ADJ) {
+        if (k > 0 || op.periodic) ok = mbar_wait(&bars[(k - 1 + P) % P], 0) && ok;
+        if (k < P - 1 || op.periodic) ok = mbar_wait(&bars[(k + 1) % P], 0) && ok;
+        // the closure rows of a closed line may reach into the second / second-to-last chunk
+        if (!op.periodic && (k == 0 || k == P - 1))
+            for (int q = 0; q < P; ++q) ok = mbar_wait(&bars[q], 0) && ok;
+    }
+    if (!ok) atomicExch(&failed, 1);
+    int unsafe = 0;
+    Pack<typename Tr::A, V> hb[2], ha[2];
+    if (!ADJ && ok) read_halo<Tr, V, false>(op, tile, xs, k, c, hb, ha, unsafe);
+    __syncthreads();
+    if (failed) {
+        // let every bulk copy land before the CTA's shared memory is released
+        for (int q = threadIdx.x; q < P; q += blockDim.x) mbar_wait(&bars[q], 0);
+        if (threadIdx.x == 0) record_timeout();
+        return;
+    }
+    group_sweep<Tr, V, ADJ>(op, tile, xs, ends, k, c, hb, ha, unsafe);
+    store_tile<Tr, V>(op, tile, out + gofs, k, c);
+}
+
+// Persistent variant: each CTA walks groups blockIdx.x, +gridDim.x, ... through `nbuf` tile
+// buffers; the TMA bulk copy of a group is issued `nbuf` groups ahead, so HBM reads stay in
+// flight while the threads sweep.  
+template <typename Tr, int V, bool ADJ>
+__global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_pipe(const __grid_constant__ DevOp op,
+                                                                      const typename Tr::S *__restrict__ in,
+                                                                      typename Tr::S *__restrict__ out, int nbuf) {
+    using S = typename Tr::S;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int failed;
+    const int n = op.n, P = op.P, G = op.ngroups;
+    constexpr int tpc = kSZ / V;
+    const int k = threadIdx.x / tpc, c = (threadIdx.x % tpc) * V;
+    const size_t tile_elems = (size_t)n * kSZ;
+    const uint32_t tile_bytes = (uint32_t)tile_bytes_of(n, sizeof(S));
+    S *tiles = reinterpret_cast<S *>(smem);
+    S *xs = reinterpret_cast<S *>(smem + (size_t)nbuf * tile_bytes);
+    double *ends = reinterpret_cast<double *>(smem + (size_t)nbuf * tile_bytes + xs_bytes_of(sizeof(S)));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ends + (size_t)2 * P * kSZ);
+
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int b = 0; b < nbuf; ++b) mbar_init(&bars[b], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < nbuf; ++b) {
+            const long long g = blockIdx.x + (long long)b * gridDim.x;
+            if (g >= G) break;
+            mbar_expect_tx(&bars[b], tile_bytes);
+            bulk_g2s(tiles + (size_t)b * tile_elems, in + (size_t)g * tile_elems, tile_bytes, &bars[b]);
+        }
+    }
+    for (int it = 0;; ++it) {
+        const long long g = blockIdx.x + (long long)it * gridDim.x;
+        if (g >= G) break;
+        const int b = it % nbuf;
+        S *tile = tiles + (size_t)b * tile_elems;
+        const bool ok = mbar_wait(&bars[b], (uint32_t)((it / nbuf) & 1));
+        if (!ok) atomicExch(&failed, 1);
+        int unsafe = 0;
+        Pack<typename Tr::A, V> hb[2], ha[2];
+        if (!ADJ && ok) read_halo<Tr, V, false>(op, tile, xs, k, c, hb, ha, unsafe);
+        __syncthreads();
+        if (failed) {
+            // drain every bulk copy still in flight into this CTA's buffers, then give up
+            for (int d = threadIdx.x; d < nbuf; d += blockDim.x)
+                if (blockIdx.x + (long long)(it + d) * gridDim.x < G)
+                    mbar_wait(&bars[(it + d) % nbuf], (uint32_t)(((it + d) / nbuf) & 1));
+            if (threadIdx.x == 0) record_timeout();
+            return;
+        }
+        group_sweep<Tr, V, ADJ>(op, tile, xs, ends, k, c, hb, ha, unsafe);
+        S *og = out + (size_t)g * tile_elems;
+        if (kBulkStore<Tr>) {
+            fence_async_smem();
+        } else {
+            const size_t o = (size_t)k * op.m * kSZ + c;
+#pragma unroll 4
+            for (int j = 0; j < op.m; ++j)
+                stv<S, V>(og + o + (size_t)j * kSZ, ldv<S, V>(tile + o + (size_t)j * kSZ));
+        }
+        __syncthreads();   // every thread is done with this tile, the scratch rows and `ends`
+        if (threadIdx.x == 0) {
+            if (kBulkStore<Tr>) {
+                bulk_s2g(og, tile, tile_bytes);
+                bulk_commit();
+            }
+            const long long gn = g + (long long)nbuf * gridDim.x;
+            if (gn < G) {
+                // the buffer is refilled only after the store has read it, and generic-proxy
+                // accesses are ordered before the async refill
+                if (kBulkStore<Tr>) bulk_wait_read();
+                fence_async_smem();
+                mbar_expect_tx(&bars[b], tile_bytes);
+                bulk_g2s(tile, in + (size_t)gn * tile_elems, tile_bytes, &bars[b]);
+            }
+        }
+    }
+    if (kBulkStore<Tr> && threadIdx.x == 0) bulk_wait_read();
+}
+
+template <typename Tr, int V, bool ADJ>
+tds_status launch_resident_t(const DevOp &op, const void *in, void *out, int smem, cudaStream_t st) {
+    using S = typename Tr::S;
+    auto kern = k_resident<Tr, V, ADJ>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return TDS_ERR_CUDA;
+    kern<<<op.ngroups, op.P * (kSZ / V), smem, st>>>(op, static_cast<const S *>(in), static_cast<S *>(out));
+    return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
+}
+
+template <typename Tr, bool ADJ>
+tds_status launch_pipe_t(const DevOp &op, const void *in, void *out, int nbuf, int smem, int grid,
+                         cudaStream_t st) {
+    using S = typename Tr::S;
+    auto kern = k_resident_pipe<Tr, 1, ADJ>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return TDS_ERR_CUDA;
+    kern<<<grid, op.P * kSZ, smem, st>>>(op, static_cast<const S *>(in), static_cast<S *>(out), nbuf);
+    return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
+}
+
+template <typename Tr, int V>
+tds_status launch_resident_v(const tds_plan *p, int which, const void *in, void *out, cudaStream_t st) {
+    const DevOp &op = p->op[which];
+    return which ? launch_resident_t<Tr, V, true>(op, in, out, p->resident_smem, st)
+                 : launch_resident_t<Tr, V, false>(op, in, out, p->resident_smem, st);
+}
+
+} // namespace
+
+size_t resident_smem_bytes(int n, int P, tds_dtype dtype) {
+    const size_t es = (dtype == TDS_F64) ? 8 : 4;
+    return tile_bytes_of(n, es) + xs_bytes_of(es) + (size_t)2 * P * kSZ * 8 + (size_t)P * 8;
+}
+
+size_t pipe_smem_bytes(int n, int P, tds_dtype dtype, int nbuf) {
+    const size_t es = (dtype == TDS_F64) ? 8 : 4;
+    return (size_t)nbuf * tile_bytes_of(n, es) + xs_bytes_of(es) + (size_t)2 * P * kSZ * 8 + (size_t)nbuf * 8;
+}
+
+// Lines per thread (tds_plan::lanes): FP32 1, 2 or 4; FP64 1 or 2.  More lanes spread the per-row
+// work (plan records, addressing, loop control) over more points and give each thread
+// independent recurrences; fewer lanes give more threads.
+tds_status launch_resident(const tds_plan *p, int which, const void *in, void *out, cudaStream_t st) {
+    if (p->dtype == TDS_F64)
+        return p->lanes == 2 ? launch_resident_v<TrF64, 2>(p, which, in, out, st)
+                             : launch_resident_v<TrF64, 1>(p, which, in, out, st);
+    return p->lanes == 4 ? launch_resident_v<TrF32, 4>(p, which, in, out, st)
+         : p->lanes == 2 ? launch_resident_v<TrF32, 2>(p, which, in, out, st)
+                         : launch_resident_v<TrF32, 1>(p, which, in, out, st);
+}
+
+tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *out, cudaStream_t st) {
+    const DevOp &op = p->op[which];
+    const int smem = (int)pipe_smem_bytes(p->n, p->P, p->dtype, p->pipe_nbuf);
+    const int grid = op.ngroups < p->pipe_grid ? op.ngroups : p->pipe_grid;
+    if (p->dtype == TDS_F64)
+        return which ? launch_pipe_t<TrF64, true>(op, in, out, p->pipe_nbuf, smem, grid, st)
+                     : launch_pipe_t<TrF64, false>(op, in, out, p->pipe_nbuf, smem, grid, st);
+    return which ? launch_pipe_t<TrF32, true>(op, in, out, p->pipe_nbuf, smem, grid, st)
+                 : launch_pipe_t<TrF32, false>(op, in, out, p->pipe_nbuf, smem, grid, st);
+}
+
+tds_status read_device_status() {
+    int v = 0, zero = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return TDS_ERR_CUDA;
+    if (cudaMemcpyFromSymbol(&v, g_device_status, sizeof(int)) != cudaSuccess) return TDS_ERR_CUDA;
+    if (cudaMemcpyToSymbol(g_device_status, &zero, sizeof(int)) != cudaSuccess) return TDS_ERR_CUDA;
+    return (tds_status)v;
+}
+
+} // namespace tds
