@@ -36,7 +36,7 @@ if ROOT not in sys.path:
 
 METRIC = "Gpoints/s and % of HBM roofline per directional derivative, FP64 vs FP32"
 UNIT = "Gpoints/s"
-KERNEL_SRC = os.path.join(ROOT, "paper_2411_13532_gb300", "csrc", "tds_kernels.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_2411_13532_gb300", "csrc", "tds_resident.cu")
 
 def fp64_ops_per_point(op, m):
     """FP64-pipe operations per interior point as the resident kernel issues them.
