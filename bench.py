@@ -144,6 +144,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# --------------------------------------------------------------------------- multi-rank
+
+def max_over_ranks(ms, world, device):
+    """Max of a per-rank time over all ranks (the job is as slow as its slowest GPU)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, ops_per_step, npts, steps, ms):
+    """Whole-job Gpoints/s: every rank processes its own field (weak scaling)."""
+    return world * ops_per_step * npts * steps / (ms * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------------------------ our arm
 
 def run_ours(args, rank, world, local_rank):
@@ -236,14 +254,10 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = t0.elapsed_time(t1)
+    ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     gpu_launches = launches[0]
-    if world > 1:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
     ops_per_step = 18
-    value = world * ops_per_step * npts * args.steps / (ms * 1e-3) / 1e9
+    value = job_throughput(world, ops_per_step, npts, args.steps, ms)
 
     # per-kernel averages
     per = {}
@@ -336,12 +350,8 @@ def run_ours(args, rank, world, local_rank):
             e2e_step()
         b.record(stream)
         torch.cuda.synchronize()
-        ems = a.elapsed_time(b)
-        if world > 1:
-            tt = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = float(tt.item())
-        e2e = {"value": round(world * ops_per_step * npts * args.e2e_steps / (ems * 1e-3) / 1e9, 3),
+        ems = max_over_ranks(a.elapsed_time(b), world, dev)
+        e2e = {"value": round(job_throughput(world, ops_per_step, npts, args.e2e_steps, ems), 3),
                "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": round(ems / args.e2e_steps, 3)}
 

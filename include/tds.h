@@ -64,8 +64,11 @@ typedef enum {
     TDS_VARIANT_AUTO = 0,
     TDS_VARIANT_RESIDENT = 1,   /* one CTA holds a whole group of SZ lines on chip          */
     TDS_VARIANT_STREAMING = 2,  /* decouple / reduced / substitute as three kernels         */
-    TDS_VARIANT_PIPELINED = 3   /* persistent CTAs, each sweeping many groups through
+    TDS_VARIANT_PIPELINED = 3,  /* persistent CTAs, each sweeping many groups through
                                    several on-chip tile buffers filled ahead by TMA         */
+    TDS_VARIANT_SEGMENTED = 4   /* lines too long for one CTA: segments of 64..256 rows that
+                                   subdivide the chunks, one CTA each, in two kernels (the
+                                   adjoint of such a plan runs STREAMING)                   */
 } tds_variant;
 
 typedef struct tds_plan tds_plan;
@@ -100,7 +103,8 @@ TDS_API tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_d
 /* Choose the kernel pipeline of a plan (tuning and test hook; call before first use, not
  * concurrently with a call that uses the plan).  TDS_ERR_ARG if the plan cannot run the
  * requested variant (a resident group larger than one CTA's shared memory).  AUTO picks
- * RESIDENT when a group fits in one CTA, else STREAMING. */
+ * RESIDENT when a group fits in one CTA (and P <= 16), else SEGMENTED when the chunk length has
+ * a divisor between 64 and the segment cap (128 rows FP64, 256 FP32), else STREAMING. */
 TDS_API tds_status tds_plan_set_variant(tds_plan *plan, tds_variant variant);
 
 /* Describe a plan: line length n, lines N, chunks P, the variant it will run, and the
@@ -168,6 +172,14 @@ TDS_API const char *tds_status_string(tds_status status);
  * word (TDS_ERR_TIMEOUT), skips its writes and returns.  Synchronises the device.
  */
 TDS_API tds_status tds_device_status(void);
+
+/*
+ * tds_selftest_timeout -- exercise the device-side failure path: launch one warp that waits on
+ * a barrier nothing completes; the wait gives up after `seconds` (0 < seconds <= 2), records
+ * TDS_ERR_TIMEOUT in the device status word and the kernel returns normally, leaving the
+ * context usable.  Read the result with tds_device_status().
+ */
+TDS_API tds_status tds_selftest_timeout(double seconds, void *stream);
 
 /*
  * tds_plan_reduced_coeffs -- copy the plan's reduced chunk-end system to host memory for

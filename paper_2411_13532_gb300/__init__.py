@@ -75,7 +75,7 @@ class Plan:
         _lib.check(L.tds_plan_info(h_, ctypes.byref(n_), ctypes.byref(nl), ctypes.byref(p_),
                                    ctypes.byref(var), ctypes.byref(smem)), "tds_plan_info")
         self.nlines = nl.value
-        self.variant = {1: "resident", 2: "streaming", 3: "pipelined"}[var.value]
+        self.variant = {1: "resident", 2: "streaming", 3: "pipelined", 4: "segmented"}[var.value]
         self.smem_bytes = smem.value
         self.numel = nx * ny * nz
 

@@ -14,7 +14,7 @@ LAYOUTS = {"cart": 0, "x": 1, "y": 2, "z": 3}
 BCS = {"periodic": 0, "closed": 1}
 DTYPES = {"f64": 0, "f32": 1}
 MODES = {"exact": 0, "paper_drop": 1}
-VARIANTS = {"auto": 0, "resident": 1, "streaming": 2, "pipelined": 3}
+VARIANTS = {"auto": 0, "resident": 1, "streaming": 2, "pipelined": 3, "segmented": 4}
 
 # (name, restype, argtypes) of every entry point declared in include/tds.h
 _vp, _i, _sz, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_double
@@ -31,6 +31,7 @@ SIGNATURES = [
     ("tds_plan_destroy", None, [_vp]),
     ("tds_status_string", ctypes.c_char_p, [_i]),
     ("tds_device_status", _i, []),
+    ("tds_selftest_timeout", _i, [_d, _vp]),
     ("tds_plan_reduced_coeffs", _i, [_vp, _vp, _vp]),
     ("tds_reduced_solve", _i, [_vp, _vp, _vp, _vp]),
     ("tds_deriv_noalloc", _i, [_vp, _vp, _vp, _vp]),

@@ -23,7 +23,13 @@ bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p
 size_t elem_size(tds_dtype dt) { return dt == TDS_F64 ? 8 : 4; }
 
 size_t ws_need(const tds_plan *p) {
-    return p->variant == TDS_VARIANT_STREAMING ? streaming_ws_bytes(p) : 0;
+    if (p->variant == TDS_VARIANT_STREAMING) return streaming_ws_bytes(p);
+    if (p->variant == TDS_VARIANT_SEGMENTED) {
+        // the adjoint of a segmented plan runs the streaming pipeline
+        const size_t a = segmented_ws_bytes(p), b = streaming_ws_bytes(p);
+        return a > b ? a : b;
+    }
+    return 0;
 }
 
 tds_status run(const tds_plan *p, int which, const void *in, void *out, void *ws, size_t ws_bytes,
@@ -40,6 +46,7 @@ tds_status run(const tds_plan *p, int which, const void *in, void *out, void *ws
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (p->variant == TDS_VARIANT_RESIDENT) return launch_resident(p, which, in, out, st);
     if (p->variant == TDS_VARIANT_PIPELINED) return launch_pipelined(p, which, in, out, st);
+    if (p->variant == TDS_VARIANT_SEGMENTED && which == 0) return launch_segmented(p, in, out, ws, st);
     return launch_streaming(p, which, in, out, ws, st);
 }
 
@@ -125,10 +132,14 @@ tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_dir dir, 
 
 tds_status tds_plan_set_variant(tds_plan *p, tds_variant v) {
     if (!p) return TDS_ERR_ARG;
-    if (v == TDS_VARIANT_AUTO) v = p->resident_smem ? TDS_VARIANT_RESIDENT : TDS_VARIANT_STREAMING;
+    if (v == TDS_VARIANT_AUTO)
+        v = p->resident_smem ? TDS_VARIANT_RESIDENT
+          : p->seg.P ? TDS_VARIANT_SEGMENTED : TDS_VARIANT_STREAMING;
     if (v == TDS_VARIANT_RESIDENT && !p->resident_smem) return TDS_ERR_ARG;
     if (v == TDS_VARIANT_PIPELINED && !p->pipe_nbuf) return TDS_ERR_ARG;
-    if (v != TDS_VARIANT_RESIDENT && v != TDS_VARIANT_STREAMING && v != TDS_VARIANT_PIPELINED)
+    if (v == TDS_VARIANT_SEGMENTED && !p->seg.P) return TDS_ERR_ARG;
+    if (v != TDS_VARIANT_RESIDENT && v != TDS_VARIANT_STREAMING && v != TDS_VARIANT_PIPELINED &&
+        v != TDS_VARIANT_SEGMENTED)
         return TDS_ERR_ARG;
     p->variant = v;
     return TDS_OK;
@@ -200,6 +211,10 @@ void tds_plan_destroy(tds_plan *p) {
 }
 
 tds_status tds_device_status(void) { return read_device_status(); }
+
+tds_status tds_selftest_timeout(double seconds, void *stream) {
+    return launch_selftest_wait(seconds, static_cast<cudaStream_t>(stream));
+}
 
 tds_status tds_plan_reduced_coeffs(const tds_plan *p, double *sub, double *sup) {
     if (!p || !sub || !sup) return TDS_ERR_ARG;

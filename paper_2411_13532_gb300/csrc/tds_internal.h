@@ -84,12 +84,13 @@ struct tds_plan {
     tds_dtype dtype;
     tds_reduced mode;
     int n, m, nlines;
-    tds_variant variant;   // resolved: RESIDENT, PIPELINED or STREAMING
+    tds_variant variant;   // resolved: RESIDENT, PIPELINED, SEGMENTED or STREAMING
     int resident_smem;     // dynamic shared memory of the resident kernel (0 = cannot run)
     int pipe_nbuf;         // > 0: run the persistent multi-buffered resident kernel
     int pipe_grid;         // its grid (resident CTAs the device holds at once)
     int lanes;             // lines per thread in the resident kernels (FP32: 1, 2, 4; FP64: 1, 2)
     tds::DevOp op[2];      // [0] = A^{-1} B, [1] = B^T A^{-T}
+    tds::DevOp seg;        // A^{-1} B on the segment partition of the SEGMENTED variant (P = 0: none)
     double *red_sub_host[2], *red_sup_host[2];
     void *dmem;            // one device allocation holding every array of both operators
     void *hmem;            // host copies (reduced coefficients)
@@ -107,6 +108,9 @@ tds_status launch_resident(const tds_plan *p, int which, const void *in, void *o
                            cudaStream_t st);
 tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *out,
                             cudaStream_t st);
+size_t segmented_ws_bytes(const tds_plan *p);
+tds_status launch_segmented(const tds_plan *p, const void *in, void *out, void *ws,
+                            cudaStream_t st);
 size_t streaming_ws_bytes(const tds_plan *p);
 tds_status launch_streaming(const tds_plan *p, int which, const void *in, void *out,
                             void *ws, cudaStream_t st);
@@ -115,5 +119,6 @@ tds_status launch_reduced_only(const tds_plan *p, const double *rhs, double *x,
 tds_status launch_reorder(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
                           tds_layout to, size_t elem, cudaStream_t st);
 tds_status read_device_status();
+tds_status launch_selftest_wait(double seconds, cudaStream_t st);
 
 } // namespace tds

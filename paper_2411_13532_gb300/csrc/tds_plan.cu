@@ -137,13 +137,13 @@ bool preprocess_chunk(int m, const double *a, const double *b, const double *c,
 } // namespace
 
 // Build one operator (A^{-1}B if which == 0, B^T A^{-T} if which == 1) into host buffers.
-static tds_status build_operator(const tds_plan *p, const LineOperator &L, int which,
+static tds_status build_operator(const tds_plan *p, int P, int m, const LineOperator &L, int which,
                                  DevOp &op, std::vector<double> &rows,
                                  std::vector<double> &n1s, std::vector<double> &red,
                                  std::vector<double> &sub, std::vector<double> &sup,
                                  std::vector<double> &fwd, std::vector<double> &bwd,
                                  std::vector<double> &ifw) {
-    const int n = p->n, m = p->m, P = p->P;
+    const int n = p->n;
     const bool periodic = (p->bc == TDS_BC_PERIODIC);
     std::memset(&op, 0, sizeof(op));
     op.n = n; op.m = m; op.P = P; op.nlines = p->nlines; op.ngroups = p->nlines / kSZ;
@@ -280,18 +280,33 @@ tds_status build_plan(tds_plan *p) {
     scheme_line(p->n, p->order, periodic, p->h, L);
     transpose_line(p->n, periodic, L, LT);
 
-    std::vector<double> rows[2], n1s[2], red[2], sub[2], sup[2], fwd[2], bwd[2], ifw[2];
-    for (int w = 0; w < 2; ++w) {
-        tds_status s = build_operator(p, w ? LT : L, w, p->op[w], rows[w], n1s[w], red[w],
-                                      sub[w], sup[w], fwd[w], bwd[w], ifw[w]);
+    // operators: [0] A^{-1} B and [1] B^T A^{-T} on the plan's P chunks; [2] A^{-1} B on the
+    // segment partition of the SEGMENTED variant: segments of sg rows, 64 <= sg <= 32 KB of one
+    // group's rows, sg dividing the chunk length (so segment boundaries include the chunk
+    // boundaries), used only if every boundary system decouples
+    int sg = 0;
+    {
+        const int cap = (p->dtype == TDS_F64) ? 128 : 256;
+        for (int d = (p->m < cap ? p->m : cap); d >= 64; --d)
+            if (p->m % d == 0) { sg = d; break; }
+    }
+    const int nops = sg ? 3 : 2;
+    std::vector<double> rows[3], n1s[3], red[3], sub[3], sup[3], fwd[3], bwd[3], ifw[3];
+    DevOp *ops[3] = {&p->op[0], &p->op[1], &p->seg};
+    std::memset(&p->seg, 0, sizeof(p->seg));
+    for (int w = 0; w < nops; ++w) {
+        const int P = (w < 2) ? p->P : p->n / sg, m = (w < 2) ? p->m : sg;
+        tds_status s = build_operator(p, P, m, (w == 1) ? LT : L, (w == 1), *ops[w], rows[w], n1s[w],
+                                      red[w], sub[w], sup[w], fwd[w], bwd[w], ifw[w]);
         if (s != TDS_OK) return s;
     }
+    if (nops == 3 && !p->seg.red_decoupled) std::memset(&p->seg, 0, sizeof(p->seg));
 
     // one device allocation per plan, 256-byte aligned parts per operator:
     // [rows64 | rows32 | n1 | red | fwd64 | fwd32 | bwd64 | bwd32 | ifw64 | ifw32]
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t off[2][10], total = 0;
-    for (int w = 0; w < 2; ++w) {
+    size_t off[3][10], total = 0;
+    for (int w = 0; w < nops; ++w) {
         off[w][0] = total; total = align(total + rows[w].size() * sizeof(double));
         off[w][1] = total; total = align(total + rows[w].size() * sizeof(float));
         off[w][2] = total; total = align(total + n1s[w].size() * sizeof(double));
@@ -311,7 +326,7 @@ tds_status build_plan(tds_plan *p) {
         float *d = reinterpret_cast<float *>(&host[o]);
         for (size_t i = 0; i < v.size(); ++i) d[i] = (float)v[i];
     };
-    for (int w = 0; w < 2; ++w) {
+    for (int w = 0; w < nops; ++w) {
         put64(off[w][0], rows[w]); put32(off[w][1], rows[w]);
         put64(off[w][2], n1s[w]); put64(off[w][3], red[w]);
         put64(off[w][4], fwd[w]); put32(off[w][5], fwd[w]);
@@ -334,17 +349,21 @@ tds_status build_plan(tds_plan *p) {
     double *hm = static_cast<double *>(std::malloc(sizeof(double) * 4 * R));
     if (!hm) { cudaFree(d); p->dmem = nullptr; return TDS_ERR_NOMEM; }
     p->hmem = hm;
+    for (int w = 0; w < nops; ++w) {
+        DevOp &o = *ops[w];
+        if (!o.P) continue;   // segment operator not used
+        o.row64 = reinterpret_cast<const double *>(base + off[w][0]);
+        o.row32 = reinterpret_cast<const float *>(base + off[w][1]);
+        o.n1 = reinterpret_cast<const double *>(base + off[w][2]);
+        o.red = reinterpret_cast<const double *>(base + off[w][3]);
+        o.fwd64 = reinterpret_cast<const double *>(base + off[w][4]);
+        o.fwd32 = reinterpret_cast<const float *>(base + off[w][5]);
+        o.bwd64 = reinterpret_cast<const double *>(base + off[w][6]);
+        o.bwd32 = reinterpret_cast<const float *>(base + off[w][7]);
+        o.ifw64 = reinterpret_cast<const double *>(base + off[w][8]);
+        o.ifw32 = reinterpret_cast<const float *>(base + off[w][9]);
+    }
     for (int w = 0; w < 2; ++w) {
-        p->op[w].row64 = reinterpret_cast<const double *>(base + off[w][0]);
-        p->op[w].row32 = reinterpret_cast<const float *>(base + off[w][1]);
-        p->op[w].n1 = reinterpret_cast<const double *>(base + off[w][2]);
-        p->op[w].red = reinterpret_cast<const double *>(base + off[w][3]);
-        p->op[w].fwd64 = reinterpret_cast<const double *>(base + off[w][4]);
-        p->op[w].fwd32 = reinterpret_cast<const float *>(base + off[w][5]);
-        p->op[w].bwd64 = reinterpret_cast<const double *>(base + off[w][6]);
-        p->op[w].bwd32 = reinterpret_cast<const float *>(base + off[w][7]);
-        p->op[w].ifw64 = reinterpret_cast<const double *>(base + off[w][8]);
-        p->op[w].ifw32 = reinterpret_cast<const float *>(base + off[w][9]);
         p->red_sub_host[w] = hm + (size_t)(2 * w) * R;
         p->red_sup_host[w] = hm + (size_t)(2 * w + 1) * R;
         std::memcpy(p->red_sub_host[w], sub[w].data(), sizeof(double) * R);

@@ -139,41 +139,52 @@ __device__ __forceinline__ void estencil(const DevOp &op, int e, const Pack<type
     }
 }
 
+// The rows of one group a CTA holds: line rows [r0, r1) are in `tile` (row r at (r - r0)*32);
+// other rows of the same group are read from HBM at `gin` (read-only input).
+template <typename S>
+struct TileView {
+    S *tile;
+    int r0, r1;
+    const S *gin;
+};
+
 // Row J of the line (cyclic wrap; zero outside a closed line) as an input or mid value.
 template <typename Tr, int V, bool MID>
-__device__ __forceinline__ Pack<typename Tr::A, V> ld_row(const DevOp &op, const typename Tr::S *tile,
+__device__ __forceinline__ Pack<typename Tr::A, V> ld_row(const DevOp &op, const TileView<typename Tr::S> &tv,
                                                           int J, int c, int &unsafe) {
     const int r = line_row(op, J);
     if (r < 0) return zero_a<Tr, V>();
-    const typename Tr::S *p = tile + (size_t)r * kSZ + c;
+    const typename Tr::S *p = (r >= tv.r0 && r < tv.r1) ? tv.tile + (size_t)(r - tv.r0) * kSZ + c
+                                                        : tv.gin + (size_t)r * kSZ + c;
     return MID ? Tr::template ld_mid<V>(p) : Tr::template ld_in<V>(op, p, unsafe);
 }
 
 // Captured before the CTA barrier that lets any thread overwrite the tile: the stencil halo of
-// this chunk (2 rows before, 2 after) in registers and, on closed lines, the first and last 7
+// chunk K (2 rows before, 2 after) in registers and, on closed lines, the first and last 7
 // rows of the line in the scratch rows xs[0..6], xs[7..13] (closure rows reach 3 points in and
 // the sweep works in place), copied as they are: raw inputs for the forward stencil, mid values
 // (MID) for the adjoint B^T pass.
 template <typename Tr, int V, bool MID>
-__device__ __forceinline__ void read_halo(const DevOp &op, const typename Tr::S *tile, typename Tr::S *xs,
-                                          int k, int c, Pack<typename Tr::A, V> (&hb)[2],
+__device__ __forceinline__ void read_halo(const DevOp &op, const TileView<typename Tr::S> &tv,
+                                          typename Tr::S *xs, int K, int c, Pack<typename Tr::A, V> (&hb)[2],
                                           Pack<typename Tr::A, V> (&ha)[2], int &unsafe) {
     using S = typename Tr::S;
-    const int J0 = k * op.m;
+    const int J0 = K * op.m;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        hb[i] = ld_row<Tr, V, MID>(op, tile, J0 - 2 + i, c, unsafe);
-        ha[i] = ld_row<Tr, V, MID>(op, tile, J0 + op.m + i, c, unsafe);
+        hb[i] = ld_row<Tr, V, MID>(op, tv, J0 - 2 + i, c, unsafe);
+        ha[i] = ld_row<Tr, V, MID>(op, tv, J0 + op.m + i, c, unsafe);
     }
     if (!op.periodic) {
         auto copy_row = [&](int src, int dst) {
-            const S *p = tile + (size_t)src * kSZ + c;
+            const S *p = (src >= tv.r0 && src < tv.r1) ? tv.tile + (size_t)(src - tv.r0) * kSZ + c
+                                                       : tv.gin + (size_t)src * kSZ + c;
             if (!MID) (void)Tr::template ld_in<V>(op, p, unsafe);   // range check of the input
             stv<S, V>(xs + (size_t)dst * kSZ + c, ldv<S, V>(p));
         };
-        if (k == 0)
+        if (K == 0)
             for (int i = 0; i < kTaps; ++i) copy_row(i, i);
-        if (k == op.P - 1)
+        if (K == op.P - 1)
             for (int i = 0; i < kTaps; ++i) copy_row(op.n - kTaps + i, kTaps + i);
     }
 }
@@ -346,23 +357,18 @@ __device__ __forceinline__ void stencil_sweep(const DevOp &op, int k, int cls, t
         sweep_edge<Tr, V, FWD>(op, cls, row, m - 4, kEdgeRows, xs + (size_t)kTaps * kSZ, c, 0, kTaps, dprev, S);
 }
 
-// One group.  Called by every thread of the CTA after the tile has landed and every thread
-// has run read_halo; leaves the result in the tile (as S).  Contains __syncthreads().
+// Forward pass of chunk K (rows at `row` in the tile): the fused stencil (forward operator) or
+// the identity right-hand side (adjoint) with the forward elimination, accumulating S.
 template <typename Tr, int V, bool ADJ>
-__device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *tile, typename Tr::S *xs,
-                                            double *ends, int k, int c,
-                                            const Pack<typename Tr::A, V> (&hb)[2],
-                                            const Pack<typename Tr::A, V> (&ha)[2], int &unsafe) {
+__device__ __forceinline__ void forward_phase(const DevOp &op, typename Tr::S *row, const typename Tr::S *xs,
+                                              int K, int cls, int c, const Pack<typename Tr::A, V> (&hb)[2],
+                                              const Pack<typename Tr::A, V> (&ha)[2],
+                                              Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &Ssum,
+                                              int &unsafe) {
     using A = typename Tr::A;
-    using S = typename Tr::S;
-    const int m = op.m, P = op.P;
-    const int cls = chunk_class(op, k);
-    S *row = tile + (size_t)k * m * kSZ + c;
-    Pack<A, V> dprev = zero_a<Tr, V>(), Ssum = zero_a<Tr, V>();
-
-    // ---- forward pass ----
+    const int m = op.m;
     if (!ADJ) {
-        stencil_sweep<Tr, V, true>(op, k, cls, row, xs, c, hb, ha, dprev, Ssum, unsafe);
+        stencil_sweep<Tr, V, true>(op, K, cls, row, xs, c, hb, ha, dprev, Ssum, unsafe);
     } else {
         // identity right-hand side: d_j = f_j g_j - (f_j r_j) d_{j-1}
         auto arow = [&](int j, bool acc) {
@@ -383,16 +389,86 @@ __device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *til
 #pragma unroll 4
         for (int j = jp; j < m; ++j) arow(j, false);
     }
+}
+
+// Chunk ends after the forward pass: row 0 eliminates the back-swept row 1,
+// e0 = N1 (d_0 - w_0 S); e1 = d_{m-1}.
+template <typename Tr, int V>
+__device__ __forceinline__ void chunk_ends(const DevOp &op, const typename Tr::S *row, int cls,
+                                           const Pack<typename Tr::A, V> &dprev,
+                                           const Pack<typename Tr::A, V> &Ssum, double (&e0)[V],
+                                           double (&e1)[V]) {
+    using A = typename Tr::A;
+    const Pack<A, V> d0 = Tr::template ld_mid<V>(row);
+    A sa0, w0;
+    Tr::bwd(op, cls, 0, sa0, w0);
+    const A n1 = Tr::from_d(__ldg(op.n1 + cls));
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        e0[i] = Tr::to_d(n1 * (d0.v[i] - w0 * Ssum.v[i]));
+        e1[i] = Tr::to_d(dprev.v[i]);
+    }
+}
+
+// Back-substitution of one chunk from its reduced unknowns F (first row) and L (last row):
+// u_{m-1} = L, u_j = d_j - s^a_j F - s^c_j u_{j+1}, u_0 = F.  MID: results stay mid values
+// (adjoint y for the B^T pass), else they are written as outputs.
+template <typename Tr, int V, bool MID>
+__device__ __forceinline__ void backsub_phase(const DevOp &op, typename Tr::S *row, int cls,
+                                              const Pack<typename Tr::A, V> &F, Pack<typename Tr::A, V> u) {
+    using A = typename Tr::A;
+    const int m = op.m;
+    auto put = [&](int j, const Pack<A, V> &v) {
+        if (MID) Tr::template st_mid<V>(row + (size_t)j * kSZ, v);
+        else Tr::template st_out<V>(op, row + (size_t)j * kSZ, v);
+    };
+    put(m - 1, u);
+    // rows at or past the s^a cut-off: u_j = d_j - s^c_j u_{j+1}
+    const int js = Tr::jsa(op, cls) > 1 ? Tr::jsa(op, cls) : 1;
+#pragma unroll 4
+    for (int j = m - 2; j >= js; --j) {
+        const Pack<A, V> d = Tr::template ld_mid<V>(row + (size_t)j * kSZ);
+        A sa, sc;
+        Tr::bwd(op, cls, j, sa, sc);
+#pragma unroll
+        for (int i = 0; i < V; ++i) u.v[i] = mad(-sc, u.v[i], d.v[i]);
+        put(j, u);
+    }
+#pragma unroll 4
+    for (int j = (js < m - 1 ? js : m - 1) - 1; j >= 1; --j) {
+        const Pack<A, V> d = Tr::template ld_mid<V>(row + (size_t)j * kSZ);
+        A sa, sc;
+        Tr::bwd(op, cls, j, sa, sc);
+#pragma unroll
+        for (int i = 0; i < V; ++i) u.v[i] = mad(-sc, u.v[i], mad(-sa, F.v[i], d.v[i]));
+        put(j, u);
+    }
+    put(0, F);
+}
+
+// One group, whole line in the tile.  Called by every thread of the CTA after the tile has
+// landed and every thread has run read_halo; leaves the result in the tile (as S).  Contains
+// __syncthreads().
+template <typename Tr, int V, bool ADJ>
+__device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *tile, typename Tr::S *xs,
+                                            double *ends, int k, int c,
+                                            const Pack<typename Tr::A, V> (&hb)[2],
+                                            const Pack<typename Tr::A, V> (&ha)[2], int &unsafe) {
+    using A = typename Tr::A;
+    using S = typename Tr::S;
+    const int m = op.m, P = op.P;
+    const int cls = chunk_class(op, k);
+    S *row = tile + (size_t)k * m * kSZ + c;
+    Pack<A, V> dprev = zero_a<Tr, V>(), Ssum = zero_a<Tr, V>();
+
+    forward_phase<Tr, V, ADJ>(op, row, xs, k, cls, c, hb, ha, dprev, Ssum, unsafe);
     {
-        // row 0 eliminates the back-swept row 1: d0~ = N1 (d_0 - w_0 S); chunk ends to `ends`
-        const Pack<A, V> d0 = Tr::template ld_mid<V>(row);
-        A sa0, w0;
-        Tr::bwd(op, cls, 0, sa0, w0);
-        const A n1 = Tr::from_d(__ldg(op.n1 + cls));
+        double e0[V], e1[V];
+        chunk_ends<Tr, V>(op, row, cls, dprev, Ssum, e0, e1);
 #pragma unroll
         for (int i = 0; i < V; ++i) {
-            ends[(size_t)(2 * k) * kSZ + c + i] = Tr::to_d(n1 * (d0.v[i] - w0 * Ssum.v[i]));
-            ends[(size_t)(2 * k + 1) * kSZ + c + i] = Tr::to_d(dprev.v[i]);
+            ends[(size_t)(2 * k) * kSZ + c + i] = e0[i];
+            ends[(size_t)(2 * k + 1) * kSZ + c + i] = e1[i];
         }
     }
     __syncthreads();
@@ -419,45 +495,19 @@ __device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *til
     }
     __syncthreads();
 
-    // ---- back-substitution: u_{m-1} = L, u_j = d_j - s^a_j F - s^c_j u_{j+1}, u_0 = F ----
-    Pack<A, V> F, u;
+    Pack<A, V> F, L;
 #pragma unroll
     for (int i = 0; i < V; ++i) {
         F.v[i] = Tr::from_d(ends[(size_t)(2 * k) * kSZ + c + i]);
-        u.v[i] = Tr::from_d(ends[(size_t)(2 * k + 1) * kSZ + c + i]);
+        L.v[i] = Tr::from_d(ends[(size_t)(2 * k + 1) * kSZ + c + i]);
     }
-    // forward operator: results as output values; adjoint: y as mid values for the B^T pass
-    auto put = [&](int j, const Pack<A, V> &v) {
-        if (ADJ) Tr::template st_mid<V>(row + (size_t)j * kSZ, v);
-        else Tr::template st_out<V>(op, row + (size_t)j * kSZ, v);
-    };
-    put(m - 1, u);
-    // rows at or past the s^a cut-off: u_j = d_j - s^c_j u_{j+1}
-    const int js = Tr::jsa(op, cls) > 1 ? Tr::jsa(op, cls) : 1;
-#pragma unroll 4
-    for (int j = m - 2; j >= js; --j) {
-        const Pack<A, V> d = Tr::template ld_mid<V>(row + (size_t)j * kSZ);
-        A sa, sc;
-        Tr::bwd(op, cls, j, sa, sc);
-#pragma unroll
-        for (int i = 0; i < V; ++i) u.v[i] = mad(-sc, u.v[i], d.v[i]);
-        put(j, u);
-    }
-#pragma unroll 4
-    for (int j = (js < m - 1 ? js : m - 1) - 1; j >= 1; --j) {
-        const Pack<A, V> d = Tr::template ld_mid<V>(row + (size_t)j * kSZ);
-        A sa, sc;
-        Tr::bwd(op, cls, j, sa, sc);
-#pragma unroll
-        for (int i = 0; i < V; ++i) u.v[i] = mad(-sc, u.v[i], mad(-sa, F.v[i], d.v[i]));
-        put(j, u);
-    }
-    put(0, F);
+    backsub_phase<Tr, V, ADJ>(op, row, cls, F, L);
     if (ADJ) {
         // ---- adjoint: x = B^T y, in place, with the same halo scheme as the forward stencil ----
         __syncthreads();
         Pack<A, V> yb[2], ya[2];
-        read_halo<Tr, V, true>(op, tile, xs, k, c, yb, ya, unsafe);
+        const TileView<S> tv{tile, 0, op.n, nullptr};
+        read_halo<Tr, V, true>(op, tv, xs, k, c, yb, ya, unsafe);
         __syncthreads();
         stencil_sweep<Tr, V, false>(op, k, cls, row, xs, c, yb, ya, dprev, Ssum, unsafe);
     }
@@ -531,7 +581,7 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_co
     if (!ok) atomicExch(&failed, 1);
     int unsafe = 0;
     Pack<typename Tr::A, V> hb[2], ha[2];
-    if (!ADJ && ok) read_halo<Tr, V, false>(op, tile, xs, k, c, hb, ha, unsafe);
+    if (!ADJ && ok) read_halo<Tr, V, false>(op, TileView<S>{tile, 0, n, in + gofs}, xs, k, c, hb, ha, unsafe);
     __syncthreads();
     if (failed) {
         // let every bulk copy land before the CTA's shared memory is released
@@ -586,7 +636,7 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_pipe(const __gr
         if (!ok) atomicExch(&failed, 1);
         int unsafe = 0;
         Pack<typename Tr::A, V> hb[2], ha[2];
-        if (!ADJ && ok) read_halo<Tr, V, false>(op, tile, xs, k, c, hb, ha, unsafe);
+        if (!ADJ && ok) read_halo<Tr, V, false>(op, TileView<S>{tile, 0, n, in + (size_t)g * tile_elems}, xs, k, c, hb, ha, unsafe);
         __syncthreads();
         if (failed) {
             // drain every bulk copy still in flight into this CTA's buffers, then give up
@@ -624,6 +674,150 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_pipe(const __gr
         }
     }
     if (kBulkStore<Tr> && threadIdx.x == 0) bulk_wait_read();
+}
+
+// ------------------------------------------------------------------------------------------
+// SEGMENTED pipeline, for lines whose group does not fit in one CTA.  The line is cut into P'
+// segments of sg rows (sg >= 64 and dividing the chunk length, so the segment boundaries
+// include the chunk boundaries and, for sg >= 64, every boundary system decouples to rounding);
+// `op` describes that partition.  One CTA (one warp, one lane per line) per segment of a group.
+//   k_seg_forward : forward pass of the segment (halo rows beyond the segment from HBM),
+//                   segment ends -> ws; with STORE_D the forward values d also go to `out`.
+//   k_seg_backward: F_K and L_K from the two boundary 2x2 systems of the segment (ends of the
+//                   neighbouring segments from ws), the forward values again (recomputed from
+//                   the input, or read back from `out`), back-substitution, result to `out`.
+// ------------------------------------------------------------------------------------------
+template <typename Tr, bool STORE_D>
+__global__ void __launch_bounds__(32) k_seg_forward(const __grid_constant__ DevOp op,
+                                                    const typename Tr::S *__restrict__ in,
+                                                    typename Tr::S *__restrict__ out,
+                                                    double *__restrict__ ws) {
+    using S = typename Tr::S;
+    using A = typename Tr::A;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int n = op.n, m = op.m, P = op.P, c = threadIdx.x;
+    const long long g = blockIdx.x / P;
+    const int K = (int)(blockIdx.x % P);
+    const size_t gofs = (size_t)g * n * kSZ;
+    S *tile = reinterpret_cast<S *>(smem);
+    S *xs = reinterpret_cast<S *>(smem + tile_bytes_of(m, sizeof(S)));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + tile_bytes_of(m, sizeof(S)) + xs_bytes_of(sizeof(S)));
+    const uint32_t bytes = (uint32_t)tile_bytes_of(m, sizeof(S));
+    const int r0 = K * m;
+    if (c == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(tile, in + gofs + (size_t)r0 * kSZ, bytes, bar);
+    }
+    __syncwarp();
+    if (!mbar_wait(bar, 0)) {
+        if (c == 0) record_timeout();
+        mbar_wait(bar, 0);
+        return;
+    }
+    int unsafe = 0;
+    Pack<A, 1> hb[2], ha[2];
+    read_halo<Tr, 1, false>(op, TileView<S>{tile, r0, r0 + m, in + gofs}, xs, K, c, hb, ha, unsafe);
+    __syncwarp();
+    const int cls = chunk_class(op, K);
+    S *row = tile + c;
+    Pack<A, 1> dprev = zero_a<Tr, 1>(), Ssum = zero_a<Tr, 1>();
+    forward_phase<Tr, 1, false>(op, row, xs, K, cls, c, hb, ha, dprev, Ssum, unsafe);
+    double e0[1], e1[1];
+    chunk_ends<Tr, 1>(op, row, cls, dprev, Ssum, e0, e1);
+    double *e = ws + ((size_t)(g * P + K) * 2) * kSZ + c;
+    e[0] = e0[0];
+    e[kSZ] = e1[0];
+    if (STORE_D) {
+        S *o = out + gofs + (size_t)r0 * kSZ + c;
+#pragma unroll 4
+        for (int j = 0; j < m; ++j) o[(size_t)j * kSZ] = row[(size_t)j * kSZ];
+    }
+}
+
+template <typename Tr, bool RECOMPUTE>
+__global__ void __launch_bounds__(32) k_seg_backward(const __grid_constant__ DevOp op,
+                                                     const typename Tr::S *__restrict__ in,
+                                                     typename Tr::S *__restrict__ out,
+                                                     const double *__restrict__ ws) {
+    using S = typename Tr::S;
+    using A = typename Tr::A;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int n = op.n, m = op.m, P = op.P, c = threadIdx.x;
+    const long long g = blockIdx.x / P;
+    const int K = (int)(blockIdx.x % P);
+    const size_t gofs = (size_t)g * n * kSZ;
+    S *tile = reinterpret_cast<S *>(smem);
+    S *xs = reinterpret_cast<S *>(smem + tile_bytes_of(m, sizeof(S)));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + tile_bytes_of(m, sizeof(S)) + xs_bytes_of(sizeof(S)));
+    const uint32_t bytes = (uint32_t)tile_bytes_of(m, sizeof(S));
+    const int r0 = K * m;
+    // the input segment (to recompute the forward pass) or its stored forward values
+    const S *src = RECOMPUTE ? in + gofs + (size_t)r0 * kSZ : out + gofs + (size_t)r0 * kSZ;
+    if (c == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(tile, src, bytes, bar);
+    }
+    // the two boundary systems of this segment, FP64
+    const int R = 2 * P, prev = (K == 0) ? P - 1 : K - 1, next = (K == P - 1) ? 0 : K + 1;
+    const double *eg = ws + (size_t)g * P * 2 * kSZ + c;
+    const double e0K = eg[(size_t)(2 * K) * kSZ], e1K = eg[(size_t)(2 * K + 1) * kSZ];
+    const double e1p = eg[(size_t)(2 * prev + 1) * kSZ], e0n = eg[(size_t)(2 * next) * kSZ];
+    const double F64 = (e0K - __ldg(op.red + (size_t)kRedBa * R + K) * e1p) * __ldg(op.red + (size_t)kRedBinv * R + K);
+    const double Fn = (e0n - __ldg(op.red + (size_t)kRedBa * R + next) * e1K) * __ldg(op.red + (size_t)kRedBinv * R + next);
+    const double L64 = e1K - __ldg(op.red + (size_t)kRedBc * R + next) * Fn;
+    __syncwarp();
+    if (!mbar_wait(bar, 0)) {
+        if (c == 0) record_timeout();
+        mbar_wait(bar, 0);
+        return;
+    }
+    const int cls = chunk_class(op, K);
+    S *row = tile + c;
+    if (RECOMPUTE) {
+        int unsafe = 0;
+        Pack<A, 1> hb[2], ha[2];
+        read_halo<Tr, 1, false>(op, TileView<S>{tile, r0, r0 + m, in + gofs}, xs, K, c, hb, ha, unsafe);
+        __syncwarp();
+        Pack<A, 1> dprev = zero_a<Tr, 1>(), Ssum = zero_a<Tr, 1>();
+        forward_phase<Tr, 1, false>(op, row, xs, K, cls, c, hb, ha, dprev, Ssum, unsafe);
+    }
+    Pack<A, 1> F, L;
+    F.v[0] = Tr::from_d(F64);
+    L.v[0] = Tr::from_d(L64);
+    backsub_phase<Tr, 1, false>(op, row, cls, F, L);
+    S *o = out + gofs + (size_t)r0 * kSZ;
+    if (kBulkStore<Tr>) {
+        fence_async_smem();
+        __syncwarp();
+        if (c == 0) {
+            bulk_s2g(o, tile, bytes);
+            bulk_commit();
+            bulk_wait_read();
+        }
+    } else {
+#pragma unroll 4
+        for (int j = 0; j < m; ++j) o[(size_t)j * kSZ + c] = row[(size_t)j * kSZ];
+    }
+}
+
+template <typename Tr>
+tds_status launch_segmented_t(const DevOp &op, const void *in, void *out, void *ws, cudaStream_t st) {
+    using S = typename Tr::S;
+    constexpr bool kFP64 = sizeof(S) == 8;   // FP64: store d (the sweep is FP64-pipe bound)
+    const int smem = (int)(tile_bytes_of(op.m, sizeof(S)) + xs_bytes_of(sizeof(S)) + 16);
+    auto kf = k_seg_forward<Tr, kFP64>;
+    auto kb = k_seg_backward<Tr, !kFP64>;
+    if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return TDS_ERR_CUDA;
+    const unsigned grid = (unsigned)((long long)op.ngroups * op.P);
+    kf<<<grid, 32, smem, st>>>(op, static_cast<const S *>(in), static_cast<S *>(out), static_cast<double *>(ws));
+    kb<<<grid, 32, smem, st>>>(op, static_cast<const S *>(in), static_cast<S *>(out), static_cast<const double *>(ws));
+    return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
 }
 
 template <typename Tr, int V, bool ADJ>
@@ -687,6 +881,35 @@ tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *
                      : launch_pipe_t<TrF64, false>(op, in, out, p->pipe_nbuf, smem, grid, st);
     return which ? launch_pipe_t<TrF32, true>(op, in, out, p->pipe_nbuf, smem, grid, st)
                  : launch_pipe_t<TrF32, false>(op, in, out, p->pipe_nbuf, smem, grid, st);
+}
+
+namespace {
+// Self-test of the bounded-wait path: waits on an mbarrier whose phase nothing completes; the
+// wait gives up after `limit_ns`, records TDS_ERR_TIMEOUT and the kernel returns normally.
+__global__ void k_selftest_wait(unsigned long long limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 2);   // two arrivals expected, none ever made
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (!mbar_wait(&bar, 0, limit_ns) && threadIdx.x == 0) record_timeout();
+}
+} // namespace
+
+tds_status launch_selftest_wait(double seconds, cudaStream_t st) {
+    if (!(seconds > 0.0) || seconds > 2.0) return TDS_ERR_ARG;
+    k_selftest_wait<<<1, 32, 0, st>>>((unsigned long long)(seconds * 1e9));
+    return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
+}
+
+size_t segmented_ws_bytes(const tds_plan *p) {
+    return ((size_t)p->nlines * p->seg.P * 2 * sizeof(double) + 255) & ~(size_t)255;
+}
+
+tds_status launch_segmented(const tds_plan *p, const void *in, void *out, void *ws, cudaStream_t st) {
+    if (p->dtype == TDS_F64) return launch_segmented_t<TrF64>(p->seg, in, out, ws, st);
+    return launch_segmented_t<TrF32>(p->seg, in, out, ws, st);
 }
 
 tds_status read_device_status() {

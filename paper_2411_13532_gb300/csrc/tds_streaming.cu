@@ -142,12 +142,16 @@ __global__ void __launch_bounds__(kStreamWarps * 32) k_subst_bt(const __grid_con
     T win[kTaps];
 #pragma unroll
     for (int i = 0; i < kTaps; ++i) win[i] = adj_y<T>(op, g, J0, J0 - 3 + i, own, ends, halo);
+    // the window never needs the next chunk's row 3: the halo holds only rows 0..2 and m-3..m-1
+    // of each chunk, so the shift after the last row is skipped rather than loaded
 #pragma unroll 2
     for (int j = 0; j < m; ++j) {
         const T x = stencil<T>(op, J0 + j, win);
+        if (j + 1 < m) {
 #pragma unroll
-        for (int i = 0; i < kTaps - 1; ++i) win[i] = win[i + 1];
-        win[kTaps - 1] = adj_y<T>(op, g, J0, J0 + j + 4, own, ends, halo);
+            for (int i = 0; i < kTaps - 1; ++i) win[i] = win[i + 1];
+            win[kTaps - 1] = adj_y<T>(op, g, J0, J0 + j + 4, own, ends, halo);
+        }
         own[(size_t)j * kSZ] = x;
     }
 }

@@ -63,6 +63,37 @@ def test_small_grid_every_point(dtype, variant, direction, order, bc, adjoint):
         assert mx <= TOL[dtype], (P, mx, rms)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+@pytest.mark.parametrize("order", [1, 2])
+def test_segmented_long_lines(dtype, bc, order):
+    """Lines longer than one CTA's shared memory: segments of 64..256 rows subdivide the chunks
+    (two kernels); every point against the oracle, for several chunk lengths."""
+    shape = (1, 32, 2048)
+    cart = np.random.default_rng(order).uniform(-1, 1, shape)
+    if dtype == "f32":
+        cart = cart.astype(np.float32).astype(np.float64)
+    h = oracle.grid_spacing(2048, bc)
+    ref = oracle.deriv(cart, "x", order, bc, h)
+    for P in (1, 2, 4, 8, 16):
+        plan = tds.Plan(shape, "x", order, bc, P=P, h=h, dtype=TORCH[dtype], variant="segmented")
+        y = plan.deriv(to_device_layout(cart, "x", dtype))
+        mx, rms = rel_errors(from_device_layout(y, "x", shape), ref)
+        assert mx <= TOL[dtype], (P, mx, rms)
+        # the adjoint of a segmented plan (streaming pipeline)
+        ya = plan.adjoint(to_device_layout(cart, "x", dtype))
+        mx, _ = rel_errors(from_device_layout(ya, "x", shape), oracle.deriv_adjoint(cart, "x", order, bc, h))
+        assert mx <= TOL[dtype], (P, "adjoint", mx)
+
+
+def test_segmented_is_chosen_for_long_lines():
+    assert tds.Plan((1, 32, 2048), "x", 1, "periodic", P=4).variant == "segmented"
+    assert tds.Plan((1, 32, 4096), "x", 1, "periodic", P=4, dtype=torch.float32).variant == "segmented"
+    assert tds.Plan((1, 32, 512), "x", 1, "periodic", P=8).variant == "resident"
+    # chunks too short for 64-row segments fall back to streaming
+    assert tds.Plan((1, 32, 2048), "x", 1, "periodic", P=64).variant == "streaming"
+
+
 @pytest.mark.parametrize("variant", ["resident", "pipelined", "streaming"])
 @pytest.mark.parametrize("bc", ["periodic", "closed"])
 def test_minimum_chunk_and_line(variant, bc):
@@ -312,3 +343,21 @@ def test_gradcheck_32cubed_fast_mode():
     x = torch.randn(plan.numel, dtype=torch.float64, device="cuda", requires_grad=True)
     assert torch.autograd.gradcheck(lambda v: tds.compact_deriv(v, plan), (x,), eps=1e-6,
                                     atol=1e-7, rtol=1e-6, fast_mode=True)
+
+
+def test_device_wait_timeout_is_reported_and_context_survives():
+    """The bounded-wait failure path: a wait that nothing completes gives up, the status word
+    says TDS_ERR_TIMEOUT, and the context keeps working (no trap, no fault)."""
+    import ctypes
+    from paper_2411_13532_gb300 import _lib
+    L = _lib.lib()
+    assert tds.device_status() == 0
+    assert L.tds_selftest_timeout(ctypes.c_double(0.05), None) == _lib.OK
+    assert tds.device_status() == _lib.ERR_TIMEOUT
+    assert tds.device_status() == 0          # reading clears it
+    assert L.tds_selftest_timeout(ctypes.c_double(5.0), None) == _lib.ERR_ARG
+    shape = (1, 32, 64)
+    cart = np.random.default_rng(1).uniform(-1, 1, shape)
+    y = tds.Plan(shape, "x", 1, "periodic", P=2).deriv(to_device_layout(cart, "x", "f64"))
+    mx, _ = rel_errors(from_device_layout(y, "x", shape), oracle.deriv(cart, "x", 1, "periodic"))
+    assert mx <= 1e-12
