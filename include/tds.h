@@ -107,11 +107,23 @@ TDS_API tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_d
  * a divisor between 64 and the segment cap (128 rows FP64, 256 FP32), else STREAMING. */
 TDS_API tds_status tds_plan_set_variant(tds_plan *plan, tds_variant variant);
 
+/* Lines of a group held by one CTA of the RESIDENT variant: 32 (the whole group, one bulk
+ * copy per chunk), 16 or 8 (the group is split over 32/lines CTAs whose rows move as 2-D TMA
+ * tensor boxes, so that several CTAs share an SM and one CTA's copies overlap another's sweep).
+ * A layout choice only: every width gives the same result.  tds_plan_create picks the largest
+ * width that lets two CTAs share an SM.  TDS_ERR_ARG when the width is not 32, 16 or 8, the tile
+ * does not fit in one CTA's shared memory, fewer than two warps would remain per CTA (widths
+ * below 32), or the plan cannot run resident (P > 16).  Not part of the method (Sec. 4.1 fixes
+ * the 32-line group; its split over CTAs is a GPU layout decision). */
+TDS_API tds_status tds_plan_set_width(tds_plan *plan, int lines);
+
 /* Describe a plan: line length n, lines N, chunks P, the variant it will run, and the
  * dynamic shared memory per CTA of its resident kernel (0 if streaming).  Any output
- * pointer may be NULL. */
+ * pointer may be NULL.  tds_plan_width gives the resident CTA width (0 if the plan cannot run
+ * resident). */
 TDS_API tds_status tds_plan_info(const tds_plan *plan, int *n, int *nlines, int *P, int *variant,
                          int *smem_bytes);
+TDS_API tds_status tds_plan_width(const tds_plan *plan, int *lines);
 
 /* Bytes of device workspace tds_deriv / tds_deriv_adjoint need with this plan (0 is
  * possible).  The workspace must be 256-byte aligned; its contents need no initialisation

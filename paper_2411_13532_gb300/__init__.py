@@ -48,7 +48,7 @@ class Plan:
     """
 
     def __init__(self, shape, direction, order, bc, P=1, h=None, dtype=torch.float64,
-                 mode="exact", variant="auto", device=None):
+                 mode="exact", variant="auto", width=None, device=None):
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
         self.direction, self.order, self.bc, self.P = direction, int(order), bc, int(P)
@@ -66,6 +66,8 @@ class Plan:
                                          _lib.DTYPES[_TORCH_DTYPES[dtype]], 32,
                                          _lib.MODES[mode]), "tds_plan_create")
         self._handle = h_
+        if width is not None:
+            _lib.check(L.tds_plan_set_width(h_, int(width)), "tds_plan_set_width")
         if variant != "auto":
             _lib.check(L.tds_plan_set_variant(h_, _lib.VARIANTS[variant]), "tds_plan_set_variant")
         nbytes = ctypes.c_size_t()
@@ -77,6 +79,9 @@ class Plan:
         self.nlines = nl.value
         self.variant = {1: "resident", 2: "streaming", 3: "pipelined", 4: "segmented"}[var.value]
         self.smem_bytes = smem.value
+        w_ = ctypes.c_int()
+        _lib.check(L.tds_plan_width(h_, ctypes.byref(w_)), "tds_plan_width")
+        self.width = w_.value   # lines per resident CTA (0: cannot run resident)
         self.numel = nx * ny * nz
 
     def __del__(self):

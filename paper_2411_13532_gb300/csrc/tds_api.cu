@@ -32,6 +32,46 @@ size_t ws_need(const tds_plan *p) {
     return 0;
 }
 
+// Whether the resident kernel can run with w lines per CTA; two: and leave room for a second CTA
+// on the SM.  Below 32 lines a CTA keeps at least two warps, its rows move as TMA tensor boxes
+// (row coordinates below 2^31, 128-byte aligned box destinations).
+bool resident_width_ok(const tds_plan *p, int w, bool two) {
+    if (w != 32 && w != 16 && w != 8) return false;
+    if (p->P > kMaxResidentP) return false;
+    const size_t sm = resident_smem_bytes(p->n, p->P, p->dtype, w);
+    if (sm > (size_t)p->smem_optin) return false;
+    if (two && 2 * (sm + 1024) > (size_t)p->smem_sm) return false;
+    if (w < kSZ) {
+        const long long rows = (long long)p->n * (p->nlines / kSZ);
+        if (p->P * w < 64 || rows >= (1ll << 31) || resident_box_rows(p->n, p->m, p->dtype, w) == 0)
+            return false;
+    }
+    return true;
+}
+
+// Persistent pipelined kernel at the plan's width: two tile buffers per CTA (one in use, one
+// loading) when they fit, else one; as many such CTAs as fit on every SM.  TDS_PIPE_NBUF (1..4)
+// overrides the buffer count (tuning).
+void configure_pipe(tds_plan *p) {
+    p->pipe_nbuf = 0;
+    p->pipe_grid = 0;
+    if (!p->width) return;
+    int want = 2;
+    if (const char *e = std::getenv("TDS_PIPE_NBUF")) {
+        const int v = std::atoi(e);
+        if (v >= 1 && v <= 4) want = v;
+    }
+    for (int nb = want; nb >= 1; --nb)
+        if (pipe_smem_bytes(p->n, p->P, p->dtype, nb, p->width) <= (size_t)p->smem_optin) {
+            p->pipe_nbuf = nb;
+            break;
+        }
+    if (!p->pipe_nbuf) return;
+    const size_t per = pipe_smem_bytes(p->n, p->P, p->dtype, p->pipe_nbuf, p->width);
+    const int ctas = (int)((size_t)p->smem_sm / (per + 1024));
+    p->pipe_grid = p->nsm * (ctas > 0 ? ctas : 1);
+}
+
 tds_status run(const tds_plan *p, int which, const void *in, void *out, void *ws, size_t ws_bytes,
                void *stream) {
     if (!p || !in || !out) return TDS_ERR_ARG;
@@ -99,26 +139,32 @@ tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_dir dir, 
         tds_plan_destroy(p);
         return TDS_ERR_CUDA;
     }
-    const size_t smem = resident_smem_bytes(n, P, dtype);
-    p->resident_smem = (P <= kMaxResidentP && smem <= (size_t)optin) ? (int)smem : 0;
-    // persistent pipelined kernel: as many tile buffers (up to 4) as one CTA can hold, and as
-    // many such CTAs as fit on every SM
     int smem_sm = 0, nsm = 0;
     if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         tds_plan_destroy(p);
         return TDS_ERR_CUDA;
     }
-    p->pipe_nbuf = 0;
-    if (p->resident_smem) {
-        for (int nb = 4; nb >= 1; --nb)
-            if (pipe_smem_bytes(n, P, dtype, nb) <= (size_t)optin) { p->pipe_nbuf = nb; break; }
-        if (p->pipe_nbuf) {
-            const size_t per = pipe_smem_bytes(n, P, dtype, p->pipe_nbuf);
-            const int ctas = (int)((size_t)smem_sm / (per + 1024));
-            p->pipe_grid = nsm * (ctas > 0 ? ctas : 1);
-        }
+    p->smem_optin = optin;
+    p->smem_sm = smem_sm;
+    // Resident kernel width (lines per CTA: 32, 16 or 8), among those that let two CTAs share
+    // an SM.  FP32 sweeps are bound by HBM: the largest such width (fewest per-CTA overheads,
+    // the longest contiguous copies).  FP64 sweeps are bound by the FP64 pipe: the smallest
+    // (most CTAs per SM keep the pipe busy through each CTA's copy and reduced-system phases).
+    // Else 32 if a whole group fits at all.
+    p->width = 0;
+    if (dtype == TDS_F64) {
+        for (int w = 8; w <= kSZ; w *= 2)
+            if (resident_width_ok(p, w, true)) { p->width = w; break; }
+    } else {
+        for (int w = kSZ; w >= 8; w /= 2)
+            if (resident_width_ok(p, w, true)) { p->width = w; break; }
     }
+    if (!p->width && resident_width_ok(p, kSZ, false)) p->width = kSZ;
+    p->resident_smem = p->width ? (int)resident_smem_bytes(n, P, dtype, p->width) : 0;
+    p->box_rows = p->width ? resident_box_rows(n, n / P, dtype, p->width) : 0;
+    p->nsm = nsm;
+    configure_pipe(p);
     // lines per thread in the resident kernels; TDS_RESIDENT_LANES overrides (tuning)
     p->lanes = 1;
     if (const char *e = std::getenv("TDS_RESIDENT_LANES")) {
@@ -145,6 +191,15 @@ tds_status tds_plan_set_variant(tds_plan *p, tds_variant v) {
     return TDS_OK;
 }
 
+tds_status tds_plan_set_width(tds_plan *p, int lines) {
+    if (!p || !resident_width_ok(p, lines, false)) return TDS_ERR_ARG;
+    p->width = lines;
+    p->resident_smem = (int)resident_smem_bytes(p->n, p->P, p->dtype, lines);
+    p->box_rows = resident_box_rows(p->n, p->m, p->dtype, lines);
+    configure_pipe(p);
+    return TDS_OK;
+}
+
 tds_status tds_plan_info(const tds_plan *p, int *n, int *nlines, int *P, int *variant, int *smem) {
     if (!p) return TDS_ERR_ARG;
     if (n) *n = p->n;
@@ -153,8 +208,14 @@ tds_status tds_plan_info(const tds_plan *p, int *n, int *nlines, int *P, int *va
     if (variant) *variant = (int)p->variant;
     if (smem)
         *smem = p->variant == TDS_VARIANT_RESIDENT ? p->resident_smem
-              : p->variant == TDS_VARIANT_PIPELINED ? (int)pipe_smem_bytes(p->n, p->P, p->dtype, p->pipe_nbuf)
+              : p->variant == TDS_VARIANT_PIPELINED ? (int)pipe_smem_bytes(p->n, p->P, p->dtype, p->pipe_nbuf, p->width)
               : 0;
+    return TDS_OK;
+}
+
+tds_status tds_plan_width(const tds_plan *p, int *lines) {
+    if (!p || !lines) return TDS_ERR_ARG;
+    *lines = p->width;
     return TDS_OK;
 }
 

@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include <cuda.h>
+
 #include "tds_internal.h"
 
 namespace tds {
@@ -53,6 +55,23 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
                  ::"l"(dst), "r"(smem_u32(src)), "r"(bytes)
+                 : "memory");
+}
+
+// 2-D TMA tensor copy global -> shared of one box of `tmap` at element coordinates (x, y),
+// completion signalled on `bar`.  The destination is 128-byte aligned; x * element size is a
+// multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tmap, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// 2-D TMA tensor copy shared -> global of one box at (x, y) (x, y >= 0), tracked by bulk groups.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *tmap, int x, int y, const void *src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                 ::"l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(src))
                  : "memory");
 }
 

@@ -86,6 +86,11 @@ struct tds_plan {
     int n, m, nlines;
     tds_variant variant;   // resolved: RESIDENT, PIPELINED, SEGMENTED or STREAMING
     int resident_smem;     // dynamic shared memory of the resident kernel (0 = cannot run)
+    int width;             // lines per resident CTA: 32 (a whole group), 16 or 8
+    int box_rows;          // rows per TMA tensor box when width < 32
+    int smem_optin;        // device limits at plan creation: shared memory per block (opt-in)
+    int smem_sm;           //   and per SM
+    int nsm;               //   and the SM count
     int pipe_nbuf;         // > 0: run the persistent multi-buffered resident kernel
     int pipe_grid;         // its grid (resident CTAs the device holds at once)
     int lanes;             // lines per thread in the resident kernels (FP32: 1, 2, 4; FP64: 1, 2)
@@ -102,8 +107,11 @@ namespace tds {
 tds_status build_plan(tds_plan *p);
 
 // Kernel launchers (tds_kernels.cu).  Each returns TDS_ERR_CUDA on a launch failure.
-size_t resident_smem_bytes(int n, int P, tds_dtype dtype);
-size_t pipe_smem_bytes(int n, int P, tds_dtype dtype, int nbuf);
+size_t resident_smem_bytes(int n, int P, tds_dtype dtype, int w);
+// Rows per TMA box for a resident CTA of w < 32 lines (m itself for w = 32); 0 when the
+// chunk or box starts in the tile would not be 128-byte aligned.
+int resident_box_rows(int n, int m, tds_dtype dtype, int w);
+size_t pipe_smem_bytes(int n, int P, tds_dtype dtype, int nbuf, int w);
 tds_status launch_resident(const tds_plan *p, int which, const void *in, void *out,
                            cudaStream_t st);
 tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *out,

@@ -14,6 +14,10 @@
 //   output   : FP32 tiles leave with one TMA bulk store; FP64 tiles with per-thread stores.
 //
 // The sweep is written once over storage/arithmetic traits (FP32, FP64).
+#include <cstring>
+
+#include <cudaTypedefs.h>
+
 #include "tds_device.cuh"
 
 namespace tds {
@@ -36,10 +40,11 @@ __device__ __forceinline__ double mad(double a, double b, double c) { return ::f
 //   mid : an intermediate value (d_j, y_j) kept in the tile slot of its row
 //   out : a final value into the tile slot, as S
 // ------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, int W_ = kSZ>
 struct TrNative {
     using S = T;
     using A = T;
+    static constexpr int W = W_;   // lines per CTA: the row stride of the tile in shared memory
     static __device__ __forceinline__ A from_d(double x) { return A(x); }
     static __device__ __forceinline__ double to_d(A x) { return double(x); }
     template <int V>
@@ -99,6 +104,8 @@ struct TrNative {
 
 using TrF32 = TrNative<float>;
 using TrF64 = TrNative<double>;
+template <int W> using TrF32w = TrNative<float, W>;
+template <int W> using TrF64w = TrNative<double, W>;
 
 // Whether a finished tile leaves with one TMA bulk store (FP32: the sweep is HBM-bound) or
 // with per-thread stores that overlap the sweep (FP64 storage).
@@ -139,8 +146,8 @@ __device__ __forceinline__ void estencil(const DevOp &op, int e, const Pack<type
     }
 }
 
-// The rows of one group a CTA holds: line rows [r0, r1) are in `tile` (row r at (r - r0)*32);
-// other rows of the same group are read from HBM at `gin` (read-only input).
+// The rows of the W lines a CTA holds: line rows [r0, r1) are in `tile` (row r at (r - r0)*W);
+// other rows of the same lines are read from HBM at `gin` (read-only input, row stride 32).
 template <typename S>
 struct TileView {
     S *tile;
@@ -154,7 +161,7 @@ __device__ __forceinline__ Pack<typename Tr::A, V> ld_row(const DevOp &op, const
                                                           int J, int c, int &unsafe) {
     const int r = line_row(op, J);
     if (r < 0) return zero_a<Tr, V>();
-    const typename Tr::S *p = (r >= tv.r0 && r < tv.r1) ? tv.tile + (size_t)(r - tv.r0) * kSZ + c
+    const typename Tr::S *p = (r >= tv.r0 && r < tv.r1) ? tv.tile + (size_t)(r - tv.r0) * Tr::W + c
                                                         : tv.gin + (size_t)r * kSZ + c;
     return MID ? Tr::template ld_mid<V>(p) : Tr::template ld_in<V>(op, p, unsafe);
 }
@@ -177,10 +184,10 @@ __device__ __forceinline__ void read_halo(const DevOp &op, const TileView<typena
     }
     if (!op.periodic) {
         auto copy_row = [&](int src, int dst) {
-            const S *p = (src >= tv.r0 && src < tv.r1) ? tv.tile + (size_t)(src - tv.r0) * kSZ + c
+            const S *p = (src >= tv.r0 && src < tv.r1) ? tv.tile + (size_t)(src - tv.r0) * Tr::W + c
                                                        : tv.gin + (size_t)src * kSZ + c;
             if (!MID) (void)Tr::template ld_in<V>(op, p, unsafe);   // range check of the input
-            stv<S, V>(xs + (size_t)dst * kSZ + c, ldv<S, V>(p));
+            stv<S, V>(xs + (size_t)dst * Tr::W + c, ldv<S, V>(p));
         };
         if (K == 0)
             for (int i = 0; i < kTaps; ++i) copy_row(i, i);
@@ -201,7 +208,7 @@ __device__ __forceinline__ void fwd_row(const DevOp &op, int cls, int j, typenam
         dprev.v[i] = f * (sv[i] - r * dprev.v[i]);
         S.v[i] = mad(pi, dprev.v[i], S.v[i]);
     }
-    Tr::template st_mid<V>(row + (size_t)j * kSZ, dprev);
+    Tr::template st_mid<V>(row + (size_t)j * Tr::W, dprev);
 }
 
 // Interior row of the forward pass with f folded into the coefficients:
@@ -223,7 +230,7 @@ __device__ __forceinline__ void fwd_irow(const DevOp &op, int cls, int j, typena
         dprev.v[i] = mad(-g, dprev.v[i], base);
         if (ACC) S.v[i] = mad(p, dprev.v[i], S.v[i]);
     }
-    Tr::template st_mid<V>(row + (size_t)j * kSZ, dprev);
+    Tr::template st_mid<V>(row + (size_t)j * Tr::W, dprev);
 }
 
 // Interior forward rows [jb, je) reading v[j+2] from the tile (inside the chunk).
@@ -233,7 +240,7 @@ __device__ __forceinline__ void fwd_irows(const DevOp &op, int cls, typename Tr:
                                           Pack<typename Tr::A, V> &S, int &unsafe) {
 #pragma unroll 4
     for (int j = jb; j < je; ++j) {
-        w[4] = Tr::template ld_in<V>(op, row + (size_t)(j + 2) * kSZ, unsafe);
+        w[4] = Tr::template ld_in<V>(op, row + (size_t)(j + 2) * Tr::W, unsafe);
         fwd_irow<Tr, V, SYM, ACC>(op, cls, j, row, w, dprev, S);
 #pragma unroll
         for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
@@ -263,13 +270,13 @@ __device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typenam
     } else {
 #pragma unroll 4
         for (int j = jb; j < jm; ++j) {
-            w[4] = Tr::template ld_mid<V>(row + (size_t)(j + 2) * kSZ);
+            w[4] = Tr::template ld_mid<V>(row + (size_t)(j + 2) * Tr::W);
             A sv[V];
             istencil<A, V, SYM>(t0, t1, t2, w, sv);
             Pack<A, V> x;
 #pragma unroll
             for (int i = 0; i < V; ++i) x.v[i] = sv[i];
-            Tr::template st_out<V>(op, row + (size_t)j * kSZ, x);
+            Tr::template st_out<V>(op, row + (size_t)j * Tr::W, x);
 #pragma unroll
             for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
         }
@@ -284,7 +291,7 @@ __device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typenam
             Pack<A, V> x;
 #pragma unroll
             for (int i = 0; i < V; ++i) x.v[i] = sv[i];
-            Tr::template st_out<V>(op, row + (size_t)j * kSZ, x);
+            Tr::template st_out<V>(op, row + (size_t)j * Tr::W, x);
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
@@ -308,8 +315,8 @@ __device__ __forceinline__ void sweep_edge(const DevOp &op, int cls, typename Tr
                 const int x = t + o + xlo;
                 int dummy = 0;
                 w7[o] = (x >= 0 && x < xhi)
-                            ? (FWD ? Tr::template ld_in<V>(op, xs + (size_t)x * kSZ + c, dummy)
-                                   : Tr::template ld_mid<V>(xs + (size_t)x * kSZ + c))
+                            ? (FWD ? Tr::template ld_in<V>(op, xs + (size_t)x * Tr::W + c, dummy)
+                                   : Tr::template ld_mid<V>(xs + (size_t)x * Tr::W + c))
                             : zero_a<Tr, V>();
             }
             estencil<Tr, V>(op, e0 + t, w7, sv);
@@ -320,7 +327,7 @@ __device__ __forceinline__ void sweep_edge(const DevOp &op, int cls, typename Tr
             Pack<A, V> x;
 #pragma unroll
             for (int i = 0; i < V; ++i) x.v[i] = sv[i];
-            Tr::template st_out<V>(op, row + (size_t)(j0 + t) * kSZ, x);
+            Tr::template st_out<V>(op, row + (size_t)(j0 + t) * Tr::W, x);
         }
     }
 }
@@ -342,19 +349,19 @@ __device__ __forceinline__ void stencil_sweep(const DevOp &op, int k, int cls, t
     if (first_edge) {
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            w[i] = FWD ? Tr::template ld_in<V>(op, xs + (size_t)(2 + i) * kSZ + c, unsafe)
-                       : Tr::template ld_mid<V>(xs + (size_t)(2 + i) * kSZ + c);
+            w[i] = FWD ? Tr::template ld_in<V>(op, xs + (size_t)(2 + i) * Tr::W + c, unsafe)
+                       : Tr::template ld_mid<V>(xs + (size_t)(2 + i) * Tr::W + c);
     } else {
         w[0] = hb[0];
         w[1] = hb[1];
         w[2] = FWD ? Tr::template ld_in<V>(op, row, unsafe) : Tr::template ld_mid<V>(row);
-        w[3] = FWD ? Tr::template ld_in<V>(op, row + kSZ, unsafe) : Tr::template ld_mid<V>(row + kSZ);
+        w[3] = FWD ? Tr::template ld_in<V>(op, row + Tr::W, unsafe) : Tr::template ld_mid<V>(row + Tr::W);
     }
     if (op.symmetric > 0) sweep_interior<Tr, V, true, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
     else sweep_interior<Tr, V, false, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
     // the last 4 rows of a closed line: scratch rows 7..13 hold v[n-7..n-1]
     if (last_edge)
-        sweep_edge<Tr, V, FWD>(op, cls, row, m - 4, kEdgeRows, xs + (size_t)kTaps * kSZ, c, 0, kTaps, dprev, S);
+        sweep_edge<Tr, V, FWD>(op, cls, row, m - 4, kEdgeRows, xs + (size_t)kTaps * Tr::W, c, 0, kTaps, dprev, S);
 }
 
 // Forward pass of chunk K (rows at `row` in the tile): the fused stencil (forward operator) or
@@ -374,14 +381,14 @@ __device__ __forceinline__ void forward_phase(const DevOp &op, typename Tr::S *r
         auto arow = [&](int j, bool acc) {
             A c0, c1, c2, gg;
             Tr::ifw(op, cls, j, c0, c1, c2, gg);
-            const Pack<A, V> g = Tr::template ld_in<V>(op, row + (size_t)j * kSZ, unsafe);
+            const Pack<A, V> g = Tr::template ld_in<V>(op, row + (size_t)j * Tr::W, unsafe);
             const A p = acc ? Tr::pi(op, cls, j) : A(0);
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 dprev.v[i] = mad(-gg, dprev.v[i], c0 * g.v[i]);
                 if (acc) Ssum.v[i] = mad(p, dprev.v[i], Ssum.v[i]);
             }
-            Tr::template st_mid<V>(row + (size_t)j * kSZ, dprev);
+            Tr::template st_mid<V>(row + (size_t)j * Tr::W, dprev);
         };
         const int jp = Tr::jpi(op, cls) < m ? Tr::jpi(op, cls) : m;
 #pragma unroll 4
@@ -419,15 +426,15 @@ __device__ __forceinline__ void backsub_phase(const DevOp &op, typename Tr::S *r
     using A = typename Tr::A;
     const int m = op.m;
     auto put = [&](int j, const Pack<A, V> &v) {
-        if (MID) Tr::template st_mid<V>(row + (size_t)j * kSZ, v);
-        else Tr::template st_out<V>(op, row + (size_t)j * kSZ, v);
+        if (MID) Tr::template st_mid<V>(row + (size_t)j * Tr::W, v);
+        else Tr::template st_out<V>(op, row + (size_t)j * Tr::W, v);
     };
     put(m - 1, u);
     // rows at or past the s^a cut-off: u_j = d_j - s^c_j u_{j+1}
     const int js = Tr::jsa(op, cls) > 1 ? Tr::jsa(op, cls) : 1;
 #pragma unroll 4
     for (int j = m - 2; j >= js; --j) {
-        const Pack<A, V> d = Tr::template ld_mid<V>(row + (size_t)j * kSZ);
+        const Pack<A, V> d = Tr::template ld_mid<V>(row + (size_t)j * Tr::W);
         A sa, sc;
         Tr::bwd(op, cls, j, sa, sc);
 #pragma unroll
@@ -436,7 +443,7 @@ __device__ __forceinline__ void backsub_phase(const DevOp &op, typename Tr::S *r
     }
 #pragma unroll 4
     for (int j = (js < m - 1 ? js : m - 1) - 1; j >= 1; --j) {
-        const Pack<A, V> d = Tr::template ld_mid<V>(row + (size_t)j * kSZ);
+        const Pack<A, V> d = Tr::template ld_mid<V>(row + (size_t)j * Tr::W);
         A sa, sc;
         Tr::bwd(op, cls, j, sa, sc);
 #pragma unroll
@@ -458,7 +465,7 @@ __device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *til
     using S = typename Tr::S;
     const int m = op.m, P = op.P;
     const int cls = chunk_class(op, k);
-    S *row = tile + (size_t)k * m * kSZ + c;
+    S *row = tile + (size_t)k * m * Tr::W + c;
     Pack<A, V> dprev = zero_a<Tr, V>(), Ssum = zero_a<Tr, V>();
 
     forward_phase<Tr, V, ADJ>(op, row, xs, k, cls, c, hb, ha, dprev, Ssum, unsafe);
@@ -467,8 +474,8 @@ __device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *til
         chunk_ends<Tr, V>(op, row, cls, dprev, Ssum, e0, e1);
 #pragma unroll
         for (int i = 0; i < V; ++i) {
-            ends[(size_t)(2 * k) * kSZ + c + i] = e0[i];
-            ends[(size_t)(2 * k + 1) * kSZ + c + i] = e1[i];
+            ends[(size_t)(2 * k) * Tr::W + c + i] = e0[i];
+            ends[(size_t)(2 * k + 1) * Tr::W + c + i] = e1[i];
         }
     }
     __syncthreads();
@@ -483,23 +490,23 @@ __device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *til
         const double inv = __ldg(op.red + (size_t)kRedBinv * R + k);
 #pragma unroll
         for (int i = 0; i < V; ++i) {
-            double *ef = ends + (size_t)(2 * k) * kSZ + c + i;
-            double *el = ends + (size_t)(2 * prev + 1) * kSZ + c + i;
+            double *ef = ends + (size_t)(2 * k) * Tr::W + c + i;
+            double *el = ends + (size_t)(2 * prev + 1) * Tr::W + c + i;
             const double dl = *el;
             const double Fk = (*ef - a * dl) * inv;
             *ef = Fk;
             *el = dl - cc * Fk;
         }
     } else {
-        for (int l = threadIdx.x; l < kSZ; l += blockDim.x) reduced_solve(op, ends + l, kSZ);
+        for (int l = threadIdx.x; l < Tr::W; l += blockDim.x) reduced_solve(op, ends + l, Tr::W);
     }
     __syncthreads();
 
     Pack<A, V> F, L;
 #pragma unroll
     for (int i = 0; i < V; ++i) {
-        F.v[i] = Tr::from_d(ends[(size_t)(2 * k) * kSZ + c + i]);
-        L.v[i] = Tr::from_d(ends[(size_t)(2 * k + 1) * kSZ + c + i]);
+        F.v[i] = Tr::from_d(ends[(size_t)(2 * k) * Tr::W + c + i]);
+        L.v[i] = Tr::from_d(ends[(size_t)(2 * k + 1) * Tr::W + c + i]);
     }
     backsub_phase<Tr, V, ADJ>(op, row, cls, F, L);
     if (ADJ) {
@@ -513,50 +520,82 @@ __device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *til
     }
 }
 
-// Shared-memory layout of the resident kernels:
-//   tiles[nbuf][n][32] (S) | xs[14][32] (S, closure rows) | ends[2P][32] (double) | bars
-__host__ __device__ inline size_t tile_bytes_of(int n, size_t es) { return (size_t)n * kSZ * es; }
-__host__ __device__ inline size_t xs_bytes_of(size_t es) { return ((size_t)2 * kTaps * kSZ * es + 15) & ~(size_t)15; }
+// Shared-memory layout of the resident kernels (W lines per CTA):
+//   tiles[nbuf][n][W] (S) | xs[14][W] (S, closure rows) | ends[2P][W] (double) | bars
+__host__ __device__ inline size_t tile_bytes_of(int n, size_t es, int w = kSZ) { return (size_t)n * w * es; }
+__host__ __device__ inline size_t xs_bytes_of(size_t es, int w = kSZ) {
+    return ((size_t)2 * kTaps * w * es + 15) & ~(size_t)15;
+}
 
-// The finished tile (in shared memory) to HBM.
+// A CTA that holds W < 32 lines of a group moves its rows with 2-D TMA tensor copies: the field
+// is seen as a [rows][32] array (rows = n x groups, row stride 32 elements) and one box is
+// box_rows rows of W elements (box_rows divides the chunk length m, at most 256).
+struct TileMaps {
+    CUtensorMap in, out;
+    int box_rows;
+};
+
+// The finished tile (in shared memory) to HBM.  og: the first element of this CTA's lines of
+// the group; y0: the group's first row in the [rows][32] view; x0: its first line.
 template <typename Tr, int V>
-__device__ __forceinline__ void store_tile(const DevOp &op, const typename Tr::S *tile,
-                                           typename Tr::S *og, int k, int c) {
+__device__ __forceinline__ void store_tile(const DevOp &op, const TileMaps &tm, const typename Tr::S *tile,
+                                           typename Tr::S *og, int x0, int y0, int k, int c) {
     using S = typename Tr::S;
     if (kBulkStore<Tr>) {
         fence_async_smem();   // this thread's tile writes are visible to the bulk store
         __syncthreads();
         if (threadIdx.x == 0) {
-            bulk_s2g(og, tile, (uint32_t)tile_bytes_of(op.n, sizeof(S)));
+            if constexpr (Tr::W == kSZ) {
+                bulk_s2g(og, tile, (uint32_t)tile_bytes_of(op.n, sizeof(S)));
+            } else {
+                for (int r = 0; r < op.n; r += tm.box_rows)
+                    tma_store_2d(&tm.out, x0, y0 + r, tile + (size_t)r * Tr::W);
+            }
             bulk_commit();
             bulk_wait_read();   // shared memory must stay valid until the copy has read it
         }
     } else {
-        const size_t o = (size_t)k * op.m * kSZ + c;
+        const size_t ot = (size_t)k * op.m * Tr::W + c, ob = (size_t)k * op.m * kSZ + c;
 #pragma unroll 4
         for (int j = 0; j < op.m; ++j)
-            stv<S, V>(og + o + (size_t)j * kSZ, ldv<S, V>(tile + o + (size_t)j * kSZ));
+            stv<S, V>(og + ob + (size_t)j * kSZ, ldv<S, V>(tile + ot + (size_t)j * Tr::W));
     }
 }
 
-// One CTA per group, P * 32/V threads.  The tile arrives as one TMA bulk copy per chunk; a
-// thread starts as soon as its own chunk and its neighbours' have landed.
+// One CTA per W lines of a group (32/W CTAs per group), P * W/V threads.  The tile arrives as
+// TMA copies, one mbarrier per chunk (W = 32: one bulk copy of the contiguous chunk; W < 32:
+// m / box_rows tensor boxes); a thread starts as soon as its own chunk and its neighbours'
+// have landed.
 template <typename Tr, int V, bool ADJ>
 __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_constant__ DevOp op,
+                                                                 const __grid_constant__ TileMaps tm,
                                                                  const typename Tr::S *__restrict__ in,
                                                                  typename Tr::S *__restrict__ out) {
     using S = typename Tr::S;
+    constexpr int W = Tr::W;
+    constexpr int tpc = W / V;
+    constexpr int parts = kSZ / W;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int failed;
     const int n = op.n, m = op.m, P = op.P;
-    constexpr int tpc = kSZ / V;
     const int k = threadIdx.x / tpc, c = (threadIdx.x % tpc) * V;
-    const size_t gofs = (size_t)blockIdx.x * n * kSZ;
+    const long long g = blockIdx.x / parts;
+    const int x0 = (int)(blockIdx.x % parts) * W;
+    const int y0 = (int)(g * n);                                // < 2^31, checked by the host
+    const size_t gofs = (size_t)g * n * kSZ + x0;
     S *tile = reinterpret_cast<S *>(smem);
-    S *xs = reinterpret_cast<S *>(smem + tile_bytes_of(n, sizeof(S)));
-    double *ends = reinterpret_cast<double *>(smem + tile_bytes_of(n, sizeof(S)) + xs_bytes_of(sizeof(S)));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(ends + (size_t)2 * P * kSZ);
-    const uint32_t chunk_bytes = (uint32_t)((size_t)m * kSZ * sizeof(S));
+    S *xs = reinterpret_cast<S *>(smem + tile_bytes_of(n, sizeof(S), W));
+    double *ends = reinterpret_cast<double *>(smem + tile_bytes_of(n, sizeof(S), W) + xs_bytes_of(sizeof(S), W));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ends + (size_t)2 * P * W);
+    const uint32_t chunk_bytes = (uint32_t)((size_t)m * W * sizeof(S));
+    if constexpr (W < kSZ) {
+        // tensor boxes land on 128-byte boundaries of the tile; never issue a misaligned one
+        // (the same address for every thread: the whole CTA returns)
+        if ((smem_u32(tile) & 127u) != 0) {
+            if (threadIdx.x == 0) atomicExch(&g_device_status, (int)TDS_ERR_CUDA);
+            return;
+        }
+    }
 
     if (threadIdx.x == 0) {
         failed = 0;
@@ -567,7 +606,12 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_co
     if (threadIdx.x == 0) {
         for (int q = 0; q < P; ++q) {
             mbar_expect_tx(&bars[q], chunk_bytes);
-            bulk_g2s(tile + (size_t)q * m * kSZ, in + gofs + (size_t)q * m * kSZ, chunk_bytes, &bars[q]);
+            if constexpr (W == kSZ) {
+                bulk_g2s(tile + (size_t)q * m * W, in + gofs + (size_t)q * m * kSZ, chunk_bytes, &bars[q]);
+            } else {
+                for (int r = q * m; r < (q + 1) * m; r += tm.box_rows)
+                    tma_load_2d(tile + (size_t)r * W, &tm.in, x0, y0 + r, &bars[q]);
+            }
         }
     }
     bool ok = mbar_wait(&bars[k], 0);
@@ -584,34 +628,58 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_co
     if (!ADJ && ok) read_halo<Tr, V, false>(op, TileView<S>{tile, 0, n, in + gofs}, xs, k, c, hb, ha, unsafe);
     __syncthreads();
     if (failed) {
-        // let every bulk copy land before the CTA's shared memory is released
+        // let every copy land before the CTA's shared memory is released
         for (int q = threadIdx.x; q < P; q += blockDim.x) mbar_wait(&bars[q], 0);
         if (threadIdx.x == 0) record_timeout();
         return;
     }
     group_sweep<Tr, V, ADJ>(op, tile, xs, ends, k, c, hb, ha, unsafe);
-    store_tile<Tr, V>(op, tile, out + gofs, k, c);
+    store_tile<Tr, V>(op, tm, tile, out + gofs, x0, y0, k, c);
 }
 
-// Persistent variant: each CTA walks groups blockIdx.x, +gridDim.x, ... through `nbuf` tile
-// buffers; the TMA bulk copy of a group is issued `nbuf` groups ahead, so HBM reads stay in
-// flight while the threads sweep.  
+// Persistent variant: each CTA walks units (W lines of a group) blockIdx.x, +gridDim.x, ...
+// through `nbuf` tile buffers; the TMA copies of a unit are issued `nbuf` units ahead, so HBM
+// reads stay in flight while the threads sweep.
 template <typename Tr, int V, bool ADJ>
 __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_pipe(const __grid_constant__ DevOp op,
+                                                                      const __grid_constant__ TileMaps tm,
                                                                       const typename Tr::S *__restrict__ in,
                                                                       typename Tr::S *__restrict__ out, int nbuf) {
     using S = typename Tr::S;
+    constexpr int W = Tr::W;
+    constexpr int tpc = W / V;
+    constexpr int parts = kSZ / W;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int failed;
-    const int n = op.n, P = op.P, G = op.ngroups;
-    constexpr int tpc = kSZ / V;
+    const int n = op.n, P = op.P;
+    const long long U = (long long)op.ngroups * parts;
     const int k = threadIdx.x / tpc, c = (threadIdx.x % tpc) * V;
-    const size_t tile_elems = (size_t)n * kSZ;
-    const uint32_t tile_bytes = (uint32_t)tile_bytes_of(n, sizeof(S));
+    const size_t tile_elems = (size_t)n * W;
+    const uint32_t tile_bytes = (uint32_t)tile_bytes_of(n, sizeof(S), W);
     S *tiles = reinterpret_cast<S *>(smem);
     S *xs = reinterpret_cast<S *>(smem + (size_t)nbuf * tile_bytes);
-    double *ends = reinterpret_cast<double *>(smem + (size_t)nbuf * tile_bytes + xs_bytes_of(sizeof(S)));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(ends + (size_t)2 * P * kSZ);
+    double *ends = reinterpret_cast<double *>(smem + (size_t)nbuf * tile_bytes + xs_bytes_of(sizeof(S), W));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ends + (size_t)2 * P * W);
+    if constexpr (W < kSZ) {
+        if ((smem_u32(tiles) & 127u) != 0) {   // see k_resident
+            if (threadIdx.x == 0) atomicExch(&g_device_status, (int)TDS_ERR_CUDA);
+            return;
+        }
+    }
+    // first element of unit u's lines, and its (line, row) coordinates in the [rows][32] view
+    auto unit_ofs = [&](long long u) { return (size_t)(u / parts) * n * kSZ + (size_t)(u % parts) * W; };
+    auto unit_x0 = [&](long long u) { return (int)(u % parts) * W; };
+    auto unit_y0 = [&](long long u) { return (int)((u / parts) * n); };
+    auto issue_load = [&](long long u, int b) {
+        S *tile = tiles + (size_t)b * tile_elems;
+        mbar_expect_tx(&bars[b], tile_bytes);
+        if constexpr (W == kSZ) {
+            bulk_g2s(tile, in + unit_ofs(u), tile_bytes, &bars[b]);
+        } else {
+            for (int r = 0; r < n; r += tm.box_rows)
+                tma_load_2d(tile + (size_t)r * W, &tm.in, unit_x0(u), unit_y0(u) + r, &bars[b]);
+        }
+    };
 
     if (threadIdx.x == 0) {
         failed = 0;
@@ -621,55 +689,56 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_pipe(const __gr
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int b = 0; b < nbuf; ++b) {
-            const long long g = blockIdx.x + (long long)b * gridDim.x;
-            if (g >= G) break;
-            mbar_expect_tx(&bars[b], tile_bytes);
-            bulk_g2s(tiles + (size_t)b * tile_elems, in + (size_t)g * tile_elems, tile_bytes, &bars[b]);
+            const long long u = blockIdx.x + (long long)b * gridDim.x;
+            if (u >= U) break;
+            issue_load(u, b);
         }
     }
     for (int it = 0;; ++it) {
-        const long long g = blockIdx.x + (long long)it * gridDim.x;
-        if (g >= G) break;
+        const long long u = blockIdx.x + (long long)it * gridDim.x;
+        if (u >= U) break;
         const int b = it % nbuf;
         S *tile = tiles + (size_t)b * tile_elems;
         const bool ok = mbar_wait(&bars[b], (uint32_t)((it / nbuf) & 1));
         if (!ok) atomicExch(&failed, 1);
         int unsafe = 0;
         Pack<typename Tr::A, V> hb[2], ha[2];
-        if (!ADJ && ok) read_halo<Tr, V, false>(op, TileView<S>{tile, 0, n, in + (size_t)g * tile_elems}, xs, k, c, hb, ha, unsafe);
+        if (!ADJ && ok) read_halo<Tr, V, false>(op, TileView<S>{tile, 0, n, in + unit_ofs(u)}, xs, k, c, hb, ha, unsafe);
         __syncthreads();
         if (failed) {
-            // drain every bulk copy still in flight into this CTA's buffers, then give up
+            // drain every copy still in flight into this CTA's buffers, then give up
             for (int d = threadIdx.x; d < nbuf; d += blockDim.x)
-                if (blockIdx.x + (long long)(it + d) * gridDim.x < G)
+                if (blockIdx.x + (long long)(it + d) * gridDim.x < U)
                     mbar_wait(&bars[(it + d) % nbuf], (uint32_t)(((it + d) / nbuf) & 1));
             if (threadIdx.x == 0) record_timeout();
             return;
         }
         group_sweep<Tr, V, ADJ>(op, tile, xs, ends, k, c, hb, ha, unsafe);
-        S *og = out + (size_t)g * tile_elems;
-        if (kBulkStore<Tr>) {
-            fence_async_smem();
-        } else {
-            const size_t o = (size_t)k * op.m * kSZ + c;
+        S *og = out + unit_ofs(u);
+        if (!kBulkStore<Tr>) {
+            const size_t ot = (size_t)k * op.m * W + c, ob = (size_t)k * op.m * kSZ + c;
 #pragma unroll 4
             for (int j = 0; j < op.m; ++j)
-                stv<S, V>(og + o + (size_t)j * kSZ, ldv<S, V>(tile + o + (size_t)j * kSZ));
+                stv<S, V>(og + ob + (size_t)j * kSZ, ldv<S, V>(tile + ot + (size_t)j * W));
         }
+        // this thread's tile accesses are ordered before the async proxy (bulk store, refill)
+        fence_async_smem();
         __syncthreads();   // every thread is done with this tile, the scratch rows and `ends`
         if (threadIdx.x == 0) {
             if (kBulkStore<Tr>) {
-                bulk_s2g(og, tile, tile_bytes);
+                if constexpr (W == kSZ) {
+                    bulk_s2g(og, tile, tile_bytes);
+                } else {
+                    for (int r = 0; r < n; r += tm.box_rows)
+                        tma_store_2d(&tm.out, unit_x0(u), unit_y0(u) + r, tile + (size_t)r * W);
+                }
                 bulk_commit();
             }
-            const long long gn = g + (long long)nbuf * gridDim.x;
-            if (gn < G) {
-                // the buffer is refilled only after the store has read it, and generic-proxy
-                // accesses are ordered before the async refill
+            const long long un = u + (long long)nbuf * gridDim.x;
+            if (un < U) {
+                // the buffer is refilled only after the store has read it
                 if (kBulkStore<Tr>) bulk_wait_read();
-                fence_async_smem();
-                mbar_expect_tx(&bars[b], tile_bytes);
-                bulk_g2s(tile, in + (size_t)gn * tile_elems, tile_bytes, &bars[b]);
+                issue_load(un, b);
             }
         }
     }
@@ -694,6 +763,7 @@ __global__ void __launch_bounds__(32) k_seg_forward(const __grid_constant__ DevO
                                                     double *__restrict__ ws) {
     using S = typename Tr::S;
     using A = typename Tr::A;
+    static_assert(Tr::W == kSZ, "one warp per segment of a 32-line group");
     extern __shared__ __align__(128) unsigned char smem[];
     const int n = op.n, m = op.m, P = op.P, c = threadIdx.x;
     const long long g = blockIdx.x / P;
@@ -743,6 +813,7 @@ __global__ void __launch_bounds__(32) k_seg_backward(const __grid_constant__ Dev
                                                      const double *__restrict__ ws) {
     using S = typename Tr::S;
     using A = typename Tr::A;
+    static_assert(Tr::W == kSZ, "one warp per segment of a 32-line group");
     extern __shared__ __align__(128) unsigned char smem[];
     const int n = op.n, m = op.m, P = op.P, c = threadIdx.x;
     const long long g = blockIdx.x / P;
@@ -821,66 +892,141 @@ tds_status launch_segmented_t(const DevOp &op, const void *in, void *out, void *
 }
 
 template <typename Tr, int V, bool ADJ>
-tds_status launch_resident_t(const DevOp &op, const void *in, void *out, int smem, cudaStream_t st) {
+tds_status launch_resident_t(const DevOp &op, const TileMaps &tm, const void *in, void *out, int smem,
+                             cudaStream_t st) {
     using S = typename Tr::S;
     auto kern = k_resident<Tr, V, ADJ>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return TDS_ERR_CUDA;
-    kern<<<op.ngroups, op.P * (kSZ / V), smem, st>>>(op, static_cast<const S *>(in), static_cast<S *>(out));
+    const unsigned grid = (unsigned)((long long)op.ngroups * (kSZ / Tr::W));
+    kern<<<grid, op.P * (Tr::W / V), smem, st>>>(op, tm, static_cast<const S *>(in), static_cast<S *>(out));
     return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
 }
 
 template <typename Tr, bool ADJ>
-tds_status launch_pipe_t(const DevOp &op, const void *in, void *out, int nbuf, int smem, int grid,
-                         cudaStream_t st) {
+tds_status launch_pipe_t(const DevOp &op, const TileMaps &tm, const void *in, void *out, int nbuf, int smem,
+                         int grid, cudaStream_t st) {
     using S = typename Tr::S;
     auto kern = k_resident_pipe<Tr, 1, ADJ>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return TDS_ERR_CUDA;
-    kern<<<grid, op.P * kSZ, smem, st>>>(op, static_cast<const S *>(in), static_cast<S *>(out), nbuf);
+    kern<<<grid, op.P * Tr::W, smem, st>>>(op, tm, static_cast<const S *>(in), static_cast<S *>(out), nbuf);
     return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
 }
 
-template <typename Tr, int V>
-tds_status launch_resident_v(const tds_plan *p, int which, const void *in, void *out, cudaStream_t st) {
+template <typename Tr>
+tds_status launch_pipe_w(const tds_plan *p, int which, const TileMaps &tm, const void *in, void *out,
+                         cudaStream_t st) {
     const DevOp &op = p->op[which];
-    return which ? launch_resident_t<Tr, V, true>(op, in, out, p->resident_smem, st)
-                 : launch_resident_t<Tr, V, false>(op, in, out, p->resident_smem, st);
+    const int smem = (int)pipe_smem_bytes(p->n, p->P, p->dtype, p->pipe_nbuf, Tr::W);
+    const long long units = (long long)op.ngroups * (kSZ / Tr::W);
+    const int grid = units < p->pipe_grid ? (int)units : p->pipe_grid;
+    return which ? launch_pipe_t<Tr, true>(op, tm, in, out, p->pipe_nbuf, smem, grid, st)
+                 : launch_pipe_t<Tr, false>(op, tm, in, out, p->pipe_nbuf, smem, grid, st);
+}
+
+template <typename Tr, int V>
+tds_status launch_resident_v(const tds_plan *p, int which, const TileMaps &tm, const void *in, void *out,
+                             cudaStream_t st) {
+    const DevOp &op = p->op[which];
+    return which ? launch_resident_t<Tr, V, true>(op, tm, in, out, p->resident_smem, st)
+                 : launch_resident_t<Tr, V, false>(op, tm, in, out, p->resident_smem, st);
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link against the driver API).
+using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// The field at `base` as a [rows][32] tensor with box [box_rows][w].
+bool encode_rows(CUtensorMap *map, const void *base, tds_dtype dt, long long rows, int w, int box_rows) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t es = (dt == TDS_F64) ? 8 : 4;
+    const cuuint64_t dims[2] = {(cuuint64_t)kSZ, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kSZ * es};
+    const cuuint32_t box[2] = {(cuuint32_t)w, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, dt == TDS_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+              const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 } // namespace
 
-size_t resident_smem_bytes(int n, int P, tds_dtype dtype) {
+size_t resident_smem_bytes(int n, int P, tds_dtype dtype, int w) {
     const size_t es = (dtype == TDS_F64) ? 8 : 4;
-    return tile_bytes_of(n, es) + xs_bytes_of(es) + (size_t)2 * P * kSZ * 8 + (size_t)P * 8;
+    return tile_bytes_of(n, es, w) + xs_bytes_of(es, w) + (size_t)2 * P * w * 8 + (size_t)P * 8;
 }
 
-size_t pipe_smem_bytes(int n, int P, tds_dtype dtype, int nbuf) {
+int resident_box_rows(int n, int m, tds_dtype dtype, int w) {
     const size_t es = (dtype == TDS_F64) ? 8 : 4;
-    return (size_t)nbuf * tile_bytes_of(n, es) + xs_bytes_of(es) + (size_t)2 * P * kSZ * 8 + (size_t)nbuf * 8;
+    if (w == kSZ) return m;
+    int box = 0;
+    for (int d = 256; d >= 1; --d)
+        if (m % d == 0) { box = d; break; }
+    // every box destination (chunk starts and box starts in the tile) 128-byte aligned
+    if (((size_t)box * w * es) % 128 != 0 || ((size_t)m * w * es) % 128 != 0 || n % box != 0) return 0;
+    return box;
+}
+
+size_t pipe_smem_bytes(int n, int P, tds_dtype dtype, int nbuf, int w) {
+    const size_t es = (dtype == TDS_F64) ? 8 : 4;
+    return (size_t)nbuf * tile_bytes_of(n, es, w) + xs_bytes_of(es, w) + (size_t)2 * P * w * 8 + (size_t)nbuf * 8;
 }
 
 // Lines per thread (tds_plan::lanes): FP32 1, 2 or 4; FP64 1 or 2.  More lanes spread the per-row
 // work (plan records, addressing, loop control) over more points and give each thread
 // independent recurrences; fewer lanes give more threads.
+// Tensor maps of this call's fields when the plan's CTAs hold fewer than 32 lines.
+bool tile_maps(const tds_plan *p, const void *in, void *out, TileMaps *tm) {
+    std::memset(tm, 0, sizeof(*tm));
+    tm->box_rows = p->box_rows;
+    if (p->width == kSZ) return true;
+    const long long rows = (long long)p->n * (p->nlines / kSZ);
+    if (!encode_rows(&tm->in, in, p->dtype, rows, p->width, p->box_rows)) return false;
+    return p->dtype != TDS_F32 || encode_rows(&tm->out, out, p->dtype, rows, p->width, p->box_rows);
+}
+
 tds_status launch_resident(const tds_plan *p, int which, const void *in, void *out, cudaStream_t st) {
-    if (p->dtype == TDS_F64)
-        return p->lanes == 2 ? launch_resident_v<TrF64, 2>(p, which, in, out, st)
-                             : launch_resident_v<TrF64, 1>(p, which, in, out, st);
-    return p->lanes == 4 ? launch_resident_v<TrF32, 4>(p, which, in, out, st)
-         : p->lanes == 2 ? launch_resident_v<TrF32, 2>(p, which, in, out, st)
-                         : launch_resident_v<TrF32, 1>(p, which, in, out, st);
+    TileMaps tm;
+    if (!tile_maps(p, in, out, &tm)) return TDS_ERR_CUDA;
+    const int W = p->width;
+    if (p->dtype == TDS_F64) {
+        if (W == 16) return launch_resident_v<TrF64w<16>, 1>(p, which, tm, in, out, st);
+        if (W == 8) return launch_resident_v<TrF64w<8>, 1>(p, which, tm, in, out, st);
+        return p->lanes == 2 ? launch_resident_v<TrF64, 2>(p, which, tm, in, out, st)
+                             : launch_resident_v<TrF64, 1>(p, which, tm, in, out, st);
+    }
+    if (W == 16) return launch_resident_v<TrF32w<16>, 1>(p, which, tm, in, out, st);
+    if (W == 8) return launch_resident_v<TrF32w<8>, 1>(p, which, tm, in, out, st);
+    return p->lanes == 4 ? launch_resident_v<TrF32, 4>(p, which, tm, in, out, st)
+         : p->lanes == 2 ? launch_resident_v<TrF32, 2>(p, which, tm, in, out, st)
+                         : launch_resident_v<TrF32, 1>(p, which, tm, in, out, st);
 }
 
 tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *out, cudaStream_t st) {
-    const DevOp &op = p->op[which];
-    const int smem = (int)pipe_smem_bytes(p->n, p->P, p->dtype, p->pipe_nbuf);
-    const int grid = op.ngroups < p->pipe_grid ? op.ngroups : p->pipe_grid;
+    TileMaps tm;
+    if (!tile_maps(p, in, out, &tm)) return TDS_ERR_CUDA;
+    const int W = p->width;
     if (p->dtype == TDS_F64)
-        return which ? launch_pipe_t<TrF64, true>(op, in, out, p->pipe_nbuf, smem, grid, st)
-                     : launch_pipe_t<TrF64, false>(op, in, out, p->pipe_nbuf, smem, grid, st);
-    return which ? launch_pipe_t<TrF32, true>(op, in, out, p->pipe_nbuf, smem, grid, st)
-                 : launch_pipe_t<TrF32, false>(op, in, out, p->pipe_nbuf, smem, grid, st);
+        return W == 16 ? launch_pipe_w<TrF64w<16>>(p, which, tm, in, out, st)
+             : W == 8  ? launch_pipe_w<TrF64w<8>>(p, which, tm, in, out, st)
+                       : launch_pipe_w<TrF64>(p, which, tm, in, out, st);
+    return W == 16 ? launch_pipe_w<TrF32w<16>>(p, which, tm, in, out, st)
+         : W == 8  ? launch_pipe_w<TrF32w<8>>(p, which, tm, in, out, st)
+                   : launch_pipe_w<TrF32>(p, which, tm, in, out, st);
 }
 
 namespace {

@@ -75,6 +75,9 @@ def test_null_pointer_errors_need_no_gpu(L):
     sz = ctypes.c_size_t()
     assert L.tds_workspace_bytes(None, ctypes.byref(sz)) == _lib.ERR_ARG
     assert L.tds_reorder(None, None, 32, 32, 1, 0, 1, 0, 32, None) == _lib.ERR_ARG
+    assert L.tds_plan_set_width(None, 32) == _lib.ERR_ARG
+    w = ctypes.c_int()
+    assert L.tds_plan_width(None, ctypes.byref(w)) == _lib.ERR_ARG
     L.tds_plan_destroy(None)
 
 

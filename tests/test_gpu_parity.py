@@ -63,6 +63,53 @@ def test_small_grid_every_point(dtype, variant, direction, order, bc, adjoint):
         assert mx <= TOL[dtype], (P, mx, rms)
 
 
+WSHAPE = (32, 48, 64)   # x lines 1536 (48 groups), y lines 2048, z lines 3072
+WIDTH_P = {16: {"x": 4, "y": 4, "z": 4}, 8: {"x": 8, "y": 12, "z": 8}}
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("variant", ["resident", "pipelined"])
+@pytest.mark.parametrize("width", [16, 8])
+@pytest.mark.parametrize("direction", ["x", "y", "z"])
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_resident_width_every_point(dtype, variant, width, direction, order, bc, adjoint):
+    """A group split over 32/width CTAs (rows moved as 2-D TMA tensor boxes), one CTA per unit
+    or persistent CTAs walking the units: every point against the oracle."""
+    P = WIDTH_P[width][direction]
+    cart = np.random.default_rng(width + P).uniform(-1, 1, WSHAPE)
+    if dtype == "f32":
+        cart = cart.astype(np.float32).astype(np.float64)
+    n = {"x": WSHAPE[2], "y": WSHAPE[1], "z": WSHAPE[0]}[direction]
+    h = oracle.grid_spacing(n, bc)
+    plan = tds.Plan(WSHAPE, direction, order, bc, P=P, h=h, dtype=TORCH[dtype], variant=variant,
+                    width=width)
+    assert plan.width == width and plan.variant == variant
+    x = to_device_layout(cart, direction, dtype)
+    y = plan.adjoint(x) if adjoint else plan.deriv(x)
+    got = from_device_layout(y, direction, WSHAPE)
+    ref = (oracle.deriv_adjoint if adjoint else oracle.deriv)(cart, direction, order, bc, h)
+    mx, rms = rel_errors(got, ref)
+    assert mx <= TOL[dtype], (P, mx, rms)
+
+
+def test_resident_width_choice_and_limits():
+    """The planner's width among those that let two CTAs share an SM: FP64 the smallest, FP32
+    the largest; impossible widths are refused."""
+    cube = (512, 512, 512)
+    assert tds.Plan(cube, "x", 1, "periodic", P=8).width == 8                       # FP64 512^3
+    assert tds.Plan(cube, "x", 1, "periodic", P=8, dtype=torch.float32).width == 32
+    assert tds.Plan((1024,) * 3, "z", 1, "periodic", P=8, dtype=torch.float32).width == 16
+    assert tds.Plan((1024,) * 3, "z", 1, "periodic", P=8).width == 8
+    assert tds.Plan((16, 16, 64), "x", 1, "periodic", P=2).width == 32              # 2 warps rule
+    for bad in (4, 24, 64):
+        with pytest.raises(tds.TdsError):
+            tds.Plan((16, 16, 64), "x", 1, "periodic", P=8, width=bad)
+    with pytest.raises(tds.TdsError):   # 2 x 8 lines: fewer than two warps per CTA
+        tds.Plan((16, 16, 64), "x", 1, "periodic", P=2, width=8)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("bc", ["periodic", "closed"])
 @pytest.mark.parametrize("order", [1, 2])
