@@ -151,13 +151,28 @@ TDS_API tds_status tds_deriv_adjoint(const tds_plan *plan, const void *g, void *
                              size_t ws_bytes, void *stream);
 
 /*
- * tds_deriv_host -- tds_deriv on HOST buffers: copies host_in to d_in, runs tds_deriv into
- * d_out and copies d_out back to host_out, all on stream (the caller synchronises).  Pinned
- * host memory makes the copies asynchronous.  d_in, d_out, ws are caller-owned device
- * buffers as in tds_deriv.
+ * tds_deriv_host -- tds_deriv with the input and the result in HOST memory (not in the paper:
+ * the end-to-end form of the call).
+ *   host_in  : N*n elements in the plan's direction layout, copied to d_in; NULL when the
+ *              input is already in d_in (no host-to-device copy).
+ *   host_out : N*n elements receiving the result (copied from d_out).
+ *   d_in, d_out, ws, ws_bytes : caller-owned device buffers, the same rules as tds_deriv.
+ * The lines are cut into up to 8 slabs of whole groups; each slab is copied in, computed and
+ * copied out as soon as it can, so the copies of one slab overlap the compute of the next
+ * (two copy streams owned by the plan, created by tds_plan_create).  The call is ordered on
+ * `stream`: it starts after the work already queued there, and work queued on `stream` after
+ * it (including a synchronisation) sees host_out complete.  Pinned host memory makes the
+ * copies asynchronous.  Host calls with one plan must not run concurrently (they share the
+ * plan's copy streams and events).  Errors: those of tds_deriv (checked before any copy),
+ * TDS_ERR_ARG for a NULL host_out, d_in or d_out, TDS_ERR_CUDA when a copy fails to queue.
  */
 TDS_API tds_status tds_deriv_host(const tds_plan *plan, const void *host_in, void *host_out,
                           void *d_in, void *d_out, void *ws, size_t ws_bytes, void *stream);
+
+/* tds_deriv_adjoint_host -- tds_deriv_adjoint with host buffers: host_g (or NULL when the
+ * input is already in d_in) and host_out; the same rules and pipeline as tds_deriv_host. */
+TDS_API tds_status tds_deriv_adjoint_host(const tds_plan *plan, const void *host_g, void *host_out,
+                                  void *d_in, void *d_out, void *ws, size_t ws_bytes, void *stream);
 
 /*
  * tds_reorder -- permute a field between the Cartesian layout and the x, y, z direction

@@ -118,9 +118,10 @@ class Plan:
         """out = B^T A^{-T} g, the transpose of ``deriv``."""
         return self._run(_lib.lib().tds_deriv_adjoint, g, out, ws, stream, "tds_deriv_adjoint")
 
-    def deriv_host(self, host_in, host_out, d_in, d_out, ws=None, stream=None):
-        """Host buffers in and out through ``tds_deriv_host`` (copies inside the call)."""
+    def _run_host(self, fn, host_in, host_out, d_in, d_out, ws, stream, what):
         for t, nm in ((host_in, "host_in"), (host_out, "host_out")):
+            if t is None and nm == "host_in":
+                continue
             if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != self.numel:
                 raise ValueError("%s must be a contiguous host tensor of %d %s" % (nm, self.numel, self.dtype))
         _check_tensor(d_in, self.dtype, self.numel, "d_in")
@@ -129,12 +130,23 @@ class Plan:
             ws = self.workspace()
         wp = ctypes.c_void_p(ws.data_ptr()) if ws is not None else None
         wb = ws.numel() if ws is not None else 0
+        hin = ctypes.c_void_p(host_in.data_ptr()) if host_in is not None else None
         with torch.cuda.device(self.device):
-            _lib.check(_lib.lib().tds_deriv_host(
-                self._handle, ctypes.c_void_p(host_in.data_ptr()), ctypes.c_void_p(host_out.data_ptr()),
-                ctypes.c_void_p(d_in.data_ptr()), ctypes.c_void_p(d_out.data_ptr()), wp, wb,
-                _stream_ptr(stream, self.device)), "tds_deriv_host")
+            _lib.check(fn(self._handle, hin, ctypes.c_void_p(host_out.data_ptr()),
+                          ctypes.c_void_p(d_in.data_ptr()), ctypes.c_void_p(d_out.data_ptr()), wp, wb,
+                          _stream_ptr(stream, self.device)), what)
         return host_out
+
+    def deriv_host(self, host_in, host_out, d_in, d_out, ws=None, stream=None):
+        """``tds_deriv_host``: host_in (a host tensor, or None when d_in already holds the input)
+        through d_in / d_out to host_out, copies pipelined with the compute inside the call."""
+        return self._run_host(_lib.lib().tds_deriv_host, host_in, host_out, d_in, d_out, ws, stream,
+                              "tds_deriv_host")
+
+    def adjoint_host(self, host_g, host_out, d_in, d_out, ws=None, stream=None):
+        """``tds_deriv_adjoint_host``: the adjoint with host buffers (see ``deriv_host``)."""
+        return self._run_host(_lib.lib().tds_deriv_adjoint_host, host_g, host_out, d_in, d_out, ws,
+                              stream, "tds_deriv_adjoint_host")
 
     def deriv_noalloc(self, x, out, stream=None):
         """``tds_deriv_noalloc``: like ``deriv`` but with the library's built-in scratch instead

@@ -29,6 +29,7 @@ SIGNATURES = [
     ("tds_deriv", _i, [_vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_deriv_adjoint", _i, [_vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_deriv_host", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    ("tds_deriv_adjoint_host", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_reorder", _i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
     ("tds_plan_destroy", None, [_vp]),
     ("tds_status_string", ctypes.c_char_p, [_i]),

@@ -72,8 +72,8 @@ void configure_pipe(tds_plan *p) {
     p->pipe_grid = p->nsm * (ctas > 0 ? ctas : 1);
 }
 
-tds_status run(const tds_plan *p, int which, const void *in, void *out, void *ws, size_t ws_bytes,
-               void *stream) {
+// Arguments of one call (device buffers): TDS_OK or the error to return before any launch.
+tds_status check_call(const tds_plan *p, const void *in, const void *out, const void *ws, size_t ws_bytes) {
     if (!p || !in || !out) return TDS_ERR_ARG;
     if (!aligned(in, 16) || !aligned(out, 16)) return TDS_ERR_ARG;
     const size_t bytes = (size_t)p->n * p->nlines * elem_size(p->dtype);
@@ -83,11 +83,78 @@ tds_status run(const tds_plan *p, int which, const void *in, void *out, void *ws
         if (!ws || ws_bytes < need || !aligned(ws, 256)) return TDS_ERR_WORKSPACE;
         if (overlaps(ws, need, in, bytes) || overlaps(ws, need, out, bytes)) return TDS_ERR_ALIAS;
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return TDS_OK;
+}
+
+// The plan's variant on device buffers (arguments already checked).
+tds_status launch(const tds_plan *p, int which, const void *in, void *out, void *ws, cudaStream_t st) {
     if (p->variant == TDS_VARIANT_RESIDENT) return launch_resident(p, which, in, out, st);
     if (p->variant == TDS_VARIANT_PIPELINED) return launch_pipelined(p, which, in, out, st);
     if (p->variant == TDS_VARIANT_SEGMENTED && which == 0) return launch_segmented(p, in, out, ws, st);
     return launch_streaming(p, which, in, out, ws, st);
+}
+
+tds_status run(const tds_plan *p, int which, const void *in, void *out, void *ws, size_t ws_bytes,
+               void *stream) {
+    const tds_status s = check_call(p, in, out, ws, ws_bytes);
+    if (s != TDS_OK) return s;
+    return launch(p, which, in, out, ws, static_cast<cudaStream_t>(stream));
+}
+
+// The plan restricted to groups [g0, g1) of its lines: the same operator arrays, fewer lines.
+// Groups are independent and contiguous (group g occupies elements [g n 32, (g+1) n 32)), so
+// the slab runs on the buffers offset by g0 n 32 elements.
+tds_plan slab_of(const tds_plan *p, int g0, int g1) {
+    tds_plan q = *p;
+    q.nlines = (g1 - g0) * kSZ;
+    for (DevOp *o : {&q.op[0], &q.op[1], &q.seg}) {
+        o->nlines = q.nlines;
+        o->ngroups = g1 - g0;
+    }
+    return q;
+}
+
+// Host buffers: the lines are cut into up to kHostSlabs slabs of whole groups; slab s is copied
+// in on the plan's input copy stream, computed on `stream` once it has landed, and copied out on
+// the output copy stream once computed, so the copies of one slab overlap the compute of the
+// next.  Ordered on `stream`: the call starts after the work already queued there, and work
+// queued after it starts once host_out is complete.
+tds_status run_host(const tds_plan *p, int which, const void *host_in, void *host_out, void *d_in,
+                    void *d_out, void *ws, size_t ws_bytes, void *stream) {
+    if (!p || !host_out || !d_in || !d_out) return TDS_ERR_ARG;
+    tds_status s = check_call(p, d_in, d_out, ws, ws_bytes);
+    if (s != TDS_OK) return s;
+    const size_t gbytes = (size_t)p->n * kSZ * elem_size(p->dtype);
+    const int G = p->nlines / kSZ;
+    const int S = G < kHostSlabs ? G : kHostSlabs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const cudaEvent_t *ev = p->ev;
+    auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+    if (!ok(cudaEventRecord(ev[0], st)) || !ok(cudaStreamWaitEvent(p->copy_in, ev[0], 0)) ||
+        !ok(cudaStreamWaitEvent(p->copy_out, ev[0], 0)))
+        return TDS_ERR_CUDA;
+    for (int k = 0; k < S; ++k) {
+        const int g0 = (int)((long long)G * k / S), g1 = (int)((long long)G * (k + 1) / S);
+        const size_t off = (size_t)g0 * gbytes, len = (size_t)(g1 - g0) * gbytes;
+        char *di = static_cast<char *>(d_in) + off;
+        char *dout = static_cast<char *>(d_out) + off;
+        if (host_in) {
+            if (!ok(cudaMemcpyAsync(di, static_cast<const char *>(host_in) + off, len, cudaMemcpyHostToDevice,
+                                    p->copy_in)) ||
+                !ok(cudaEventRecord(ev[2 + k], p->copy_in)) || !ok(cudaStreamWaitEvent(st, ev[2 + k], 0)))
+                return TDS_ERR_CUDA;
+        }
+        const tds_plan q = slab_of(p, g0, g1);
+        s = launch(&q, which, di, dout, ws, st);
+        if (s != TDS_OK) return s;
+        if (!ok(cudaEventRecord(ev[2 + kHostSlabs + k], st)) ||
+            !ok(cudaStreamWaitEvent(p->copy_out, ev[2 + kHostSlabs + k], 0)) ||
+            !ok(cudaMemcpyAsync(static_cast<char *>(host_out) + off, dout, len, cudaMemcpyDeviceToHost,
+                                p->copy_out)))
+            return TDS_ERR_CUDA;
+    }
+    if (!ok(cudaEventRecord(ev[1], p->copy_out)) || !ok(cudaStreamWaitEvent(st, ev[1], 0))) return TDS_ERR_CUDA;
+    return TDS_OK;
 }
 
 } // namespace
@@ -171,6 +238,16 @@ tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_dir dir, 
         const int v = std::atoi(e);
         if (v == 1 || v == 2 || (v == 4 && dtype == TDS_F32)) p->lanes = v;
     }
+    if (cudaStreamCreateWithFlags(&p->copy_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->copy_out, cudaStreamNonBlocking) != cudaSuccess) {
+        tds_plan_destroy(p);
+        return TDS_ERR_CUDA;
+    }
+    for (cudaEvent_t &e : p->ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            tds_plan_destroy(p);
+            return TDS_ERR_CUDA;
+        }
     tds_plan_set_variant(p, TDS_VARIANT_AUTO);
     *out = p;
     return TDS_OK;
@@ -237,16 +314,12 @@ tds_status tds_deriv_adjoint(const tds_plan *p, const void *g, void *out, void *
 
 tds_status tds_deriv_host(const tds_plan *p, const void *host_in, void *host_out, void *d_in,
                           void *d_out, void *ws, size_t ws_bytes, void *stream) {
-    if (!p || !host_in || !host_out || !d_in || !d_out) return TDS_ERR_ARG;
-    const size_t bytes = (size_t)p->n * p->nlines * elem_size(p->dtype);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(d_in, host_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return TDS_ERR_CUDA;
-    tds_status s = run(p, 0, d_in, d_out, ws, ws_bytes, stream);
-    if (s != TDS_OK) return s;
-    if (cudaMemcpyAsync(host_out, d_out, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        return TDS_ERR_CUDA;
-    return TDS_OK;
+    return run_host(p, 0, host_in, host_out, d_in, d_out, ws, ws_bytes, stream);
+}
+
+tds_status tds_deriv_adjoint_host(const tds_plan *p, const void *host_g, void *host_out, void *d_in,
+                                  void *d_out, void *ws, size_t ws_bytes, void *stream) {
+    return run_host(p, 1, host_g, host_out, d_in, d_out, ws, ws_bytes, stream);
 }
 
 tds_status tds_reorder(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
@@ -266,6 +339,10 @@ tds_status tds_reorder(const void *in, void *out, int nx, int ny, int nz, tds_la
 
 void tds_plan_destroy(tds_plan *p) {
     if (!p) return;
+    for (cudaEvent_t e : p->ev)
+        if (e) cudaEventDestroy(e);
+    if (p->copy_in) cudaStreamDestroy(p->copy_in);
+    if (p->copy_out) cudaStreamDestroy(p->copy_out);
     if (p->dmem) cudaFree(p->dmem);
     std::free(p->hmem);
     delete p;

@@ -14,6 +14,7 @@ constexpr int kSZ = 32;           // lines per group: one warp lane per line (Se
 constexpr int kTaps = 7;          // stencil offsets -3..3 (closure rows reach 3 points in)
 constexpr int kEdgeRows = 4;      // closed lines: rows 0..3 and n-4..n-1 carry their own taps
 constexpr int kMaxResidentP = 16; // resident kernel: one warp per chunk, at most 16 warps
+constexpr int kHostSlabs = 8;     // host entry points: copies and compute pipelined over 8 slabs
 
 // Number of per-row coefficient arrays of one operator (Algorithm 4 output, per chunk class):
 //   f  : forward factor, 1/b_j for j <= 1, 1/(b_j - a_j s^c_{j-1}) for j >= 2
@@ -97,6 +98,10 @@ struct tds_plan {
     tds::DevOp op[2];      // [0] = A^{-1} B, [1] = B^T A^{-T}
     tds::DevOp seg;        // A^{-1} B on the segment partition of the SEGMENTED variant (P = 0: none)
     double *red_sub_host[2], *red_sup_host[2];
+    // host entry points: two copy streams (in, out) and their events (start, done, per slab:
+    // input landed, slab computed), created with the plan
+    cudaStream_t copy_in, copy_out;
+    cudaEvent_t ev[2 + 2 * tds::kHostSlabs];
     void *dmem;            // one device allocation holding every array of both operators
     void *hmem;            // host copies (reduced coefficients)
 };

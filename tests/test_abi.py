@@ -72,6 +72,8 @@ def test_null_pointer_errors_need_no_gpu(L):
     assert L.tds_plan_create(None, 64, 64, 64, 0, 1, 0, 1, 0.1, 0, 32, 0) == _lib.ERR_ARG
     assert L.tds_deriv(None, None, None, None, 0, None) == _lib.ERR_ARG
     assert L.tds_deriv_adjoint(None, None, None, None, 0, None) == _lib.ERR_ARG
+    assert L.tds_deriv_host(None, None, None, None, None, None, 0, None) == _lib.ERR_ARG
+    assert L.tds_deriv_adjoint_host(None, None, None, None, None, None, 0, None) == _lib.ERR_ARG
     sz = ctypes.c_size_t()
     assert L.tds_workspace_bytes(None, ctypes.byref(sz)) == _lib.ERR_ARG
     assert L.tds_reorder(None, None, 32, 32, 1, 0, 1, 0, 32, None) == _lib.ERR_ARG

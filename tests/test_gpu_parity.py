@@ -110,6 +110,43 @@ def test_resident_width_choice_and_limits():
         tds.Plan((16, 16, 64), "x", 1, "periodic", P=2, width=8)
 
 
+HOST_CASES = [   # (shape, direction, P, variant, width): groups = lines / 32
+    ((12, 40, 32), "x", 8, "resident", None),     # 15 groups: ragged slabs
+    ((16, 48, 64), "x", 8, "resident", 8),        # 24 groups, 4 CTAs per group
+    ((12, 40, 32), "z", 3, "streaming", None),    # 40 groups
+    ((12, 40, 32), "y", 5, "pipelined", None),    # 12 groups
+    ((1, 32, 2048), "x", 4, "segmented", None),   # 1 group: fewer groups than slabs
+    ((2, 32, 256), "x", 2, "resident", None),     # 2 groups
+]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("case", range(len(HOST_CASES)))
+def test_host_entry_points_match_device_calls(dtype, case):
+    """tds_deriv_host / tds_deriv_adjoint_host (slab-pipelined copies) give bitwise the result
+    of tds_deriv / tds_deriv_adjoint on device buffers, with and without the input copy."""
+    shape, direction, P, variant, width = HOST_CASES[case]
+    bc = "closed" if case % 2 else "periodic"
+    plan = tds.Plan(shape, direction, 1, bc, P=P, dtype=TORCH[dtype], variant=variant, width=width)
+    numel = plan.numel
+    g = torch.Generator(device="cuda").manual_seed(case)
+    x = torch.rand(numel, generator=g, device="cuda", dtype=TORCH[dtype]) - 0.5
+    ref_f = plan.deriv(x)
+    ref_a = plan.adjoint(x)
+    host_in = x.cpu().pin_memory()
+    outs = [torch.full((numel,), float("nan"), dtype=TORCH[dtype]).pin_memory() for _ in range(3)]
+    d_in = torch.zeros_like(x)
+    d_out = torch.empty_like(x)
+    plan.deriv_host(host_in, outs[0], d_in, d_out)          # copies the input in
+    plan.deriv_host(None, outs[1], d_in, d_out)             # input already in d_in
+    plan.adjoint_host(None, outs[2], d_in, d_out)
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(outs[0], ref_f.cpu())
+    assert torch.equal(outs[1], ref_f.cpu())
+    assert torch.equal(outs[2], ref_a.cpu())
+    assert torch.equal(d_in, x)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("bc", ["periodic", "closed"])
 @pytest.mark.parametrize("order", [1, 2])
