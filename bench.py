@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--P", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time every workload configuration one operator at a time (one JSON line per "
+                         "case) instead of the benchmark step")
     return ap.parse_args()
 
 
@@ -358,6 +361,76 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches}
 
 
+# ------------------------------------------------------------------ per-configuration sweep
+
+SWEEP_CASES = [
+    # (label, shape (nz, ny, nx), directions, orders, bcs, Ps, dtypes, adjoint)
+    ("64^3 D1 x periodic P=1", (64, 64, 64), "x", (1,), ("periodic",), (1,), ("f64",), False),
+    ("256^3 D1/D2 x,y,z periodic/closed P=1,4", (256, 256, 256), "xyz", (1, 2), ("periodic", "closed"),
+     (1, 4), ("f64",), False),
+    ("512^3 D1/D2 x,y,z periodic P=8 FP64/FP32", (512, 512, 512), "xyz", (1, 2), ("periodic",), (8,),
+     ("f64", "f32"), False),
+    ("256^3 D1^T z closed P=4 FP64/FP32", (256, 256, 256), "z", (1,), ("closed",), (4,), ("f64", "f32"), True),
+    ("1024^3 D1 x,y,z periodic P=8,2", (1024, 1024, 1024), "xyz", (1,), ("periodic",), (8, 2), ("f64",), False),
+    ("256 x 262144 D1 x periodic P=64", (1, 256, 262144), "x", (1,), ("periodic",), (64,), ("f64",), False),
+]
+
+
+def run_sweep(args):
+    """Every workload configuration, one operator at a time: CUDA events around each launch,
+    a 2x-L2 buffer written between launches, median of the timed launches."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_13532_gb300 as tds
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(2 * 135 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    peaks, kind = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    TD = {"f64": torch.float64, "f32": torch.float32}
+    reps = max(args.steps, 5)
+    for label, shape, dirs, orders, bcs, Ps, dts, adj in SWEEP_CASES:
+        npts = shape[0] * shape[1] * shape[2]
+        for dname in dts:
+            dt = TD[dname]
+            x = (torch.rand(npts, dtype=dt, device=dev) - 0.5) * 2
+            y = torch.empty_like(x)
+            for direc in dirs:
+                for order in orders:
+                    for bc in bcs:
+                        for P in Ps:
+                            plan = tds.Plan(shape, direc, order, bc, P=P, dtype=dt)
+                            ws = plan.workspace()
+                            fn = (lambda: plan.adjoint(x, y, ws)) if adj else (lambda: plan.deriv(x, y, ws))
+                            for _ in range(max(args.warmup, 3)):
+                                fn()
+                            times = []
+                            for _ in range(reps):
+                                flush.fill_(1.0)
+                                a = torch.cuda.Event(enable_timing=True)
+                                b = torch.cuda.Event(enable_timing=True)
+                                a.record()
+                                fn()
+                                b.record()
+                                b.synchronize()
+                                times.append(a.elapsed_time(b))
+                            ms = statistics.median(times)
+                            es = x.element_size()
+                            gbs = 2 * es * npts / (ms * 1e-3) / 1e9
+                            print(json.dumps({
+                                "case": label, "dtype": dname, "op": ("D%dT" if adj else "D%d") % order,
+                                "dir": direc, "bc": bc, "P": P, "variant": plan.variant, "width": plan.width,
+                                "ms": round(ms, 4), "gpoints_s": round(npts / (ms * 1e-3) / 1e9, 2),
+                                "alg_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                                "peak_source": kind}), flush=True)
+                            del plan, ws
+            del x, y
+            torch.cuda.empty_cache()
+    if tds.device_status() != 0:
+        raise RuntimeError("device status after the sweep")
+
+
 # ------------------------------------------------------------------------ CPU oracle arm
 
 def oracle_sample_step(S, lines_per_dir, rng_seed=0):
@@ -437,6 +510,9 @@ def main():
         out = run_reference(args, rank, world)
         if out is not None:
             print(json.dumps(out))
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if world > 1:
         import torch

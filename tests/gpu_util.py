@@ -46,3 +46,10 @@ def sample_lines(nlines, count, seed):
     pick = set(rng.choice(nlines, size=min(count, nlines), replace=False).tolist())
     pick.update({0, nlines - 1, min(31, nlines - 1), nlines // 2})
     return sorted(pick)
+
+
+def report(case, **values):
+    """Print one measured parity figure (a JSON line tagged PARITY; shown with ``pytest -s``)."""
+    import json
+    print("PARITY " + json.dumps(dict(case=case, **{k: (float(v) if isinstance(v, (float, np.floating)) else v)
+                                                   for k, v in values.items()})))

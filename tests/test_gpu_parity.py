@@ -13,7 +13,7 @@ import torch
 
 import oracle
 from paper_2411_13532_gb300 import inputs
-from tests.gpu_util import (TOL, TORCH, from_device_layout, gather_lines, rel_errors,
+from tests.gpu_util import (TOL, TORCH, from_device_layout, gather_lines, rel_errors, report,
                             sample_lines, to_device_layout)
 
 pytestmark = pytest.mark.gpu
@@ -319,9 +319,10 @@ def test_reorder_bitwise(dtype):
 # --------------------------------------------------------------------- full-size workloads
 
 def sampled_check(field_cart_dev, shape, direction, order, bc, P, dtype, adjoint=False,
-                  nsample=48, seed=0, fp64_input=None):
+                  nsample=48, seed=0, vs_fp64=False):
     """Reorder the device field to the direction layout, run the plan, compare sampled lines
-    with the oracle.  Returns (max-rel, rms-rel) against the oracle on the same input."""
+    with the oracle.  Returns (max-rel, rms-rel) against the oracle on the same input; with
+    vs_fp64 also (max-rel, rms-rel) against the oracle on the original FP64 field."""
     t = field_cart_dev.to(TORCH[dtype])
     x = tds.reorder(t, shape, "cart", direction)
     del t
@@ -334,7 +335,13 @@ def sampled_check(field_cart_dev, shape, direction, order, bc, P, dtype, adjoint
     fout = gather_lines(y, direction, shape, lines).double().cpu().numpy()
     del x, y
     ref = (oracle.deriv_adjoint_lines if adjoint else oracle.deriv_lines)(fin, order, bc, h)
-    return rel_errors(fout, ref)
+    if not vs_fp64:
+        return rel_errors(fout, ref)
+    x64 = tds.reorder(field_cart_dev.to(torch.float64), shape, "cart", direction)
+    f64 = gather_lines(x64, direction, shape, lines).double().cpu().numpy()
+    del x64
+    ref64 = (oracle.deriv_adjoint_lines if adjoint else oracle.deriv_lines)(f64, order, bc, h)
+    return rel_errors(fout, ref) + rel_errors(fout, ref64)
 
 
 def test_config_64cubed_fourier_x_periodic_p1():
@@ -345,6 +352,7 @@ def test_config_64cubed_fourier_x_periodic_p1():
     y = tds.Plan(shape, "x", 1, "periodic", P=1).deriv(x)
     got = from_device_layout(y, "x", shape)
     mx, rms = rel_errors(got, oracle.deriv(cart, "x", 1, "periodic"))
+    report("64^3 D1 x periodic P=1 f64", max_rel=mx, rms_rel=rms)
     assert mx <= 1e-12, (mx, rms)
 
 
@@ -356,6 +364,7 @@ def test_config_256cubed_orders_dirs_bcs_p1_p4(direction, bc):
     for order in (1, 2):
         for P in (1, 4):
             mx, rms = sampled_check(f, shape, direction, order, bc, P, "f64", seed=order * 10 + P)
+            report("256^3 D%d %s %s P=%d f64" % (order, direction, bc, P), max_rel=mx, rms_rel=rms)
             assert mx <= 1e-12, (order, P, mx, rms)
 
 
@@ -366,8 +375,12 @@ def test_config_512cubed_fp32_vs_fp64(direction):
                                 device="cuda")
     for order in (1, 2):
         mx, rms = sampled_check(f, shape, direction, order, "periodic", 8, "f64", nsample=24)
+        report("512^3 D%d %s periodic P=8 f64" % (order, direction), max_rel=mx, rms_rel=rms)
         assert mx <= 1e-12, ("f64", order, mx, rms)
-        mx, rms = sampled_check(f, shape, direction, order, "periodic", 8, "f32", nsample=24)
+        mx, rms, mx64, rms64 = sampled_check(f, shape, direction, order, "periodic", 8, "f32", nsample=24,
+                                             vs_fp64=True)
+        report("512^3 D%d %s periodic P=8 f32" % (order, direction), max_rel=mx, rms_rel=rms,
+               max_rel_vs_fp64_input=mx64, rms_rel_vs_fp64_input=rms64)
         assert mx <= 1e-5, ("f32", order, mx, rms)
 
 
@@ -375,7 +388,10 @@ def test_config_512cubed_fp32_vs_fp64(direction):
 def test_config_256cubed_adjoint_z_closed_p4(dtype):
     shape = (256, 256, 256)
     g = inputs.normal_field(shape, seed=3, device="cuda")
-    mx, rms = sampled_check(g, shape, "z", 1, "closed", 4, dtype, adjoint=True)
+    res = sampled_check(g, shape, "z", 1, "closed", 4, dtype, adjoint=True, vs_fp64=(dtype == "f32"))
+    mx, rms = res[0], res[1]
+    extra = dict(max_rel_vs_fp64_input=res[2], rms_rel_vs_fp64_input=res[3]) if dtype == "f32" else {}
+    report("256^3 D1^T z closed P=4 %s" % dtype, max_rel=mx, rms_rel=rms, **extra)
     assert mx <= TOL[dtype], (mx, rms)
 
 
@@ -383,6 +399,7 @@ def test_config_1d_batch_long_lines_p64():
     shape = (1, 256, 262144)
     f = inputs.uniform_field(shape, seed=5, device="cuda")
     mx, rms = sampled_check(f, shape, "x", 1, "periodic", 64, "f64", nsample=6)
+    report("256 x 262144 D1 x periodic P=64 f64", max_rel=mx, rms_rel=rms)
     assert mx <= 1e-12, (mx, rms)
 
 
@@ -393,6 +410,7 @@ def test_config_1024cubed_three_directions(P):
     f = inputs.uniform_field(shape, seed=4, device="cuda")
     for direction in "xyz":
         mx, rms = sampled_check(f, shape, direction, 1, "periodic", P, "f64", nsample=16)
+        report("1024^3 D1 %s periodic P=%d f64" % (direction, P), max_rel=mx, rms_rel=rms)
         assert mx <= 1e-12, (direction, mx, rms)
     del f
     torch.cuda.empty_cache()
