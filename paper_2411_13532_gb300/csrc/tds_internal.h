@@ -63,6 +63,13 @@ struct DevOp {
     // per chunk class: rows j >= jpi carry |pi_j| below the cut-off and rows j >= jsa carry
     // |s^a_j| below it (2^-60 for FP64 sweeps, 2^-30 for FP32): those terms are not issued
     int jpi64[3], jsa64[3], jpi32[3], jsa32[3];
+    // per chunk class: rows [kfl, kfh) carry the same folded forward record (bitwise, in the
+    // sweep's precision) kf = {c0, c1, c2, g}, and rows [kbl, kbh) the same back-substitution
+    // coupling kb = s^c_j: the forward factor converges geometrically away from the chunk's
+    // first rows, so the sweeps take these rows' coefficients from registers
+    int kfl64[3], kfh64[3], kbl64[3], kbh64[3], kfl32[3], kfh32[3], kbl32[3], kbh32[3];
+    double kf64[3][4], kb64[3];
+    float kf32[3][4], kb32[3];
     const double *n1;     // [ncls] row-0 normaliser 1/(1 - s^c_1 s^a_2) (Algorithm 4, last lines)
     const double *red;    // [kNumRedArrays][2P]
     int red_cyclic;

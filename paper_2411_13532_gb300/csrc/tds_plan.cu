@@ -208,6 +208,39 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
         op.jsa64[cl] = cutoff(1, std::ldexp(1.0, -60));
         op.jpi32[cl] = cutoff(0, std::ldexp(1.0, -30));
         op.jsa32[cl] = cutoff(1, std::ldexp(1.0, -30));
+        // the run of rows around row m-3 (interior in every class) whose records equal that
+        // row's, bitwise in each precision
+        const int ref = m - 3;
+        auto run = [&](auto same, int &lo, int &hi) {
+            lo = ref;
+            while (lo > 0 && same(lo - 1)) --lo;
+            hi = ref + 1;
+            while (hi < m && same(hi)) ++hi;
+        };
+        const double *rf = &ifw[((size_t)cl * m + ref) * 4];
+        auto fsame64 = [&](int j) {
+            const double *x = &ifw[((size_t)cl * m + j) * 4];
+            return x[0] == rf[0] && x[1] == rf[1] && x[2] == rf[2] && x[3] == rf[3];
+        };
+        auto fsame32 = [&](int j) {
+            const double *x = &ifw[((size_t)cl * m + j) * 4];
+            for (int q = 0; q < 4; ++q)
+                if ((float)x[q] != (float)rf[q]) return false;
+            return true;
+        };
+        const double rb = bwd[((size_t)cl * m + ref) * 2 + 1];
+        auto bsame64 = [&](int j) { return bwd[((size_t)cl * m + j) * 2 + 1] == rb; };
+        auto bsame32 = [&](int j) { return (float)bwd[((size_t)cl * m + j) * 2 + 1] == (float)rb; };
+        run(fsame64, op.kfl64[cl], op.kfh64[cl]);
+        run(fsame32, op.kfl32[cl], op.kfh32[cl]);
+        run(bsame64, op.kbl64[cl], op.kbh64[cl]);
+        run(bsame32, op.kbl32[cl], op.kbh32[cl]);
+        for (int q = 0; q < 4; ++q) {
+            op.kf64[cl][q] = rf[q];
+            op.kf32[cl][q] = (float)rf[q];
+        }
+        op.kb64[cl] = rb;
+        op.kb32[cl] = (float)rb;
     }
 
     // reduced chunk-end system, unknowns F_0, L_0, F_1, L_1, ... (2P)

@@ -100,6 +100,27 @@ struct TrNative {
     static __device__ __forceinline__ int jsa(const DevOp &op, int cls) {
         return sizeof(T) == 4 ? op.jsa32[cls] : op.jsa64[cls];
     }
+    // the run of rows [lo, hi) with the constant forward record, and that record
+    static __device__ __forceinline__ void kf_run(const DevOp &op, int cls, int &lo, int &hi) {
+        lo = sizeof(T) == 4 ? op.kfl32[cls] : op.kfl64[cls];
+        hi = sizeof(T) == 4 ? op.kfh32[cls] : op.kfh64[cls];
+    }
+    static __device__ __forceinline__ void kf(const DevOp &op, int cls, A &c0, A &c1, A &c2, A &g) {
+        if constexpr (sizeof(T) == 4) {
+            c0 = op.kf32[cls][0]; c1 = op.kf32[cls][1]; c2 = op.kf32[cls][2]; g = op.kf32[cls][3];
+        } else {
+            c0 = op.kf64[cls][0]; c1 = op.kf64[cls][1]; c2 = op.kf64[cls][2]; g = op.kf64[cls][3];
+        }
+    }
+    // the run of rows [lo, hi) with the constant back-substitution coupling s^c, and that value
+    static __device__ __forceinline__ void kb_run(const DevOp &op, int cls, int &lo, int &hi) {
+        lo = sizeof(T) == 4 ? op.kbl32[cls] : op.kbl64[cls];
+        hi = sizeof(T) == 4 ? op.kbh32[cls] : op.kbh64[cls];
+    }
+    static __device__ __forceinline__ A kb(const DevOp &op, int cls) {
+        if constexpr (sizeof(T) == 4) return op.kb32[cls];
+        else return op.kb64[cls];
+    }
 };
 
 using TrF32 = TrNative<float>;
@@ -215,12 +236,12 @@ __device__ __forceinline__ void fwd_row(const DevOp &op, int cls, int j, typenam
 // d_j = c1 (v[j+1] -+ v[j-1]) + c2 (v[j+2] -+ v[j-2]) (+ c0 v[j]) - g d_{j-1}, one FMA on the
 // recurrence; ACC: S += pi_j d_j (rows past the plan's cut-off skip it).
 template <typename Tr, int V, bool SYM, bool ACC>
-__device__ __forceinline__ void fwd_irow(const DevOp &op, int cls, int j, typename Tr::S *row,
-                                         const Pack<typename Tr::A, V> (&w)[5],
-                                         Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S) {
+__device__ __forceinline__ void fwd_irow_c(const DevOp &op, int cls, int j, typename Tr::S *row,
+                                           const Pack<typename Tr::A, V> (&w)[5],
+                                           Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S,
+                                           typename Tr::A c0, typename Tr::A c1, typename Tr::A c2,
+                                           typename Tr::A g) {
     using A = typename Tr::A;
-    A c0, c1, c2, g;
-    Tr::ifw(op, cls, j, c0, c1, c2, g);
     A p = A(0);
     if (ACC) p = Tr::pi(op, cls, j);
 #pragma unroll
@@ -233,18 +254,48 @@ __device__ __forceinline__ void fwd_irow(const DevOp &op, int cls, int j, typena
     Tr::template st_mid<V>(row + (size_t)j * Tr::W, dprev);
 }
 
-// Interior forward rows [jb, je) reading v[j+2] from the tile (inside the chunk).
+// The same with the row's own record from the plan.
 template <typename Tr, int V, bool SYM, bool ACC>
+__device__ __forceinline__ void fwd_irow(const DevOp &op, int cls, int j, typename Tr::S *row,
+                                         const Pack<typename Tr::A, V> (&w)[5],
+                                         Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S) {
+    typename Tr::A c0, c1, c2, g;
+    Tr::ifw(op, cls, j, c0, c1, c2, g);
+    fwd_irow_c<Tr, V, SYM, ACC>(op, cls, j, row, w, dprev, S, c0, c1, c2, g);
+}
+
+// Interior forward rows [jb, je) reading v[j+2] from the tile (inside the chunk); CONST: every
+// row has the class's constant record (k0..kg), else each row loads its own.
+template <typename Tr, int V, bool SYM, bool ACC, bool CONST>
 __device__ __forceinline__ void fwd_irows(const DevOp &op, int cls, typename Tr::S *row, int jb, int je,
                                           Pack<typename Tr::A, V> (&w)[5], Pack<typename Tr::A, V> &dprev,
-                                          Pack<typename Tr::A, V> &S, int &unsafe) {
+                                          Pack<typename Tr::A, V> &S, int &unsafe, typename Tr::A k0 = 0,
+                                          typename Tr::A k1 = 0, typename Tr::A k2 = 0, typename Tr::A kg = 0) {
 #pragma unroll 4
     for (int j = jb; j < je; ++j) {
         w[4] = Tr::template ld_in<V>(op, row + (size_t)(j + 2) * Tr::W, unsafe);
-        fwd_irow<Tr, V, SYM, ACC>(op, cls, j, row, w, dprev, S);
+        if (CONST) fwd_irow_c<Tr, V, SYM, ACC>(op, cls, j, row, w, dprev, S, k0, k1, k2, kg);
+        else fwd_irow<Tr, V, SYM, ACC>(op, cls, j, row, w, dprev, S);
 #pragma unroll
         for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
     }
+}
+
+// Forward rows [jb, je): the part inside the class's constant-record run [lo, hi) with the
+// record in registers, the rest with per-row records.
+template <typename Tr, int V, bool SYM, bool ACC>
+__device__ __forceinline__ void fwd_span(const DevOp &op, int cls, typename Tr::S *row, int jb, int je,
+                                         Pack<typename Tr::A, V> (&w)[5], Pack<typename Tr::A, V> &dprev,
+                                         Pack<typename Tr::A, V> &S, int &unsafe) {
+    int lo, hi;
+    Tr::kf_run(op, cls, lo, hi);
+    const int a = (lo < jb) ? jb : (lo > je ? je : lo);
+    const int b = (hi < a) ? a : (hi > je ? je : hi);
+    typename Tr::A k0, k1, k2, kg;
+    Tr::kf(op, cls, k0, k1, k2, kg);
+    fwd_irows<Tr, V, SYM, ACC, false>(op, cls, row, jb, a, w, dprev, S, unsafe);
+    fwd_irows<Tr, V, SYM, ACC, true>(op, cls, row, a, b, w, dprev, S, unsafe, k0, k1, k2, kg);
+    fwd_irows<Tr, V, SYM, ACC, false>(op, cls, row, b, je, w, dprev, S, unsafe);
 }
 
 // Interior rows [jb, je) of a stencil sweep over this chunk, in place: w[0..3] holds
@@ -265,8 +316,8 @@ __device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typenam
         // rows before the pi cut-off accumulate S, the rest do not
         const int jp = Tr::jpi(op, cls);
         const int j1 = (jp < jb) ? jb : (jp > jm ? jm : jp);
-        fwd_irows<Tr, V, SYM, true>(op, cls, row, jb, j1, w, dprev, S, unsafe);
-        fwd_irows<Tr, V, SYM, false>(op, cls, row, j1, jm, w, dprev, S, unsafe);
+        fwd_span<Tr, V, SYM, true>(op, cls, row, jb, j1, w, dprev, S, unsafe);
+        fwd_span<Tr, V, SYM, false>(op, cls, row, j1, jm, w, dprev, S, unsafe);
     } else {
 #pragma unroll 4
         for (int j = jb; j < jm; ++j) {
@@ -381,9 +432,13 @@ __device__ __forceinline__ void forward_phase(const DevOp &op, typename Tr::S *r
         stencil_sweep<Tr, V, true>(op, K, cls, row, xs, c, hb, ha, dprev, Ssum, unsafe);
     } else {
         // identity right-hand side: d_j = f_j g_j - (f_j r_j) d_{j-1}
-        auto arow = [&](int j, bool acc) {
-            A c0, c1, c2, gg;
-            Tr::ifw(op, cls, j, c0, c1, c2, gg);
+        int lo, hi;
+        Tr::kf_run(op, cls, lo, hi);
+        A k0, k1, k2, kg;
+        Tr::kf(op, cls, k0, k1, k2, kg);
+        auto arow = [&](int j, bool acc, bool cst) {
+            A c0 = k0, c1, c2, gg = kg;
+            if (!cst) Tr::ifw(op, cls, j, c0, c1, c2, gg);
             const Pack<A, V> g = Tr::template ld_in<V>(op, row + (size_t)j * Tr::W, unsafe);
             const A p = acc ? Tr::pi(op, cls, j) : A(0);
 #pragma unroll
@@ -393,11 +448,20 @@ __device__ __forceinline__ void forward_phase(const DevOp &op, typename Tr::S *r
             }
             Tr::template st_mid<V>(row + (size_t)j * Tr::W, dprev);
         };
+        // rows [a, b): per-row records outside the constant run, the register record inside it
+        auto span = [&](int a, int b, bool acc) {
+            const int x = (lo < a) ? a : (lo > b ? b : lo);
+            const int y = (hi < x) ? x : (hi > b ? b : hi);
+#pragma unroll 4
+            for (int j = a; j < x; ++j) arow(j, acc, false);
+#pragma unroll 4
+            for (int j = x; j < y; ++j) arow(j, acc, true);
+#pragma unroll 4
+            for (int j = y; j < b; ++j) arow(j, acc, false);
+        };
         const int jp = Tr::jpi(op, cls) < m ? Tr::jpi(op, cls) : m;
-#pragma unroll 4
-        for (int j = 0; j < jp; ++j) arow(j, true);
-#pragma unroll 4
-        for (int j = jp; j < m; ++j) arow(j, false);
+        span(0, jp, true);
+        span(jp, m, false);
     }
 }
 
@@ -433,16 +497,33 @@ __device__ __forceinline__ void backsub_phase(const DevOp &op, typename Tr::S *r
         else Tr::template st_out<V>(op, row + (size_t)j * Tr::W, v);
     };
     put(m - 1, u);
-    // rows at or past the s^a cut-off: u_j = d_j - s^c_j u_{j+1}
+    // rows at or past the s^a cut-off: u_j = d_j - s^c_j u_{j+1}; inside the class's constant
+    // run [lo, hi) s^c comes from a register
     const int js = Tr::jsa(op, cls) > 1 ? Tr::jsa(op, cls) : 1;
-#pragma unroll 8
-    for (int j = m - 2; j >= js; --j) {
+    int lo, hi;
+    Tr::kb_run(op, cls, lo, hi);
+    const int kh = (hi < js) ? js : (hi > m - 1 ? m - 1 : hi);
+    const int kl = (lo < js) ? js : (lo > kh ? kh : lo);
+    auto step = [&](int j, A sc) {
         const Pack<A, V> d = Tr::template ld_mid<V>(row + (size_t)j * Tr::W);
-        A sa, sc;
-        Tr::bwd(op, cls, j, sa, sc);
 #pragma unroll
         for (int i = 0; i < V; ++i) u.v[i] = mad(-sc, u.v[i], d.v[i]);
         put(j, u);
+    };
+#pragma unroll 8
+    for (int j = m - 2; j >= kh; --j) {
+        A sa, sc;
+        Tr::bwd(op, cls, j, sa, sc);
+        step(j, sc);
+    }
+    const A kc = Tr::kb(op, cls);
+#pragma unroll 8
+    for (int j = kh - 1; j >= kl; --j) step(j, kc);
+#pragma unroll 8
+    for (int j = kl - 1; j >= js; --j) {
+        A sa, sc;
+        Tr::bwd(op, cls, j, sa, sc);
+        step(j, sc);
     }
 #pragma unroll 8
     for (int j = (js < m - 1 ? js : m - 1) - 1; j >= 1; --j) {
