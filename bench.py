@@ -39,20 +39,22 @@ METRIC = "Gpoints/s and % of HBM roofline per directional derivative, FP64 vs FP
 UNIT = "Gpoints/s"
 KERNEL_SRC = os.path.join(ROOT, "paper_2411_13532_gb300", "csrc", "tds_resident.cu")
 
-def fp64_ops_per_point(op, m):
+def fp64_ops_per_point(op, m, periodic=True):
     """FP64-pipe operations per interior point as the resident kernel issues them.
 
     Forward row with f folded into the coefficients: 2 adds (the stencil differences or sums)
-    + 1 multiply + 2 FMAs (first derivative) or 3 FMAs (second: the centre tap); the adjoint's
-    forward row (identity right-hand side) is 1 multiply + 1 FMA and its B^T pass 4.  Back-
+    + 1 multiply + 2 FMAs (first derivative) or 3 FMAs (second: the centre tap).  Back-
     substitution: 1 FMA.  The accumulation S += pi_j d_j and the s^a_j F term of the back-
     substitution are issued only on the rows before the plan's cut-off, where those weights,
     decaying like lambda^j (lambda = 0.382 for alpha = 1/3, 0.188 for alpha = 2/11), fall
-    below 2^-60: about 44 and 25 rows."""
+    below 2^-60: about 44 and 25 rows.  The adjoint on periodic lines is the forward form with
+    the transposed stencil (A and B circulant commute); on closed lines it is the identity
+    forward row (1 multiply + 1 FMA), the back-substitution and the B^T pass (4)."""
     lam = {"d1": 0.38196601125, "d2": 0.18826230851, "d1t": 0.38196601125}[op]
     cut = min(m, math.ceil(math.log(2.0 ** -60) / math.log(lam)))
     extra = 2.0 * cut / m
-    return {"d1": 5.0 + 1.0, "d2": 6.0 + 1.0, "d1t": 2.0 + 1.0 + 4.0}[op] + extra
+    base = {"d1": 5.0 + 1.0, "d2": 6.0 + 1.0, "d1t": (5.0 + 1.0) if periodic else (2.0 + 1.0 + 4.0)}
+    return base[op] + extra
 
 
 def parse():

@@ -137,6 +137,10 @@ bool preprocess_chunk(int m, const double *a, const double *b, const double *c,
 } // namespace
 
 // Build one operator (A^{-1}B if which == 0, B^T A^{-T} if which == 1) into host buffers.
+// On periodic lines A and B are circulant, so they commute and A is symmetric:
+// B^T A^{-T} = A^{-1} B^T, the forward form with the transposed stencil (L is then the
+// transposed line operator, whose band equals A's); op.adjoint is set only for closed lines,
+// whose adjoint runs the transposed solve followed by the transposed stencil.
 static tds_status build_operator(const tds_plan *p, int P, int m, const LineOperator &L, int which,
                                  DevOp &op, std::vector<double> &rows,
                                  std::vector<double> &n1s, std::vector<double> &red,
@@ -147,7 +151,8 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
     const bool periodic = (p->bc == TDS_BC_PERIODIC);
     std::memset(&op, 0, sizeof(op));
     op.n = n; op.m = m; op.P = P; op.nlines = p->nlines; op.ngroups = p->nlines / kSZ;
-    op.periodic = periodic; op.adjoint = which;
+    const bool fwd_form = (which == 0) || periodic;
+    op.periodic = periodic; op.adjoint = fwd_form ? 0 : 1;
     op.symmetric = (p->order == 2) ? 1 : -1;
 
     // chunk classes: cyclic lines have one; closed lines distinguish first / interior / last
@@ -193,7 +198,7 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
         for (int j = 0; j < m; ++j) {
             const double f = fwd[((size_t)cl * m + j) * 4], r = fwd[((size_t)cl * m + j) * 4 + 1];
             double *c = &ifw[((size_t)cl * m + j) * 4];
-            if (which == 0) { c[0] = f * op.tap[3]; c[1] = f * op.tap[4]; c[2] = f * op.tap[5]; }
+            if (fwd_form) { c[0] = f * op.tap[3]; c[1] = f * op.tap[4]; c[2] = f * op.tap[5]; }
             else { c[0] = f; c[1] = 0.0; c[2] = 0.0; }
             c[3] = f * r;
         }

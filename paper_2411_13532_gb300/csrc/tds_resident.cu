@@ -1005,7 +1005,7 @@ tds_status launch_pipe_w(const tds_plan *p, int which, const TileMaps &tm, const
     const int smem = (int)pipe_smem_bytes(p->n, p->P, p->dtype, p->pipe_nbuf, Tr::W);
     const long long units = (long long)op.ngroups * (kSZ / Tr::W);
     const int grid = units < p->pipe_grid ? (int)units : p->pipe_grid;
-    return which ? launch_pipe_t<Tr, true>(op, tm, in, out, p->pipe_nbuf, smem, grid, st)
+    return op.adjoint ? launch_pipe_t<Tr, true>(op, tm, in, out, p->pipe_nbuf, smem, grid, st)
                  : launch_pipe_t<Tr, false>(op, tm, in, out, p->pipe_nbuf, smem, grid, st);
 }
 
@@ -1013,7 +1013,7 @@ template <typename Tr, int V>
 tds_status launch_resident_v(const tds_plan *p, int which, const TileMaps &tm, const void *in, void *out,
                              cudaStream_t st) {
     const DevOp &op = p->op[which];
-    return which ? launch_resident_t<Tr, V, true>(op, tm, in, out, p->resident_smem, st)
+    return op.adjoint ? launch_resident_t<Tr, V, true>(op, tm, in, out, p->resident_smem, st)
                  : launch_resident_t<Tr, V, false>(op, tm, in, out, p->resident_smem, st);
 }
 

@@ -191,9 +191,9 @@ tds_status launch_streaming(const tds_plan *p, int which, const void *in, void *
                             cudaStream_t st) {
     const DevOp &op = p->op[which];
     if (p->dtype == TDS_F64)
-        return which ? launch_streaming_t<double, true>(op, in, out, ws, st)
+        return op.adjoint ? launch_streaming_t<double, true>(op, in, out, ws, st)
                      : launch_streaming_t<double, false>(op, in, out, ws, st);
-    return which ? launch_streaming_t<float, true>(op, in, out, ws, st)
+    return op.adjoint ? launch_streaming_t<float, true>(op, in, out, ws, st)
                  : launch_streaming_t<float, false>(op, in, out, ws, st);
 }
 
