@@ -6,9 +6,11 @@ FP32 storage:
     x layout:  D1 u, D2 u, D1^T u          (first, second derivative, adjoint of the first)
     reorder x -> y;  the same three along y
     reorder y -> z;  the same three along z
-i.e. 18 directional operators of 512^3 points and 4 reorders.  ``value`` is directional-
-derivative points per second (Gpoints/s) over all ranks, with the field resident in HBM;
-every field is 0.5-1 GiB, larger than L2, so no flush is needed between steps.
+i.e. 18 directional operators of 512^3 points and 4 reorders.  The three operators of one
+direction share one read of the field (``tds_deriv_multi``: one fused pass).  ``value`` is
+directional-derivative points per second (Gpoints/s) over all ranks, with the field resident in
+HBM; every field is 0.5-1 GiB, larger than L2, so no flush is needed between steps.  After the
+timed steps each operator is also timed on its own (``breakdown`` entries ``single/...``).
 
 ``e2e`` repeats the step through host buffers: the x-layout field comes from pinned host
 memory each step (``tds_deriv_host`` copies it in for the first operator) and every one of
@@ -183,6 +185,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     S, P = args.size, args.P
     shape = (S, S, S)
+    bc = "periodic"
     npts = S ** 3
     f, _ = inputs.fourier_field(shape, seed=2 + rank, kmax=100, noise=0.1, noise_kind="normal",
                                 device=dev)
@@ -196,14 +199,14 @@ def run_ours(args, rank, world, local_rank):
              "o": [torch.empty_like(ux) for _ in range(3)], "plans": {}}
         for direc in "xyz":
             for order in (1, 2):
-                d["plans"][(direc, order)] = tds.Plan(shape, direc, order, "periodic", P=P, dtype=dt)
+                d["plans"][(direc, order)] = tds.Plan(shape, direc, order, bc, P=P, dtype=dt)
         d["ws"] = {k: p.workspace() for k, p in d["plans"].items()}
         data[name] = d
     del f
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
 
-    # per-operator CUDA events on the launching stream
+    # per-launch CUDA events on the launching stream
     timing = {}
 
     def timed(key, fn):
@@ -216,22 +219,27 @@ def run_ours(args, rank, world, local_rank):
 
     launches = [0]
 
+    def fused(p1, p2):
+        # one pass computes D1, D2 and D1^T when both plans run resident with one width and
+        # the adjoint has the forward form (periodic lines)
+        return (p1.variant == p2.variant == "resident" and p1.width == p2.width and bc == "periodic")
+
     def step(record):
+        # per direction: D1, D2 and D1^T of one input through tds_deriv_multi (one fused pass)
         for name, _ in dtypes:
             d = data[name]
             src = d["ux"]
             for direc, nxt in (("x", "uy"), ("y", "uz"), ("z", None)):
                 p1, p2 = d["plans"][(direc, 1)], d["plans"][(direc, 2)]
-                w1, w2 = d["ws"][(direc, 1)], d["ws"][(direc, 2)]
-                ops = [("d1", lambda: p1.deriv(src, d["o"][0], w1)),
-                       ("d2", lambda: p2.deriv(src, d["o"][1], w2)),
-                       ("d1t", lambda: p1.adjoint(src, d["o"][2], w1))]
-                for key, fn in ops:
-                    if record:
-                        timed((name, key, p1.variant if key != "d2" else p2.variant), fn)
-                    else:
-                        fn()
-                    launches[0] += 3 if p1.variant == "streaming" else 1
+                ws = d["ws"][(direc, 1)] if p1.ws_bytes >= p2.ws_bytes else d["ws"][(direc, 2)]
+                fn = (lambda s=src, a=p1, b=p2, w=ws:
+                      tds.deriv_multi([(a, False), (b, False), (a, True)], s, outs=d["o"], ws=w))
+                if record:
+                    timed((name, "multi", p1.variant), fn)
+                else:
+                    fn()
+                launches[0] += 1 if fused(p1, p2) else sum(3 if p.variant == "streaming" else 1
+                                                           for p in (p1, p2, p1))
                 if nxt is not None:
                     rfn = (lambda s=src, t=d[nxt], a=direc, b={"uy": "y", "uz": "z"}[nxt]:
                            tds.reorder(s, shape, a, b, out=t))
@@ -265,48 +273,82 @@ def run_ours(args, rank, world, local_rank):
     ops_per_step = 18
     value = job_throughput(world, ops_per_step, npts, args.steps, ms)
 
-    # per-kernel averages
+    # per-kernel averages over the timed steps
     per = {}
     for key, evs in timing.items():
         per[key] = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
 
+    # the single operators, one launch each (after the timed region, not part of `value`):
+    # the per-kernel fractions of HBM of D1, D2 and D1^T on their own
+    single = {}
+    for name, _ in dtypes:
+        d = data[name]
+        p1, p2 = d["plans"][("x", 1)], d["plans"][("x", 2)]
+        w1, w2 = d["ws"][("x", 1)], d["ws"][("x", 2)]
+        for key, fn, var in (("d1", lambda: p1.deriv(d["ux"], d["o"][0], w1), p1.variant),
+                             ("d2", lambda: p2.deriv(d["ux"], d["o"][1], w2), p2.variant),
+                             ("d1t", lambda: p1.adjoint(d["ux"], d["o"][2], w1), p1.variant)):
+            for _ in range(2):
+                fn()
+            evs = []
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+            single[(name, key, var)] = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+
+    m_chunk = S // args.P
+
+    def algorithmic(key):
+        """(directional-derivative points, algorithmic HBM bytes, FP64 operations) of one launch."""
+        name, kind = key[0], key[1]
+        es = 8 if name == "f64" else 4
+        if kind == "multi":   # one read of the field, three results written
+            return 3 * npts, 4 * es * npts, sum(fp64_ops_per_point(o, m_chunk) for o in ("d1", "d2", "d1t")) * npts
+        if kind == "reorder":
+            return npts, 2 * es * npts, 0.0
+        return npts, 2 * es * npts, fp64_ops_per_point(kind, m_chunk) * npts
+
     peaks, peak_kind = load_peaks()
     hbm = float(peaks["hbm_gbs"])
     breakdown = {}
-    for key, avg_ms in sorted(per.items()):
-        name = key[0]
-        es = 8 if name == "f64" else 4
-        gpts = npts / (avg_ms * 1e-3) / 1e9
-        gbs = 2 * es * npts / (avg_ms * 1e-3) / 1e9
-        ent = {"ms": round(avg_ms, 4), "gpoints_s": round(gpts, 2), "alg_GB_s": round(gbs, 1),
-               "hbm_frac": round(gbs / hbm, 4)}
-        breakdown["/".join(str(k) for k in key)] = ent
-    # dominant kernel by total time
+    for src_tab, tag in ((per, ""), (single, "single/")):
+        for key, avg_ms in sorted(src_tab.items()):
+            pts, nbytes, _ = algorithmic(key)
+            gbs = nbytes / (avg_ms * 1e-3) / 1e9
+            breakdown[tag + "/".join(str(k) for k in key)] = {
+                "ms": round(avg_ms, 4), "gpoints_s": round(pts / (avg_ms * 1e-3) / 1e9, 2),
+                "alg_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+    # dominant kernel of the timed step by total time
     totals = {k: per[k] * len(timing[k]) for k in per}
     dom = max(totals, key=totals.get)
     dom_ms = per[dom]
-    es = 8 if dom[0] == "f64" else 4
+    pts, nbytes, ops = algorithmic(dom)
     clocks = clk.summary()
-    roofline = None
     if dom[0] == "f64" and dom[1] != "reorder":
-        # FP64 pipe bound: ops per point issued by the kernel vs the FP64 pipe's peak rate,
+        # FP64 pipe bound: FP64 operations issued vs the FP64 pipe's peak rate,
         # 2 FP64 instructions per clock per SM x 152 SMs x sampled SM clock
         sm_mhz = clocks["sm_mhz"] or 2070.0
         peak = 2 * 152 * sm_mhz * 1e6 / 1e9
-        ach = fp64_ops_per_point(dom[1], S // args.P) * npts / (dom_ms * 1e-3) / 1e9
+        ach = ops / (dom_ms * 1e-3) / 1e9
         roofline = {"kernel": "/".join(str(k) for k in dom), "bound": "alu", "achieved": round(ach, 1),
                     "peak": round(peak, 1), "unit": "Gop/s (FP64 pipe)", "frac": round(ach / peak, 4),
                     "peak_source": "derived: 2 FP64 ops/clk/SM x 152 SMs x median SM clock",
-                    "hbm_frac": round(2 * es * npts / (dom_ms * 1e-3) / 1e9 / hbm, 4)}
+                    "hbm_frac": round(nbytes / (dom_ms * 1e-3) / 1e9 / hbm, 4)}
     else:
-        ach = 2 * es * npts / (dom_ms * 1e-3) / 1e9
+        ach = nbytes / (dom_ms * 1e-3) / 1e9
         roofline = {"kernel": "/".join(str(k) for k in dom), "bound": "hbm", "achieved": round(ach, 1),
-                    "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
-                    "peak_source": peak_kind}
+                    "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "peak_source": peak_kind}
     kkey = "%s_%s_%s_%d" % (dom[0], dom[1], dom[2] if len(dom) > 2 else "", S)
-    roofline["traffic"] = traffic_from_profiles(kkey)
-    # the FP32 derivative kernels against HBM (the 70 % target)
-    f32 = [v for k, v in breakdown.items() if k.startswith("f32/d")]
+    traffic = traffic_from_profiles(kkey)
+    roofline["traffic"] = traffic
+    roofline["alg_bytes_per_launch"] = nbytes
+    # the FP32 derivative kernels on their own against HBM (the 70 % target)
+    f32 = [v for k, v in breakdown.items() if k.startswith("single/f32/d")]
     roofline["f32_deriv_hbm_frac_min"] = min(e["hbm_frac"] for e in f32) if f32 else None
 
     # ------------------------------------------------------------------ end to end

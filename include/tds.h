@@ -151,6 +151,24 @@ TDS_API tds_status tds_deriv_adjoint(const tds_plan *plan, const void *g, void *
                              size_t ws_bytes, void *stream);
 
 /*
+ * tds_deriv_multi -- several operators of one input: outs[i] = plans[i]'s derivative
+ * (adjoint[i] = 0) or its adjoint (adjoint[i] = 1) of `in`, 1 <= count <= 4.  When every plan
+ * runs RESIDENT with the same chunks and CTA width and every operator has the forward form
+ * (derivatives, and adjoints on periodic lines), one kernel computes them all from a single
+ * read of `in` (the field is read from HBM once and each result written once; Sec. 5 fuses the
+ * transport equation's derivative operators the same way); otherwise the operators run one
+ * after another on `stream`.  Results are those of the single calls.
+ *   plans   : count plans over the same field shape, direction and dtype (TDS_ERR_ARG otherwise).
+ *   adjoint : count flags, 0 or 1.
+ *   in, outs: device arrays as in tds_deriv; no output may overlap `in` or another output
+ *             (TDS_ERR_ALIAS).
+ *   ws, ws_bytes : one workspace of at least the largest tds_workspace_bytes of the plans
+ *             (used only when the operators run one after another).
+ */
+TDS_API tds_status tds_deriv_multi(int count, const tds_plan *const *plans, const int *adjoint,
+                           const void *in, void *const *outs, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * tds_deriv_host -- tds_deriv with the input and the result in HOST memory (not in the paper:
  * the end-to-end form of the call).
  *   host_in  : N*n elements in the plan's direction layout, copied to d_in; NULL when the

@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import TdsError  # noqa: F401
 
-__all__ = ["Plan", "deriv", "deriv_adjoint", "reorder", "CompactDeriv", "compact_deriv",
+__all__ = ["Plan", "deriv", "deriv_adjoint", "deriv_multi", "reorder", "CompactDeriv", "compact_deriv",
            "device_status", "grid_spacing", "TdsError"]
 
 _TORCH_DTYPES = {torch.float64: "f64", torch.float32: "f32"}
@@ -192,6 +192,34 @@ def _plan(shape, direction, order, bc, P, h, dtype, mode, device):
     if p is None:
         p = _PLANS[key] = Plan(shape, direction, order, bc, P, h, dtype, mode, device=dev)
     return p
+
+
+def deriv_multi(ops, x, outs=None, ws=None, stream=None):
+    """Several operators of one input through ``tds_deriv_multi``: ``ops`` is a list of
+    ``(plan, adjoint)`` pairs (up to 4) over the same field; returns the list of results.
+    Resident plans of one geometry with forward-form operators run as one fused pass."""
+    if not 1 <= len(ops) <= 4:
+        raise ValueError("deriv_multi takes 1 to 4 operators")
+    plans = [p for p, _ in ops]
+    p0 = plans[0]
+    _check_tensor(x, p0.dtype, p0.numel, "input")
+    if outs is None:
+        outs = [torch.empty_like(x) for _ in ops]
+    for o in outs:
+        _check_tensor(o, p0.dtype, p0.numel, "out")
+    if ws is None:
+        need = max(p.ws_bytes for p in plans)
+        ws = torch.empty(need, dtype=torch.uint8, device=x.device) if need else None
+    n = len(ops)
+    hp = (ctypes.c_void_p * n)(*[p._handle.value for p in plans])
+    ad = (ctypes.c_int * n)(*[1 if a else 0 for _, a in ops])
+    op_ = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    wp = ctypes.c_void_p(ws.data_ptr()) if ws is not None else None
+    wb = ws.numel() if ws is not None else 0
+    with torch.cuda.device(p0.device):
+        _lib.check(_lib.lib().tds_deriv_multi(n, hp, ad, ctypes.c_void_p(x.data_ptr()), op_, wp, wb,
+                                              _stream_ptr(stream, p0.device)), "tds_deriv_multi")
+    return outs
 
 
 def deriv(field, shape, direction, order, bc, P=1, h=None, mode="exact", out=None):

@@ -312,6 +312,39 @@ tds_status tds_deriv_adjoint(const tds_plan *p, const void *g, void *out, void *
     return run(p, 1, g, out, ws, ws_bytes, stream);
 }
 
+tds_status tds_deriv_multi(int count, const tds_plan *const *plans, const int *adjoint, const void *in,
+                           void *const *outs, void *ws, size_t ws_bytes, void *stream) {
+    if (count < 1 || count > kMaxMulti || !plans || !adjoint || !outs) return TDS_ERR_ARG;
+    const tds_plan *p0 = plans[0];
+    if (!p0) return TDS_ERR_ARG;
+    const size_t bytes = (size_t)p0->n * p0->nlines * elem_size(p0->dtype);
+    int which[kMaxMulti];
+    bool fused = true;
+    for (int i = 0; i < count; ++i) {
+        const tds_plan *p = plans[i];
+        if (!p || (adjoint[i] != 0 && adjoint[i] != 1)) return TDS_ERR_ARG;
+        which[i] = adjoint[i];
+        // every operator maps the same field shape in the same direction layout
+        if (p->nx != p0->nx || p->ny != p0->ny || p->nz != p0->nz || p->dir != p0->dir ||
+            p->dtype != p0->dtype)
+            return TDS_ERR_ARG;
+        const tds_status s = check_call(p, in, outs[i], ws, ws_bytes);
+        if (s != TDS_OK) return s;
+        for (int j = 0; j < i; ++j)
+            if (overlaps(outs[i], bytes, outs[j], bytes)) return TDS_ERR_ALIAS;
+        // one pass needs resident plans of one geometry and width, forward-form operators
+        fused = fused && p->variant == TDS_VARIANT_RESIDENT && p->lanes == 1 && p->P == p0->P &&
+                p->width == p0->width && p->op[which[i]].adjoint == 0;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (fused) return launch_resident_multi(plans, which, count, in, outs, st);
+    for (int i = 0; i < count; ++i) {
+        const tds_status s = launch(plans[i], which[i], in, outs[i], ws, st);
+        if (s != TDS_OK) return s;
+    }
+    return TDS_OK;
+}
+
 tds_status tds_deriv_host(const tds_plan *p, const void *host_in, void *host_out, void *d_in,
                           void *d_out, void *ws, size_t ws_bytes, void *stream) {
     return run_host(p, 0, host_in, host_out, d_in, d_out, ws, ws_bytes, stream);

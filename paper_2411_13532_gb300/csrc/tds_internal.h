@@ -15,6 +15,7 @@ constexpr int kTaps = 7;          // stencil offsets -3..3 (closure rows reach 3
 constexpr int kEdgeRows = 4;      // closed lines: rows 0..3 and n-4..n-1 carry their own taps
 constexpr int kMaxResidentP = 16; // resident kernel: one warp per chunk, at most 16 warps
 constexpr int kHostSlabs = 8;     // host entry points: copies and compute pipelined over 8 slabs
+constexpr int kMaxMulti = 4;      // operators one fused pass (tds_deriv_multi) may compute
 
 // Number of per-row coefficient arrays of one operator (Algorithm 4 output, per chunk class):
 //   f  : forward factor, 1/b_j for j <= 1, 1/(b_j - a_j s^c_{j-1}) for j >= 2
@@ -126,6 +127,10 @@ int resident_box_rows(int n, int m, tds_dtype dtype, int w);
 size_t pipe_smem_bytes(int n, int P, tds_dtype dtype, int nbuf, int w);
 tds_status launch_resident(const tds_plan *p, int which, const void *in, void *out,
                            cudaStream_t st);
+// Fused pass: operators plans[i]->op[which[i]] (forward form, one shared geometry, resident
+// width and shared memory of plans[0]) of one input into outs[i].
+tds_status launch_resident_multi(const tds_plan *const *plans, const int *which, int count, const void *in,
+                                 void *const *outs, cudaStream_t st);
 tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *out,
                             cudaStream_t st);
 size_t segmented_ws_bytes(const tds_plan *p);

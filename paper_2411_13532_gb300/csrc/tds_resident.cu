@@ -721,6 +721,113 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_co
     store_tile<Tr, V>(op, tm, tile, out + gofs, x0, y0, k, c);
 }
 
+// Several forward-form operators of one input in one pass (the transport-equation kernels of
+// Sec. 5 share one read of the field among several derivative operators): each CTA sweeps its
+// W lines once per operator, re-loading the tile for every operator after the first from L2
+// (the CTA stored its previous result only microseconds before), so HBM sees one read of the
+// input and one write per result.  All operators share the geometry of op[0].
+struct MultiArgs {
+    DevOp op[kMaxMulti];
+    void *out[kMaxMulti];
+    int count;
+};
+
+struct MultiMaps {
+    CUtensorMap in;
+    CUtensorMap out[kMaxMulti];
+    int box_rows;
+};
+
+template <typename Tr>
+__global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_multi(const __grid_constant__ MultiArgs ma,
+                                                                       const __grid_constant__ MultiMaps mm,
+                                                                       const typename Tr::S *__restrict__ in) {
+    using S = typename Tr::S;
+    constexpr int W = Tr::W;
+    constexpr int parts = kSZ / W;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int failed;
+    const DevOp &op0 = ma.op[0];
+    const int n = op0.n, m = op0.m, P = op0.P;
+    const int k = threadIdx.x / W, c = threadIdx.x % W;
+    const long long g = blockIdx.x / parts;
+    const int x0 = (int)(blockIdx.x % parts) * W;
+    const int y0 = (int)(g * n);                                // < 2^31, checked by the host
+    const size_t gofs = (size_t)g * n * kSZ + x0;
+    S *tile = reinterpret_cast<S *>(smem);
+    S *xs = reinterpret_cast<S *>(smem + tile_bytes_of(n, sizeof(S), W));
+    double *ends = reinterpret_cast<double *>(smem + tile_bytes_of(n, sizeof(S), W) + xs_bytes_of(sizeof(S), W));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ends + (size_t)2 * P * W);
+    const uint32_t chunk_bytes = (uint32_t)((size_t)m * W * sizeof(S));
+    if constexpr (W < kSZ) {
+        if ((smem_u32(tile) & 127u) != 0) {   // see k_resident
+            if (threadIdx.x == 0) atomicExch(&g_device_status, (int)TDS_ERR_CUDA);
+            return;
+        }
+    }
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int q = 0; q < P; ++q) mbar_init(&bars[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    for (int o = 0; o < ma.count; ++o) {
+        const DevOp &op = ma.op[o];
+        const uint32_t par = (uint32_t)(o & 1);
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < P; ++q) {
+                mbar_expect_tx(&bars[q], chunk_bytes);
+                if constexpr (W == kSZ) {
+                    bulk_g2s(tile + (size_t)q * m * W, in + gofs + (size_t)q * m * kSZ, chunk_bytes, &bars[q]);
+                } else {
+                    for (int r = q * m; r < (q + 1) * m; r += mm.box_rows)
+                        tma_load_2d(tile + (size_t)r * W, &mm.in, x0, y0 + r, &bars[q]);
+                }
+            }
+        }
+        bool ok = mbar_wait(&bars[k], par);
+        if (k > 0 || op.periodic) ok = mbar_wait(&bars[(k - 1 + P) % P], par) && ok;
+        if (k < P - 1 || op.periodic) ok = mbar_wait(&bars[(k + 1) % P], par) && ok;
+        if (!op.periodic && (k == 0 || k == P - 1))
+            for (int q = 0; q < P; ++q) ok = mbar_wait(&bars[q], par) && ok;
+        if (!ok) atomicExch(&failed, 1);
+        int unsafe = 0;
+        Pack<typename Tr::A, 1> hb[2], ha[2];
+        if (ok) read_halo<Tr, 1, false>(op, TileView<S>{tile, 0, n, in + gofs}, xs, k, c, hb, ha, unsafe);
+        __syncthreads();
+        if (failed) {
+            // let this round's copies land before the CTA's shared memory is released
+            for (int q = threadIdx.x; q < P; q += blockDim.x) mbar_wait(&bars[q], par);
+            if (threadIdx.x == 0) record_timeout();
+            return;
+        }
+        group_sweep<Tr, 1, false>(op, tile, xs, ends, k, c, hb, ha, unsafe);
+        S *og = static_cast<S *>(ma.out[o]) + gofs;
+        if (kBulkStore<Tr>) {
+            fence_async_smem();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if constexpr (W == kSZ) {
+                    bulk_s2g(og, tile, (uint32_t)tile_bytes_of(n, sizeof(S)));
+                } else {
+                    for (int r = 0; r < n; r += mm.box_rows)
+                        tma_store_2d(&mm.out[o], x0, y0 + r, tile + (size_t)r * W);
+                }
+                bulk_commit();
+                bulk_wait_read();   // the tile is refilled by the next operator's copies
+            }
+        } else {
+            const size_t ot = (size_t)k * m * W + c, ob = (size_t)k * m * kSZ + c;
+#pragma unroll 4
+            for (int j = 0; j < m; ++j) og[ob + (size_t)j * kSZ] = tile[ot + (size_t)j * W];
+        }
+        // every thread is done with the tile, the scratch rows and `ends` before the next
+        // operator's copies (async proxy) overwrite them
+        fence_async_smem();
+        __syncthreads();
+    }
+}
+
 // Persistent variant: each CTA walks units (W lines of a group) blockIdx.x, +gridDim.x, ...
 // through `nbuf` tile buffers; the TMA copies of a unit are issued `nbuf` units ahead, so HBM
 // reads stay in flight while the threads sweep.
@@ -1111,6 +1218,48 @@ tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *
     return W == 16 ? launch_pipe_w<TrF32w<16>>(p, which, tm, in, out, st)
          : W == 8  ? launch_pipe_w<TrF32w<8>>(p, which, tm, in, out, st)
                    : launch_pipe_w<TrF32>(p, which, tm, in, out, st);
+}
+
+namespace {
+template <typename Tr>
+tds_status launch_multi_t(const MultiArgs &ma, const MultiMaps &mm, const void *in, int smem, cudaStream_t st) {
+    using S = typename Tr::S;
+    auto kern = k_resident_multi<Tr>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return TDS_ERR_CUDA;
+    const unsigned grid = (unsigned)((long long)ma.op[0].ngroups * (kSZ / Tr::W));
+    kern<<<grid, ma.op[0].P * Tr::W, smem, st>>>(ma, mm, static_cast<const S *>(in));
+    return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
+}
+} // namespace
+
+tds_status launch_resident_multi(const tds_plan *const *plans, const int *which, int count, const void *in,
+                                 void *const *outs, cudaStream_t st) {
+    const tds_plan *p = plans[0];
+    if (count < 1 || count > kMaxMulti) return TDS_ERR_ARG;
+    MultiArgs ma;
+    MultiMaps mm;
+    std::memset(&ma, 0, sizeof(ma));
+    std::memset(&mm, 0, sizeof(mm));
+    ma.count = count;
+    mm.box_rows = p->box_rows;
+    const long long rows = (long long)p->n * (p->nlines / kSZ);
+    for (int i = 0; i < count; ++i) {
+        ma.op[i] = plans[i]->op[which[i]];
+        ma.out[i] = outs[i];
+        if (p->width < kSZ && p->dtype == TDS_F32 &&
+            !encode_rows(&mm.out[i], outs[i], p->dtype, rows, p->width, p->box_rows))
+            return TDS_ERR_CUDA;
+    }
+    if (p->width < kSZ && !encode_rows(&mm.in, in, p->dtype, rows, p->width, p->box_rows)) return TDS_ERR_CUDA;
+    const int W = p->width, smem = p->resident_smem;
+    if (p->dtype == TDS_F64)
+        return W == 16 ? launch_multi_t<TrF64w<16>>(ma, mm, in, smem, st)
+             : W == 8  ? launch_multi_t<TrF64w<8>>(ma, mm, in, smem, st)
+                       : launch_multi_t<TrF64>(ma, mm, in, smem, st);
+    return W == 16 ? launch_multi_t<TrF32w<16>>(ma, mm, in, smem, st)
+         : W == 8  ? launch_multi_t<TrF32w<8>>(ma, mm, in, smem, st)
+                   : launch_multi_t<TrF32>(ma, mm, in, smem, st);
 }
 
 namespace {

@@ -73,6 +73,8 @@ def test_null_pointer_errors_need_no_gpu(L):
     assert L.tds_deriv(None, None, None, None, 0, None) == _lib.ERR_ARG
     assert L.tds_deriv_adjoint(None, None, None, None, 0, None) == _lib.ERR_ARG
     assert L.tds_deriv_host(None, None, None, None, None, None, 0, None) == _lib.ERR_ARG
+    assert L.tds_deriv_multi(0, None, None, None, None, None, 0, None) == _lib.ERR_ARG
+    assert L.tds_deriv_multi(5, None, None, None, None, None, 0, None) == _lib.ERR_ARG
     assert L.tds_deriv_adjoint_host(None, None, None, None, None, None, 0, None) == _lib.ERR_ARG
     sz = ctypes.c_size_t()
     assert L.tds_workspace_bytes(None, ctypes.byref(sz)) == _lib.ERR_ARG

@@ -149,6 +149,46 @@ def test_host_entry_points_match_device_calls(dtype, case):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("bc", ["periodic", "closed"])
+@pytest.mark.parametrize("width", [None, 16, 8])
+def test_multi_operator_pass_matches_single_calls(dtype, bc, width):
+    """tds_deriv_multi (D1, D2 and D1^T of one input; one fused pass when the operators have
+    the forward form, one after another otherwise) gives bitwise the single calls' results."""
+    shape = (16, 48, 64)
+    t = TORCH[dtype]
+    p1 = tds.Plan(shape, "x", 1, bc, P=8, dtype=t, width=width)
+    p2 = tds.Plan(shape, "x", 2, bc, P=8, dtype=t, width=width)
+    x = inputs.uniform_field(shape, seed=21, device="cuda", dtype=t).reshape(-1)
+    refs = [p1.deriv(x), p2.deriv(x), p1.adjoint(x)]
+    outs = tds.deriv_multi([(p1, False), (p2, False), (p1, True)], x)
+    for r, o in zip(refs, outs):
+        assert torch.equal(r, o)
+    # one operator, and a repeated operator
+    o1 = tds.deriv_multi([(p2, False)], x)[0]
+    assert torch.equal(o1, refs[1])
+    o2 = tds.deriv_multi([(p1, False), (p2, False), (p1, False), (p2, False)], x)
+    assert torch.equal(o2[2], refs[0]) and torch.equal(o2[3], refs[1])
+
+
+def test_multi_operator_pass_fallbacks_and_errors():
+    shape = (12, 40, 32)
+    x = inputs.uniform_field(shape, seed=22, device="cuda").reshape(-1)
+    ps = tds.Plan(shape, "z", 1, "periodic", P=3, variant="streaming")
+    pr = tds.Plan(shape, "z", 2, "periodic", P=3)
+    outs = tds.deriv_multi([(ps, False), (pr, False), (ps, True)], x)
+    assert torch.equal(outs[0], ps.deriv(x)) and torch.equal(outs[1], pr.deriv(x))
+    assert torch.equal(outs[2], ps.adjoint(x))
+    other = tds.Plan(shape, "y", 1, "periodic", P=5)   # another direction: another layout
+    with pytest.raises(tds.TdsError):
+        tds.deriv_multi([(pr, False), (other, False)], x)
+    with pytest.raises(tds.TdsError):   # an output aliasing the input
+        tds.deriv_multi([(pr, False)], x, outs=[x])
+    o = torch.empty_like(x)
+    with pytest.raises(tds.TdsError):   # two outputs aliasing each other
+        tds.deriv_multi([(pr, False), (pr, False)], x, outs=[o, o])
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
 @pytest.mark.parametrize("order", [1, 2])
 def test_segmented_long_lines(dtype, bc, order):
     """Lines longer than one CTA's shared memory: segments of 64..256 rows subdivide the chunks
