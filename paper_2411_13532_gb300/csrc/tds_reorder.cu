@@ -67,30 +67,47 @@ __global__ void __launch_bounds__(256) k_rows(const T *__restrict__ in, T *__res
 }
 
 // 32 x 32 (x, y) tile transposes between the x layout and an x-run layout, kTilesZ
-// consecutive z per block (all loads of a block are issued before its stores).
-// grid (nx/32, ny/32, ceil(nz/kTilesZ)), block (32, 8).  to_x selects the direction.
+// consecutive z per block (all loads of a block are issued before its stores).  Global memory
+// moves in 16-byte vectors on both sides: a row of 32 elements is VPR vectors, a pass of 256
+// threads covers 256/VPR rows of a tile; the shared tile is padded to 33 columns.
+// grid (nx/32, ny/32, ceil(nz/kTilesZ)), 256 threads.  to_x selects the direction.
 constexpr int kTilesZ = 4;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_transpose(const T *__restrict__ in, T *__restrict__ out,
                                                   int nx, int ny, int nz, tds_layout other,
                                                   int to_x) {
+    constexpr int epv = 16 / sizeof(T);        // elements per 16-byte vector
+    constexpr int vpr = R / epv;               // vectors per 32-element row
+    constexpr int rpp = 256 / vpr;             // rows per pass
     __shared__ T tile[kTilesZ][R][R + 1];
     const int xb = blockIdx.x, yb = blockIdx.y, z0 = blockIdx.z * kTilesZ;
-    const int t = threadIdx.x, r0 = threadIdx.y;
+    const int vg = threadIdx.x % vpr, rr = threadIdx.x / vpr;
     const int nt = (nz - z0 < kTilesZ) ? nz - z0 : kTilesZ;
     for (int q = 0; q < nt; ++q) {
         const int z = z0 + q;
-        for (int i = r0; i < R; i += 8)
-            tile[q][i][t] = to_x ? __ldg(in + xrun_row(other, xb, yb * R + i, z, nx, ny, nz) + t)
-                                 : __ldg(in + xlayout_row(xb * R + i, yb, z, nx, ny) + t);
+#pragma unroll
+        for (int i = rr; i < R; i += rpp) {
+            const T *src = to_x ? in + xrun_row(other, xb, yb * R + i, z, nx, ny, nz)
+                                : in + xlayout_row(xb * R + i, yb, z, nx, ny);
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(src) + vg);
+            const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+            for (int u = 0; u < epv; ++u) tile[q][i][vg * epv + u] = e[u];
+        }
     }
     __syncthreads();
     for (int q = 0; q < nt; ++q) {
         const int z = z0 + q;
-        for (int i = r0; i < R; i += 8) {
-            if (to_x) out[xlayout_row(xb * R + i, yb, z, nx, ny) + t] = tile[q][t][i];
-            else out[xrun_row(other, xb, yb * R + i, z, nx, ny, nz) + t] = tile[q][t][i];
+#pragma unroll
+        for (int i = rr; i < R; i += rpp) {
+            float4 v;
+            T *e = reinterpret_cast<T *>(&v);
+#pragma unroll
+            for (int u = 0; u < epv; ++u) e[u] = tile[q][vg * epv + u][i];
+            T *dst = to_x ? out + xlayout_row(xb * R + i, yb, z, nx, ny)
+                          : out + xrun_row(other, xb, yb * R + i, z, nx, ny, nz);
+            reinterpret_cast<float4 *>(dst)[vg] = v;
         }
     }
 }
@@ -106,7 +123,7 @@ tds_status launch_t(const void *in, void *out, int nx, int ny, int nz, tds_layou
     } else {
         dim3 grid((unsigned)(nx / R), (unsigned)(ny / R), (unsigned)((nz + kTilesZ - 1) / kTilesZ));
         const int to_x = (to == TDS_LAYOUT_X);
-        k_transpose<T><<<grid, dim3(32, 8), 0, st>>>(src, dst, nx, ny, nz, to_x ? from : to, to_x);
+        k_transpose<T><<<grid, 256, 0, st>>>(src, dst, nx, ny, nz, to_x ? from : to, to_x);
     }
     return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
 }
