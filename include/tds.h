@@ -103,8 +103,13 @@ TDS_API tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_d
 /* Choose the kernel pipeline of a plan (tuning and test hook; call before first use, not
  * concurrently with a call that uses the plan).  TDS_ERR_ARG if the plan cannot run the
  * requested variant (a resident group larger than one CTA's shared memory).  AUTO picks
- * RESIDENT when a group fits in one CTA (and P <= 16), else SEGMENTED when the chunk length has
- * a divisor between 64 and the segment cap (128 rows FP64, 256 FP32), else STREAMING. */
+ * RESIDENT when the lines fit in a CTA (P <= 16) unless, in FP64, its CTAs would leave fewer
+ * than 6 warps per SM (few chunks, large tiles) while the chunk splits into at least two
+ * segments; then
+ * SEGMENTED (segments of 64 up to the cap, 128 rows FP64 / 256 FP32, dividing the chunk length);
+ * else STREAMING.  The
+ * adjoint of a SEGMENTED plan runs on the segment partition on periodic lines, else resident
+ * when the lines fit in a CTA, else through the streaming pipeline. */
 TDS_API tds_status tds_plan_set_variant(tds_plan *plan, tds_variant variant);
 
 /* Lines of a group held by one CTA of the RESIDENT variant: 32 (the whole group, one bulk

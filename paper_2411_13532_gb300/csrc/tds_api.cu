@@ -90,7 +90,12 @@ tds_status check_call(const tds_plan *p, const void *in, const void *out, const 
 tds_status launch(const tds_plan *p, int which, const void *in, void *out, void *ws, cudaStream_t st) {
     if (p->variant == TDS_VARIANT_RESIDENT) return launch_resident(p, which, in, out, st);
     if (p->variant == TDS_VARIANT_PIPELINED) return launch_pipelined(p, which, in, out, st);
-    if (p->variant == TDS_VARIANT_SEGMENTED && which == 0) return launch_segmented(p, in, out, ws, st);
+    if (p->variant == TDS_VARIANT_SEGMENTED) {
+        // the adjoint: on the segment partition when it has the forward form (periodic lines),
+        // else resident when a CTA can hold the lines, else the streaming pipeline
+        if (which == 0 || p->seg_adj.P) return launch_segmented(p, which, in, out, ws, st);
+        if (p->resident_smem) return launch_resident(p, which, in, out, st);
+    }
     return launch_streaming(p, which, in, out, ws, st);
 }
 
@@ -107,7 +112,7 @@ tds_status run(const tds_plan *p, int which, const void *in, void *out, void *ws
 tds_plan slab_of(const tds_plan *p, int g0, int g1) {
     tds_plan q = *p;
     q.nlines = (g1 - g0) * kSZ;
-    for (DevOp *o : {&q.op[0], &q.op[1], &q.seg}) {
+    for (DevOp *o : {&q.op[0], &q.op[1], &q.seg, &q.seg_adj}) {
         o->nlines = q.nlines;
         o->ngroups = g1 - g0;
     }
@@ -255,9 +260,22 @@ tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_dir dir, 
 
 tds_status tds_plan_set_variant(tds_plan *p, tds_variant v) {
     if (!p) return TDS_ERR_ARG;
-    if (v == TDS_VARIANT_AUTO)
-        v = p->resident_smem ? TDS_VARIANT_RESIDENT
-          : p->seg.P ? TDS_VARIANT_SEGMENTED : TDS_VARIANT_STREAMING;
+    if (v == TDS_VARIANT_AUTO) {
+        // resident unless, for FP64 sweeps (bound by the FP64 pipe, which needs warps), its CTAs
+        // would leave fewer than 6 warps per SM (few chunks, large tiles) while the lines split
+        // into at least two segments (one warp per segment keeps more warps per SM; measured:
+        // 256^3 P = 1, 3 warps per SM, segmented 26 % faster; P = 2, 6 warps per SM, resident
+        // 7 % faster).  FP32 sweeps stay resident: the FP32 segmented variant reads its input
+        // twice.  Then segmented, else streaming.
+        bool thin = false;
+        if (p->dtype == TDS_F64 && p->resident_smem && p->seg.P >= 2) {
+            const int ctas = (int)((size_t)p->smem_sm / ((size_t)p->resident_smem + 1024));
+            thin = ctas * (p->P * p->width / 32) < 6;
+        }
+        v = (p->resident_smem && !thin) ? TDS_VARIANT_RESIDENT
+          : p->seg.P ? TDS_VARIANT_SEGMENTED
+          : p->resident_smem ? TDS_VARIANT_RESIDENT : TDS_VARIANT_STREAMING;
+    }
     if (v == TDS_VARIANT_RESIDENT && !p->resident_smem) return TDS_ERR_ARG;
     if (v == TDS_VARIANT_PIPELINED && !p->pipe_nbuf) return TDS_ERR_ARG;
     if (v == TDS_VARIANT_SEGMENTED && !p->seg.P) return TDS_ERR_ARG;

@@ -105,6 +105,7 @@ struct tds_plan {
     int lanes;             // lines per thread in the resident kernels (FP32: 1, 2, 4; FP64: 1, 2)
     tds::DevOp op[2];      // [0] = A^{-1} B, [1] = B^T A^{-T}
     tds::DevOp seg;        // A^{-1} B on the segment partition of the SEGMENTED variant (P = 0: none)
+    tds::DevOp seg_adj;    // periodic lines: the adjoint (forward form) on that partition (P = 0: none)
     double *red_sub_host[2], *red_sup_host[2];
     // host entry points: two copy streams (in, out) and their events (start, done, per slab:
     // input landed, slab computed), created with the plan
@@ -134,7 +135,7 @@ tds_status launch_resident_multi(const tds_plan *const *plans, const int *which,
 tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *out,
                             cudaStream_t st);
 size_t segmented_ws_bytes(const tds_plan *p);
-tds_status launch_segmented(const tds_plan *p, const void *in, void *out, void *ws,
+tds_status launch_segmented(const tds_plan *p, int which, const void *in, void *out, void *ws,
                             cudaStream_t st);
 size_t streaming_ws_bytes(const tds_plan *p);
 tds_status launch_streaming(const tds_plan *p, int which, const void *in, void *out,

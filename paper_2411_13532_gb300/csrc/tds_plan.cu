@@ -321,29 +321,35 @@ tds_status build_plan(tds_plan *p) {
     // operators: [0] A^{-1} B and [1] B^T A^{-T} on the plan's P chunks; [2] A^{-1} B on the
     // segment partition of the SEGMENTED variant: segments of sg rows, 64 <= sg <= 32 KB of one
     // group's rows, sg dividing the chunk length (so segment boundaries include the chunk
-    // boundaries), used only if every boundary system decouples
+    // boundaries), used only if every boundary system decouples; [3] on periodic lines the
+    // adjoint on that partition (forward form, see build_operator)
     int sg = 0;
     {
         const int cap = (p->dtype == TDS_F64) ? 128 : 256;
         for (int d = (p->m < cap ? p->m : cap); d >= 64; --d)
             if (p->m % d == 0) { sg = d; break; }
     }
-    const int nops = sg ? 3 : 2;
-    std::vector<double> rows[3], n1s[3], red[3], sub[3], sup[3], fwd[3], bwd[3], ifw[3];
-    DevOp *ops[3] = {&p->op[0], &p->op[1], &p->seg};
+    const int nops = sg ? (periodic ? 4 : 3) : 2;
+    std::vector<double> rows[4], n1s[4], red[4], sub[4], sup[4], fwd[4], bwd[4], ifw[4];
+    DevOp *ops[4] = {&p->op[0], &p->op[1], &p->seg, &p->seg_adj};
     std::memset(&p->seg, 0, sizeof(p->seg));
+    std::memset(&p->seg_adj, 0, sizeof(p->seg_adj));
     for (int w = 0; w < nops; ++w) {
         const int P = (w < 2) ? p->P : p->n / sg, m = (w < 2) ? p->m : sg;
-        tds_status s = build_operator(p, P, m, (w == 1) ? LT : L, (w == 1), *ops[w], rows[w], n1s[w],
+        const bool adj = (w == 1 || w == 3);
+        tds_status s = build_operator(p, P, m, adj ? LT : L, adj, *ops[w], rows[w], n1s[w],
                                       red[w], sub[w], sup[w], fwd[w], bwd[w], ifw[w]);
         if (s != TDS_OK) return s;
     }
-    if (nops == 3 && !p->seg.red_decoupled) std::memset(&p->seg, 0, sizeof(p->seg));
+    if (nops >= 3 && (!p->seg.red_decoupled || (nops == 4 && !p->seg_adj.red_decoupled))) {
+        std::memset(&p->seg, 0, sizeof(p->seg));
+        std::memset(&p->seg_adj, 0, sizeof(p->seg_adj));
+    }
 
     // one device allocation per plan, 256-byte aligned parts per operator:
     // [rows64 | rows32 | n1 | red | fwd64 | fwd32 | bwd64 | bwd32 | ifw64 | ifw32]
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t off[3][10], total = 0;
+    size_t off[4][10], total = 0;
     for (int w = 0; w < nops; ++w) {
         off[w][0] = total; total = align(total + rows[w].size() * sizeof(double));
         off[w][1] = total; total = align(total + rows[w].size() * sizeof(float));

@@ -1286,9 +1286,11 @@ size_t segmented_ws_bytes(const tds_plan *p) {
     return ((size_t)p->nlines * p->seg.P * 2 * sizeof(double) + 255) & ~(size_t)255;
 }
 
-tds_status launch_segmented(const tds_plan *p, const void *in, void *out, void *ws, cudaStream_t st) {
-    if (p->dtype == TDS_F64) return launch_segmented_t<TrF64>(p->seg, in, out, ws, st);
-    return launch_segmented_t<TrF32>(p->seg, in, out, ws, st);
+tds_status launch_segmented(const tds_plan *p, int which, const void *in, void *out, void *ws, cudaStream_t st) {
+    const DevOp &op = which ? p->seg_adj : p->seg;
+    if (!op.P || op.adjoint) return TDS_ERR_ARG;
+    if (p->dtype == TDS_F64) return launch_segmented_t<TrF64>(op, in, out, ws, st);
+    return launch_segmented_t<TrF32>(op, in, out, ws, st);
 }
 
 tds_status read_device_status() {

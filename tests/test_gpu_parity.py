@@ -117,6 +117,7 @@ HOST_CASES = [   # (shape, direction, P, variant, width): groups = lines / 32
     ((12, 40, 32), "y", 5, "pipelined", None),    # 12 groups
     ((1, 32, 2048), "x", 4, "segmented", None),   # 1 group: fewer groups than slabs
     ((2, 32, 256), "x", 2, "resident", None),     # 2 groups
+    ((4, 32, 512), "x", 1, "segmented", None),    # 4 groups, periodic: the adjoint on the segments
 ]
 
 
@@ -214,6 +215,14 @@ def test_segmented_is_chosen_for_long_lines():
     assert tds.Plan((1, 32, 2048), "x", 1, "periodic", P=4).variant == "segmented"
     assert tds.Plan((1, 32, 4096), "x", 1, "periodic", P=4, dtype=torch.float32).variant == "segmented"
     assert tds.Plan((1, 32, 512), "x", 1, "periodic", P=8).variant == "resident"
+    # few chunks: resident CTAs would leave fewer than 6 warps per SM, segments give more
+    assert tds.Plan((8, 32, 256), "x", 1, "periodic", P=1).variant == "segmented"   # 3 warps / SM
+    assert tds.Plan((8, 32, 256), "x", 1, "periodic", P=2).variant == "resident"    # 6 warps / SM
+    assert tds.Plan((1, 32, 512), "x", 1, "periodic", P=2).variant == "segmented"   # 2 warps / SM
+    # FP32 stays resident (its segmented variant reads the input twice)
+    assert tds.Plan((1, 32, 512), "x", 1, "periodic", P=1, dtype=torch.float32).variant == "resident"
+    # a single 64-row segment per line: resident
+    assert tds.Plan((8, 32, 64), "x", 1, "periodic", P=1).variant == "resident"
     # chunks too short for 64-row segments fall back to streaming
     assert tds.Plan((1, 32, 2048), "x", 1, "periodic", P=64).variant == "streaming"
 
