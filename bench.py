@@ -408,15 +408,19 @@ def run_ours(args, rank, world, local_rank):
 # ------------------------------------------------------------------ per-configuration sweep
 
 SWEEP_CASES = [
-    # (label, shape (nz, ny, nx), directions, orders, bcs, Ps, dtypes, adjoint)
-    ("64^3 D1 x periodic P=1", (64, 64, 64), "x", (1,), ("periodic",), (1,), ("f64",), False),
+    # (label, shape (nz, ny, nx), directions, orders, bcs, Ps, dtypes, kind: "deriv" | "adjoint" | "solve")
+    ("64^3 D1 x periodic P=1", (64, 64, 64), "x", (1,), ("periodic",), (1,), ("f64",), "deriv"),
     ("256^3 D1/D2 x,y,z periodic/closed P=1,4", (256, 256, 256), "xyz", (1, 2), ("periodic", "closed"),
-     (1, 4), ("f64",), False),
+     (1, 4), ("f64",), "deriv"),
     ("512^3 D1/D2 x,y,z periodic P=8 FP64/FP32", (512, 512, 512), "xyz", (1, 2), ("periodic",), (8,),
-     ("f64", "f32"), False),
-    ("256^3 D1^T z closed P=4 FP64/FP32", (256, 256, 256), "z", (1,), ("closed",), (4,), ("f64", "f32"), True),
-    ("1024^3 D1 x,y,z periodic P=8,2", (1024, 1024, 1024), "xyz", (1,), ("periodic",), (8, 2), ("f64",), False),
-    ("256 x 262144 D1 x periodic P=64", (1, 256, 262144), "x", (1,), ("periodic",), (64,), ("f64",), False),
+     ("f64", "f32"), "deriv"),
+    ("512^3 D1^T x periodic P=8 FP64/FP32", (512, 512, 512), "x", (1,), ("periodic",), (8,), ("f64", "f32"),
+     "adjoint"),
+    ("256^3 D1^T z closed P=4 FP64/FP32", (256, 256, 256), "z", (1,), ("closed",), (4,), ("f64", "f32"), "adjoint"),
+    ("1024^3 D1 x,y,z periodic P=8,2", (1024, 1024, 1024), "xyz", (1,), ("periodic",), (8, 2), ("f64",), "deriv"),
+    ("256 x 262144 D1 x periodic P=64", (1, 256, 262144), "x", (1,), ("periodic",), (64,), ("f64",), "deriv"),
+    ("512^3 solve A x = d, x periodic/closed P=8 FP64/FP32", (512, 512, 512), "x", (1, 2),
+     ("periodic", "closed"), (8,), ("f64", "f32"), "solve"),
 ]
 
 
@@ -434,7 +438,7 @@ def run_sweep(args):
     hbm = float(peaks["hbm_gbs"])
     TD = {"f64": torch.float64, "f32": torch.float32}
     reps = max(args.steps, 5)
-    for label, shape, dirs, orders, bcs, Ps, dts, adj in SWEEP_CASES:
+    for label, shape, dirs, orders, bcs, Ps, dts, kind in SWEEP_CASES:
         npts = shape[0] * shape[1] * shape[2]
         for dname in dts:
             dt = TD[dname]
@@ -446,7 +450,8 @@ def run_sweep(args):
                         for P in Ps:
                             plan = tds.Plan(shape, direc, order, bc, P=P, dtype=dt)
                             ws = plan.workspace()
-                            fn = (lambda: plan.adjoint(x, y, ws)) if adj else (lambda: plan.deriv(x, y, ws))
+                            fn = {"adjoint": lambda: plan.adjoint(x, y, ws), "solve": lambda: plan.solve(x, y, ws),
+                                  "deriv": lambda: plan.deriv(x, y, ws)}[kind]
                             for _ in range(max(args.warmup, 3)):
                                 fn()
                             times = []
@@ -463,7 +468,8 @@ def run_sweep(args):
                             es = x.element_size()
                             gbs = 2 * es * npts / (ms * 1e-3) / 1e9
                             print(json.dumps({
-                                "case": label, "dtype": dname, "op": ("D%dT" if adj else "D%d") % order,
+                                "case": label, "dtype": dname,
+                                "op": {"adjoint": "D%dT", "solve": "A%d^-1", "deriv": "D%d"}[kind] % order,
                                 "dir": direc, "bc": bc, "P": P, "variant": plan.variant, "width": plan.width,
                                 "ms": round(ms, 4), "gpoints_s": round(npts / (ms * 1e-3) / 1e9, 2),
                                 "alg_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),

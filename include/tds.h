@@ -156,6 +156,18 @@ TDS_API tds_status tds_deriv_adjoint(const tds_plan *plan, const void *g, void *
                              size_t ws_bytes, void *stream);
 
 /*
+ * tds_solve -- x = A^{-1} d: the DistD2 tridiagonal solve of the plan's compact scheme alone
+ * (Algorithms 4-6 with the reduced chunk-end system between them, the right-hand side given
+ * instead of computed from a stencil), e.g. for a caller that forms its own right-hand side.
+ * A is the plan's left-hand side: alpha on the off-diagonals and 1 on the diagonal (cyclic on
+ * periodic lines), with the closure rows on closed lines.  Same arguments, layout and errors
+ * as tds_deriv.  Runs resident when the plan's lines fit a CTA (any variant but STREAMING),
+ * else through the streaming pipeline.
+ */
+TDS_API tds_status tds_solve(const tds_plan *plan, const void *d, void *x, void *ws, size_t ws_bytes,
+                     void *stream);
+
+/*
  * tds_deriv_multi -- several operators of one input: outs[i] = plans[i]'s derivative
  * (adjoint[i] = 0) or its adjoint (adjoint[i] = 1) of `in`, 1 <= count <= 4.  When every plan
  * runs RESIDENT with the same chunks and CTA width and every operator has the forward form

@@ -137,6 +137,10 @@ class Plan:
                           _stream_ptr(stream, self.device)), what)
         return host_out
 
+    def solve(self, d, out=None, ws=None, stream=None):
+        """x = A^{-1} d: the tridiagonal solve of this plan's compact scheme alone (``tds_solve``)."""
+        return self._run(_lib.lib().tds_solve, d, out, ws, stream, "tds_solve")
+
     def deriv_host(self, host_in, host_out, d_in, d_out, ws=None, stream=None):
         """``tds_deriv_host``: host_in (a host tensor, or None when d_in already holds the input)
         through d_in / d_out to host_out, copies pipelined with the compute inside the call."""

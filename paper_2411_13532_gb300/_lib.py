@@ -28,6 +28,7 @@ SIGNATURES = [
     ("tds_workspace_bytes", _i, [_vp, ctypes.POINTER(_sz)]),
     ("tds_deriv", _i, [_vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_deriv_adjoint", _i, [_vp, _vp, _vp, _vp, _sz, _vp]),
+    ("tds_solve", _i, [_vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_deriv_multi", _i, [_i, ctypes.POINTER(_vp), _ip, _vp, ctypes.POINTER(_vp), _vp, _sz, _vp]),
     ("tds_deriv_host", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_deriv_adjoint_host", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),

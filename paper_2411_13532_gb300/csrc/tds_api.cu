@@ -86,8 +86,13 @@ tds_status check_call(const tds_plan *p, const void *in, const void *out, const 
     return TDS_OK;
 }
 
-// The plan's variant on device buffers (arguments already checked).
+// The plan's variant on device buffers (arguments already checked).  which: 0 the derivative,
+// 1 its adjoint, 2 the solve alone (resident when the lines fit a CTA, else streaming).
 tds_status launch(const tds_plan *p, int which, const void *in, void *out, void *ws, cudaStream_t st) {
+    if (which == 2) {
+        if (p->variant != TDS_VARIANT_STREAMING && p->resident_smem) return launch_resident(p, 2, in, out, st);
+        return launch_streaming(p, 2, in, out, ws, st);
+    }
     if (p->variant == TDS_VARIANT_RESIDENT) return launch_resident(p, which, in, out, st);
     if (p->variant == TDS_VARIANT_PIPELINED) return launch_pipelined(p, which, in, out, st);
     if (p->variant == TDS_VARIANT_SEGMENTED) {
@@ -112,7 +117,7 @@ tds_status run(const tds_plan *p, int which, const void *in, void *out, void *ws
 tds_plan slab_of(const tds_plan *p, int g0, int g1) {
     tds_plan q = *p;
     q.nlines = (g1 - g0) * kSZ;
-    for (DevOp *o : {&q.op[0], &q.op[1], &q.seg, &q.seg_adj}) {
+    for (DevOp *o : {&q.op[0], &q.op[1], &q.op[2], &q.seg, &q.seg_adj}) {
         o->nlines = q.nlines;
         o->ngroups = g1 - g0;
     }
@@ -328,6 +333,10 @@ tds_status tds_deriv(const tds_plan *p, const void *in, void *out, void *ws, siz
 tds_status tds_deriv_adjoint(const tds_plan *p, const void *g, void *out, void *ws,
                              size_t ws_bytes, void *stream) {
     return run(p, 1, g, out, ws, ws_bytes, stream);
+}
+
+tds_status tds_solve(const tds_plan *p, const void *d, void *x, void *ws, size_t ws_bytes, void *stream) {
+    return run(p, 2, d, x, ws, ws_bytes, stream);
 }
 
 tds_status tds_deriv_multi(int count, const tds_plan *const *plans, const int *adjoint, const void *in,

@@ -40,7 +40,9 @@ constexpr double kDecoupleTol = 5.421010862427522e-20;   // 2^-64
 struct DevOp {
     int n, m, P, nlines, ngroups;
     int periodic;   // cyclic lines
-    int adjoint;    // 1: operator is B^T A^{-T} (solve on A^T, then apply the B^T taps)
+    int adjoint;    // how the sweep runs: 0 stencil right-hand side (A^{-1} B, and B^T A^{-T} on
+                    // periodic lines); 1 identity right-hand side on A^T, then the B^T taps
+                    // (the adjoint on closed lines); 2 identity right-hand side, no taps (A^{-1})
     int symmetric;  // interior taps: +1 symmetric (order 2), -1 antisymmetric (order 1)
     int ncls;       // chunk classes (first / interior / last differ on closed lines)
     int cls_first, cls_mid, cls_last;
@@ -103,7 +105,7 @@ struct tds_plan {
     int pipe_nbuf;         // > 0: run the persistent multi-buffered resident kernel
     int pipe_grid;         // its grid (resident CTAs the device holds at once)
     int lanes;             // lines per thread in the resident kernels (FP32: 1, 2, 4; FP64: 1, 2)
-    tds::DevOp op[2];      // [0] = A^{-1} B, [1] = B^T A^{-T}
+    tds::DevOp op[3];      // [0] = A^{-1} B, [1] = B^T A^{-T}, [2] = A^{-1} (the solve alone)
     tds::DevOp seg;        // A^{-1} B on the segment partition of the SEGMENTED variant (P = 0: none)
     tds::DevOp seg_adj;    // periodic lines: the adjoint (forward form) on that partition (P = 0: none)
     double *red_sub_host[2], *red_sup_host[2];

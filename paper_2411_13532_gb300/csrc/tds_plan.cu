@@ -136,7 +136,8 @@ bool preprocess_chunk(int m, const double *a, const double *b, const double *c,
 
 } // namespace
 
-// Build one operator (A^{-1}B if which == 0, B^T A^{-T} if which == 1) into host buffers.
+// Build one operator (A^{-1}B if which == 0, B^T A^{-T} if which == 1, A^{-1} if which == 2)
+// into host buffers.
 // On periodic lines A and B are circulant, so they commute and A is symmetric:
 // B^T A^{-T} = A^{-1} B^T, the forward form with the transposed stencil (L is then the
 // transposed line operator, whose band equals A's); op.adjoint is set only for closed lines,
@@ -151,8 +152,8 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
     const bool periodic = (p->bc == TDS_BC_PERIODIC);
     std::memset(&op, 0, sizeof(op));
     op.n = n; op.m = m; op.P = P; op.nlines = p->nlines; op.ngroups = p->nlines / kSZ;
-    const bool fwd_form = (which == 0) || periodic;
-    op.periodic = periodic; op.adjoint = fwd_form ? 0 : 1;
+    const bool fwd_form = (which == 0) || (which == 1 && periodic);
+    op.periodic = periodic; op.adjoint = fwd_form ? 0 : which;
     op.symmetric = (p->order == 2) ? 1 : -1;
 
     // chunk classes: cyclic lines have one; closed lines distinguish first / interior / last
@@ -318,10 +319,10 @@ tds_status build_plan(tds_plan *p) {
     scheme_line(p->n, p->order, periodic, p->h, L);
     transpose_line(p->n, periodic, L, LT);
 
-    // operators: [0] A^{-1} B and [1] B^T A^{-T} on the plan's P chunks; [2] A^{-1} B on the
-    // segment partition of the SEGMENTED variant: segments of sg rows, 64 <= sg <= 32 KB of one
-    // group's rows, sg dividing the chunk length (so segment boundaries include the chunk
-    // boundaries), used only if every boundary system decouples; [3] on periodic lines the
+    // operators: [0] A^{-1} B, [1] B^T A^{-T} and [2] A^{-1} on the plan's P chunks; [3] A^{-1} B
+    // on the segment partition of the SEGMENTED variant: segments of sg rows, 64 <= sg <= 32 KB of
+    // one group's rows, sg dividing the chunk length (so segment boundaries include the chunk
+    // boundaries), used only if every boundary system decouples; [4] on periodic lines the
     // adjoint on that partition (forward form, see build_operator)
     int sg = 0;
     {
@@ -329,19 +330,19 @@ tds_status build_plan(tds_plan *p) {
         for (int d = (p->m < cap ? p->m : cap); d >= 64; --d)
             if (p->m % d == 0) { sg = d; break; }
     }
-    const int nops = sg ? (periodic ? 4 : 3) : 2;
-    std::vector<double> rows[4], n1s[4], red[4], sub[4], sup[4], fwd[4], bwd[4], ifw[4];
-    DevOp *ops[4] = {&p->op[0], &p->op[1], &p->seg, &p->seg_adj};
+    const int nops = sg ? (periodic ? 5 : 4) : 3;
+    std::vector<double> rows[5], n1s[5], red[5], sub[5], sup[5], fwd[5], bwd[5], ifw[5];
+    DevOp *ops[5] = {&p->op[0], &p->op[1], &p->op[2], &p->seg, &p->seg_adj};
     std::memset(&p->seg, 0, sizeof(p->seg));
     std::memset(&p->seg_adj, 0, sizeof(p->seg_adj));
     for (int w = 0; w < nops; ++w) {
-        const int P = (w < 2) ? p->P : p->n / sg, m = (w < 2) ? p->m : sg;
-        const bool adj = (w == 1 || w == 3);
-        tds_status s = build_operator(p, P, m, adj ? LT : L, adj, *ops[w], rows[w], n1s[w],
+        const int P = (w < 3) ? p->P : p->n / sg, m = (w < 3) ? p->m : sg;
+        const int kind = (w == 1 || w == 4) ? 1 : (w == 2 ? 2 : 0);
+        tds_status s = build_operator(p, P, m, kind == 1 ? LT : L, kind, *ops[w], rows[w], n1s[w],
                                       red[w], sub[w], sup[w], fwd[w], bwd[w], ifw[w]);
         if (s != TDS_OK) return s;
     }
-    if (nops >= 3 && (!p->seg.red_decoupled || (nops == 4 && !p->seg_adj.red_decoupled))) {
+    if (nops >= 4 && (!p->seg.red_decoupled || (nops == 5 && !p->seg_adj.red_decoupled))) {
         std::memset(&p->seg, 0, sizeof(p->seg));
         std::memset(&p->seg_adj, 0, sizeof(p->seg_adj));
     }
@@ -349,7 +350,7 @@ tds_status build_plan(tds_plan *p) {
     // one device allocation per plan, 256-byte aligned parts per operator:
     // [rows64 | rows32 | n1 | red | fwd64 | fwd32 | bwd64 | bwd32 | ifw64 | ifw32]
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t off[4][10], total = 0;
+    size_t off[5][10], total = 0;
     for (int w = 0; w < nops; ++w) {
         off[w][0] = total; total = align(total + rows[w].size() * sizeof(double));
         off[w][1] = total; total = align(total + rows[w].size() * sizeof(float));

@@ -540,7 +540,7 @@ __device__ __forceinline__ void backsub_phase(const DevOp &op, typename Tr::S *r
 // One group, whole line in the tile.  Called by every thread of the CTA after the tile has
 // landed and every thread has run read_halo; leaves the result in the tile (as S).  Contains
 // __syncthreads().
-template <typename Tr, int V, bool ADJ>
+template <typename Tr, int V, int MODE>
 __device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *tile, typename Tr::S *xs,
                                             double *ends, int k, int c,
                                             const Pack<typename Tr::A, V> (&hb)[2],
@@ -552,7 +552,7 @@ __device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *til
     S *row = tile + (size_t)k * m * Tr::W + c;
     Pack<A, V> dprev = zero_a<Tr, V>(), Ssum = zero_a<Tr, V>();
 
-    forward_phase<Tr, V, ADJ>(op, row, xs, k, cls, c, hb, ha, dprev, Ssum, unsafe);
+    forward_phase<Tr, V, MODE != 0>(op, row, xs, k, cls, c, hb, ha, dprev, Ssum, unsafe);
     {
         double e0[V], e1[V];
         chunk_ends<Tr, V>(op, row, cls, dprev, Ssum, e0, e1);
@@ -592,8 +592,8 @@ __device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *til
         F.v[i] = Tr::from_d(ends[(size_t)(2 * k) * Tr::W + c + i]);
         L.v[i] = Tr::from_d(ends[(size_t)(2 * k + 1) * Tr::W + c + i]);
     }
-    backsub_phase<Tr, V, ADJ>(op, row, cls, F, L);
-    if (ADJ) {
+    backsub_phase<Tr, V, MODE == 1>(op, row, cls, F, L);
+    if (MODE == 1) {
         // ---- adjoint: x = B^T y, in place, with the same halo scheme as the forward stencil ----
         __syncthreads();
         Pack<A, V> yb[2], ya[2];
@@ -650,7 +650,7 @@ __device__ __forceinline__ void store_tile(const DevOp &op, const TileMaps &tm, 
 // TMA copies, one mbarrier per chunk (W = 32: one bulk copy of the contiguous chunk; W < 32:
 // m / box_rows tensor boxes); a thread starts as soon as its own chunk and its neighbours'
 // have landed.
-template <typename Tr, int V, bool ADJ>
+template <typename Tr, int V, int MODE>
 __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_constant__ DevOp op,
                                                                  const __grid_constant__ TileMaps tm,
                                                                  const typename Tr::S *__restrict__ in,
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_co
         }
     }
     bool ok = mbar_wait(&bars[k], 0);
-    if (!ADJ) {
+    if (MODE == 0) {
         if (k > 0 || op.periodic) ok = mbar_wait(&bars[(k - 1 + P) % P], 0) && ok;
         if (k < P - 1 || op.periodic) ok = mbar_wait(&bars[(k + 1) % P], 0) && ok;
         // the closure rows of a closed line may reach into the second / second-to-last chunk
@@ -709,7 +709,7 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_co
     if (!ok) atomicExch(&failed, 1);
     int unsafe = 0;
     Pack<typename Tr::A, V> hb[2], ha[2];
-    if (!ADJ && ok) read_halo<Tr, V, false>(op, TileView<S>{tile, 0, n, in + gofs}, xs, k, c, hb, ha, unsafe);
+    if (MODE == 0 && ok) read_halo<Tr, V, false>(op, TileView<S>{tile, 0, n, in + gofs}, xs, k, c, hb, ha, unsafe);
     __syncthreads();
     if (failed) {
         // let every copy land before the CTA's shared memory is released
@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_co
         if (threadIdx.x == 0) record_timeout();
         return;
     }
-    group_sweep<Tr, V, ADJ>(op, tile, xs, ends, k, c, hb, ha, unsafe);
+    group_sweep<Tr, V, MODE>(op, tile, xs, ends, k, c, hb, ha, unsafe);
     store_tile<Tr, V>(op, tm, tile, out + gofs, x0, y0, k, c);
 }
 
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_multi(const __g
             if (threadIdx.x == 0) record_timeout();
             return;
         }
-        group_sweep<Tr, 1, false>(op, tile, xs, ends, k, c, hb, ha, unsafe);
+        group_sweep<Tr, 1, 0>(op, tile, xs, ends, k, c, hb, ha, unsafe);
         S *og = static_cast<S *>(ma.out[o]) + gofs;
         if (kBulkStore<Tr>) {
             fence_async_smem();
@@ -831,7 +831,7 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_multi(const __g
 // Persistent variant: each CTA walks units (W lines of a group) blockIdx.x, +gridDim.x, ...
 // through `nbuf` tile buffers; the TMA copies of a unit are issued `nbuf` units ahead, so HBM
 // reads stay in flight while the threads sweep.
-template <typename Tr, int V, bool ADJ>
+template <typename Tr, int V, int MODE>
 __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_pipe(const __grid_constant__ DevOp op,
                                                                       const __grid_constant__ TileMaps tm,
                                                                       const typename Tr::S *__restrict__ in,
@@ -894,7 +894,7 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_pipe(const __gr
         if (!ok) atomicExch(&failed, 1);
         int unsafe = 0;
         Pack<typename Tr::A, V> hb[2], ha[2];
-        if (!ADJ && ok) read_halo<Tr, V, false>(op, TileView<S>{tile, 0, n, in + unit_ofs(u)}, xs, k, c, hb, ha, unsafe);
+        if (MODE == 0 && ok) read_halo<Tr, V, false>(op, TileView<S>{tile, 0, n, in + unit_ofs(u)}, xs, k, c, hb, ha, unsafe);
         __syncthreads();
         if (failed) {
             // drain every copy still in flight into this CTA's buffers, then give up
@@ -904,7 +904,7 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_pipe(const __gr
             if (threadIdx.x == 0) record_timeout();
             return;
         }
-        group_sweep<Tr, V, ADJ>(op, tile, xs, ends, k, c, hb, ha, unsafe);
+        group_sweep<Tr, V, MODE>(op, tile, xs, ends, k, c, hb, ha, unsafe);
         S *og = out + unit_ofs(u);
         if (!kBulkStore<Tr>) {
             const size_t ot = (size_t)k * op.m * W + c, ob = (size_t)k * op.m * kSZ + c;
@@ -1082,11 +1082,11 @@ tds_status launch_segmented_t(const DevOp &op, const void *in, void *out, void *
     return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
 }
 
-template <typename Tr, int V, bool ADJ>
+template <typename Tr, int V, int MODE>
 tds_status launch_resident_t(const DevOp &op, const TileMaps &tm, const void *in, void *out, int smem,
                              cudaStream_t st) {
     using S = typename Tr::S;
-    auto kern = k_resident<Tr, V, ADJ>;
+    auto kern = k_resident<Tr, V, MODE>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return TDS_ERR_CUDA;
     const unsigned grid = (unsigned)((long long)op.ngroups * (kSZ / Tr::W));
@@ -1094,11 +1094,11 @@ tds_status launch_resident_t(const DevOp &op, const TileMaps &tm, const void *in
     return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
 }
 
-template <typename Tr, bool ADJ>
+template <typename Tr, int MODE>
 tds_status launch_pipe_t(const DevOp &op, const TileMaps &tm, const void *in, void *out, int nbuf, int smem,
                          int grid, cudaStream_t st) {
     using S = typename Tr::S;
-    auto kern = k_resident_pipe<Tr, 1, ADJ>;
+    auto kern = k_resident_pipe<Tr, 1, MODE>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return TDS_ERR_CUDA;
     kern<<<grid, op.P * Tr::W, smem, st>>>(op, tm, static_cast<const S *>(in), static_cast<S *>(out), nbuf);
@@ -1112,16 +1112,21 @@ tds_status launch_pipe_w(const tds_plan *p, int which, const TileMaps &tm, const
     const int smem = (int)pipe_smem_bytes(p->n, p->P, p->dtype, p->pipe_nbuf, Tr::W);
     const long long units = (long long)op.ngroups * (kSZ / Tr::W);
     const int grid = units < p->pipe_grid ? (int)units : p->pipe_grid;
-    return op.adjoint ? launch_pipe_t<Tr, true>(op, tm, in, out, p->pipe_nbuf, smem, grid, st)
-                 : launch_pipe_t<Tr, false>(op, tm, in, out, p->pipe_nbuf, smem, grid, st);
+    if (op.adjoint == 2) return TDS_ERR_ARG;   // the solve alone runs resident or streaming
+    return op.adjoint ? launch_pipe_t<Tr, 1>(op, tm, in, out, p->pipe_nbuf, smem, grid, st)
+                      : launch_pipe_t<Tr, 0>(op, tm, in, out, p->pipe_nbuf, smem, grid, st);
 }
 
 template <typename Tr, int V>
 tds_status launch_resident_v(const tds_plan *p, int which, const TileMaps &tm, const void *in, void *out,
                              cudaStream_t st) {
     const DevOp &op = p->op[which];
-    return op.adjoint ? launch_resident_t<Tr, V, true>(op, tm, in, out, p->resident_smem, st)
-                 : launch_resident_t<Tr, V, false>(op, tm, in, out, p->resident_smem, st);
+    if (op.adjoint == 2) {   // the solve alone: one line per thread
+        if constexpr (V == 1) return launch_resident_t<Tr, 1, 2>(op, tm, in, out, p->resident_smem, st);
+        else return TDS_ERR_ARG;
+    }
+    return op.adjoint ? launch_resident_t<Tr, V, 1>(op, tm, in, out, p->resident_smem, st)
+                      : launch_resident_t<Tr, V, 0>(op, tm, in, out, p->resident_smem, st);
 }
 
 // cuTensorMapEncodeTiled, looked up once through the runtime (no link against the driver API).
@@ -1194,17 +1199,18 @@ tds_status launch_resident(const tds_plan *p, int which, const void *in, void *o
     TileMaps tm;
     if (!tile_maps(p, in, out, &tm)) return TDS_ERR_CUDA;
     const int W = p->width;
+    const int lanes = (p->op[which].adjoint == 2) ? 1 : p->lanes;
     if (p->dtype == TDS_F64) {
         if (W == 16) return launch_resident_v<TrF64w<16>, 1>(p, which, tm, in, out, st);
         if (W == 8) return launch_resident_v<TrF64w<8>, 1>(p, which, tm, in, out, st);
-        return p->lanes == 2 ? launch_resident_v<TrF64, 2>(p, which, tm, in, out, st)
-                             : launch_resident_v<TrF64, 1>(p, which, tm, in, out, st);
+        return lanes == 2 ? launch_resident_v<TrF64, 2>(p, which, tm, in, out, st)
+                          : launch_resident_v<TrF64, 1>(p, which, tm, in, out, st);
     }
     if (W == 16) return launch_resident_v<TrF32w<16>, 1>(p, which, tm, in, out, st);
     if (W == 8) return launch_resident_v<TrF32w<8>, 1>(p, which, tm, in, out, st);
-    return p->lanes == 4 ? launch_resident_v<TrF32, 4>(p, which, tm, in, out, st)
-         : p->lanes == 2 ? launch_resident_v<TrF32, 2>(p, which, tm, in, out, st)
-                         : launch_resident_v<TrF32, 1>(p, which, tm, in, out, st);
+    return lanes == 4 ? launch_resident_v<TrF32, 4>(p, which, tm, in, out, st)
+         : lanes == 2 ? launch_resident_v<TrF32, 2>(p, which, tm, in, out, st)
+                      : launch_resident_v<TrF32, 1>(p, which, tm, in, out, st);
 }
 
 tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *out, cudaStream_t st) {

@@ -165,16 +165,18 @@ __global__ void k_reduced_lines(const __grid_constant__ DevOp op, const double *
     reduced_solve(op, xl, 1);
 }
 
-template <typename T, bool ADJ>
+// MODE: 0 stencil right-hand side; 1 identity right-hand side then B^T (adjoint on closed
+// lines); 2 identity right-hand side only (the solve alone).
+template <typename T, int MODE>
 tds_status launch_streaming_t(const DevOp &op, const void *in, void *out, void *ws, cudaStream_t st) {
     double *ends = static_cast<double *>(ws);
     T *halo = reinterpret_cast<T *>(ends + (size_t)op.nlines * op.P * 2);
     const long long warps = (long long)op.ngroups * op.P;
     const unsigned blocks = (unsigned)((warps + kStreamWarps - 1) / kStreamWarps);
-    k_decouple<T, ADJ><<<blocks, kStreamWarps * 32, 0, st>>>(op, static_cast<const T *>(in),
-                                                            static_cast<T *>(out), ends, halo);
+    k_decouple<T, MODE != 0><<<blocks, kStreamWarps * 32, 0, st>>>(op, static_cast<const T *>(in),
+                                                                   static_cast<T *>(out), ends, halo);
     k_reduced<<<(unsigned)((op.nlines + 127) / 128), 128, 0, st>>>(op, ends);
-    if (!ADJ) k_substitute<T><<<blocks, kStreamWarps * 32, 0, st>>>(op, static_cast<T *>(out), ends);
+    if (MODE != 1) k_substitute<T><<<blocks, kStreamWarps * 32, 0, st>>>(op, static_cast<T *>(out), ends);
     else k_subst_bt<T><<<blocks, kStreamWarps * 32, 0, st>>>(op, static_cast<T *>(out), ends, halo);
     return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
 }
@@ -191,10 +193,12 @@ tds_status launch_streaming(const tds_plan *p, int which, const void *in, void *
                             cudaStream_t st) {
     const DevOp &op = p->op[which];
     if (p->dtype == TDS_F64)
-        return op.adjoint ? launch_streaming_t<double, true>(op, in, out, ws, st)
-                     : launch_streaming_t<double, false>(op, in, out, ws, st);
-    return op.adjoint ? launch_streaming_t<float, true>(op, in, out, ws, st)
-                 : launch_streaming_t<float, false>(op, in, out, ws, st);
+        return op.adjoint == 2 ? launch_streaming_t<double, 2>(op, in, out, ws, st)
+             : op.adjoint == 1 ? launch_streaming_t<double, 1>(op, in, out, ws, st)
+                               : launch_streaming_t<double, 0>(op, in, out, ws, st);
+    return op.adjoint == 2 ? launch_streaming_t<float, 2>(op, in, out, ws, st)
+         : op.adjoint == 1 ? launch_streaming_t<float, 1>(op, in, out, ws, st)
+                           : launch_streaming_t<float, 0>(op, in, out, ws, st);
 }
 
 tds_status launch_reduced_only(const tds_plan *p, const double *rhs, double *x, cudaStream_t st) {

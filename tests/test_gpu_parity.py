@@ -148,6 +148,50 @@ def test_host_entry_points_match_device_calls(dtype, case):
     assert torch.equal(d_in, x)
 
 
+def oracle_solve_lines(lines, order, bc, h):
+    """x = A^{-1} d per line with the oracle's band and its (cyclic) Thomas solver."""
+    n = lines.shape[1]
+    a, b, c, _ = oracle.bands(n, order, bc, h)
+    return np.stack([oracle.tridiag_solve(a, b, c, d, bc == "periodic") for d in lines])
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("variant", ["resident", "streaming", "segmented"])
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+def test_solve_every_point(dtype, variant, order, bc):
+    """tds_solve (A^{-1} d, the DistD2 solve alone) against the oracle's Thomas / Sherman-Morrison
+    solve of the same band, every point, several chunk counts."""
+    shape = (2, 32, 512) if variant == "segmented" else (4, 40, 64)
+    n = shape[2]
+    h = oracle.grid_spacing(n, bc)
+    cart = np.random.default_rng(order + 3).uniform(-1, 1, shape)
+    if dtype == "f32":
+        cart = cart.astype(np.float32).astype(np.float64)
+    ref = oracle.from_lines_view(oracle_solve_lines(oracle.lines_view(cart, "x"), order, bc, h), "x", shape)
+    for P in ((1, 2, 4) if variant == "segmented" else (1, 2, 8)):
+        try:
+            plan = tds.Plan(shape, "x", order, bc, P=P, h=h, dtype=TORCH[dtype], variant=variant)
+        except tds.TdsError:
+            continue   # segments need chunks of at least 64 rows
+        y = plan.solve(to_device_layout(cart, "x", dtype))
+        mx, rms = rel_errors(from_device_layout(y, "x", shape), ref)
+        assert mx <= TOL[dtype], (P, mx, rms)
+
+
+@pytest.mark.parametrize("width", [16, 8])
+def test_solve_split_groups(width):
+    P = WIDTH_P[width]["x"]
+    cart = np.random.default_rng(width).uniform(-1, 1, WSHAPE)
+    for bc in ("periodic", "closed"):
+        h = oracle.grid_spacing(WSHAPE[2], bc)
+        plan = tds.Plan(WSHAPE, "x", 1, bc, P=P, h=h, variant="resident", width=width)
+        y = plan.solve(to_device_layout(cart, "x", "f64"))
+        ref = oracle.from_lines_view(oracle_solve_lines(oracle.lines_view(cart, "x"), 1, bc, h), "x", WSHAPE)
+        mx, rms = rel_errors(from_device_layout(y, "x", WSHAPE), ref)
+        assert mx <= TOL["f64"], (bc, mx, rms)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("bc", ["periodic", "closed"])
 @pytest.mark.parametrize("width", [None, 16, 8])
