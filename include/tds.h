@@ -100,6 +100,25 @@ TDS_API tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_d
                            tds_bc bc, int P, double h, tds_dtype dtype, int sz,
                            tds_reduced mode);
 
+/*
+ * tds_plan_create_band -- a plan for the batched tridiagonal solve A x = d with a caller-given
+ * band (Algorithms 4-6 solve any such system; not restricted to the compact schemes), e.g. the
+ * implicit systems of ADI schemes.  Row j of every line is
+ *     a[j] x_{j-1} + b[j] x_j + c[j] x_{j+1} = d_j,   j = 0 .. n-1,
+ * with a[0] coupling to x_{n-1} and c[n-1] to x_0 on periodic lines (ignored on closed lines).
+ *   a, b, c : host arrays of n doubles each (n = the extent along dir), copied by the call.
+ *   other arguments as in tds_plan_create.
+ * The method sweeps without pivoting: the band should be diagonally dominant.  Chunks that share
+ * a coefficient class must carry the same band: every chunk on periodic lines, the interior
+ * chunks (1 .. P-2) on closed lines -- a uniform interior with its own first and last rows.
+ * Errors: TDS_ERR_ARG for a NULL array, a non-finite entry, chunks that differ where they must
+ * not, or a zero pivot; the shape rules of tds_plan_create.  Only tds_solve (and the plan
+ * queries and tuning calls) accept a band plan; the derivative calls return TDS_ERR_ARG.
+ */
+TDS_API tds_status tds_plan_create_band(tds_plan **out, int nx, int ny, int nz, tds_dir dir,
+                                const double *a, const double *b, const double *c, tds_bc bc,
+                                int P, tds_dtype dtype, int sz, tds_reduced mode);
+
 /* Choose the kernel pipeline of a plan (tuning and test hook; call before first use, not
  * concurrently with a call that uses the plan).  TDS_ERR_ARG if the plan cannot run the
  * requested variant (a resident group larger than one CTA's shared memory).  AUTO picks

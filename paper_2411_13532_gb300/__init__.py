@@ -44,11 +44,13 @@ class Plan:
     """One derivative operator: direction, order (1 or 2), boundary condition, P chunks.
 
     Creation runs the operator preprocessing (Algorithm 4) on the host and uploads it to the
-    current (or given) CUDA device.
+    current (or given) CUDA device.  With ``band=(a, b, c)`` (n values each) the plan is the
+    batched tridiagonal solve of that band instead (``tds_plan_create_band``; ``order`` and ``h``
+    are ignored and only ``solve`` is available).
     """
 
     def __init__(self, shape, direction, order, bc, P=1, h=None, dtype=torch.float64,
-                 mode="exact", variant="auto", width=None, device=None):
+                 mode="exact", variant="auto", width=None, device=None, band=None):
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
         self.direction, self.order, self.bc, self.P = direction, int(order), bc, int(P)
@@ -61,10 +63,20 @@ class Plan:
         L = _lib.lib()
         h_ = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            _lib.check(L.tds_plan_create(ctypes.byref(h_), nx, ny, nz, _lib.DIRS[direction],
-                                         self.order, _lib.BCS[bc], self.P, self.h,
-                                         _lib.DTYPES[_TORCH_DTYPES[dtype]], 32,
-                                         _lib.MODES[mode]), "tds_plan_create")
+            if band is None:
+                _lib.check(L.tds_plan_create(ctypes.byref(h_), nx, ny, nz, _lib.DIRS[direction],
+                                             self.order, _lib.BCS[bc], self.P, self.h,
+                                             _lib.DTYPES[_TORCH_DTYPES[dtype]], 32,
+                                             _lib.MODES[mode]), "tds_plan_create")
+            else:
+                arrs = [torch.as_tensor(v, dtype=torch.float64).contiguous().cpu() for v in band]
+                if any(a.numel() != self.n for a in arrs):
+                    raise ValueError("band arrays must have %d entries each" % self.n)
+                self.order = 0
+                _lib.check(L.tds_plan_create_band(ctypes.byref(h_), nx, ny, nz, _lib.DIRS[direction],
+                                                  *[ctypes.c_void_p(a.data_ptr()) for a in arrs],
+                                                  _lib.BCS[bc], self.P, _lib.DTYPES[_TORCH_DTYPES[dtype]],
+                                                  32, _lib.MODES[mode]), "tds_plan_create_band")
         self._handle = h_
         if width is not None:
             _lib.check(L.tds_plan_set_width(h_, int(width)), "tds_plan_set_width")

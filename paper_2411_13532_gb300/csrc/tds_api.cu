@@ -106,6 +106,7 @@ tds_status launch(const tds_plan *p, int which, const void *in, void *out, void 
 
 tds_status run(const tds_plan *p, int which, const void *in, void *out, void *ws, size_t ws_bytes,
                void *stream) {
+    if (p && p->band && which != 2) return TDS_ERR_ARG;   // a band plan has no stencil
     const tds_status s = check_call(p, in, out, ws, ws_bytes);
     if (s != TDS_OK) return s;
     return launch(p, which, in, out, ws, static_cast<cudaStream_t>(stream));
@@ -131,7 +132,7 @@ tds_plan slab_of(const tds_plan *p, int g0, int g1) {
 // queued after it starts once host_out is complete.
 tds_status run_host(const tds_plan *p, int which, const void *host_in, void *host_out, void *d_in,
                     void *d_out, void *ws, size_t ws_bytes, void *stream) {
-    if (!p || !host_out || !d_in || !d_out) return TDS_ERR_ARG;
+    if (!p || !host_out || !d_in || !d_out || p->band) return TDS_ERR_ARG;
     tds_status s = check_call(p, d_in, d_out, ws, ws_bytes);
     if (s != TDS_OK) return s;
     const size_t gbytes = (size_t)p->n * kSZ * elem_size(p->dtype);
@@ -167,46 +168,33 @@ tds_status run_host(const tds_plan *p, int which, const void *host_in, void *hos
     return TDS_OK;
 }
 
-} // namespace
-
-extern "C" {
-
-const char *tds_status_string(tds_status s) {
-    switch (s) {
-    case TDS_OK: return "ok";
-    case TDS_ERR_ARG: return "invalid argument";
-    case TDS_ERR_SHAPE: return "shape rule violated";
-    case TDS_ERR_ALIAS: return "input and output overlap";
-    case TDS_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
-    case TDS_ERR_CUDA: return "CUDA error";
-    case TDS_ERR_TIMEOUT: return "device-side wait timed out";
-    case TDS_ERR_NOMEM: return "out of memory";
-    }
-    return "unknown status";
-}
-
-tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_dir dir, int order,
-                           tds_bc bc, int P, double h, tds_dtype dtype, int sz, tds_reduced mode) {
-    if (!out) return TDS_ERR_ARG;
-    *out = nullptr;
-    if (dir < TDS_DIR_X || dir > TDS_DIR_Z || (order != 1 && order != 2) ||
-        (bc != TDS_BC_PERIODIC && bc != TDS_BC_CLOSED) || (dtype != TDS_F64 && dtype != TDS_F32) ||
-        (mode != TDS_REDUCED_EXACT && mode != TDS_REDUCED_PAPER_DROP) || sz != kSZ ||
-        !(h > 0.0) || !std::isfinite(h) || P < 1)
-        return TDS_ERR_ARG;
+// Shape rules shared by every plan (TDS_ERR_SHAPE).
+tds_status check_shape(int nx, int ny, int nz, tds_dir dir, int P) {
     if (nx < 1 || ny < 1 || nz < 1) return TDS_ERR_SHAPE;
     const int n = extent(nx, ny, nz, dir);
     const long long lines = (long long)nx * ny * nz / n;
     if (n < 8 || n % P != 0 || n / P < 4 || lines % kSZ != 0 || lines > (1ll << 31) - 1 ||
         (long long)n * lines > (1ll << 40))
         return TDS_ERR_SHAPE;
+    return TDS_OK;
+}
 
+tds_plan *new_plan(int nx, int ny, int nz, tds_dir dir, tds_bc bc, int P, tds_dtype dtype, tds_reduced mode) {
     tds_plan *p = new (std::nothrow) tds_plan;
-    if (!p) return TDS_ERR_NOMEM;
+    if (!p) return nullptr;
     std::memset(p, 0, sizeof(*p));
-    p->nx = nx; p->ny = ny; p->nz = nz; p->dir = dir; p->order = order; p->bc = bc; p->P = P;
-    p->h = h; p->dtype = dtype; p->mode = mode;
-    p->n = n; p->m = n / P; p->nlines = (int)lines;
+    const int n = extent(nx, ny, nz, dir);
+    p->nx = nx; p->ny = ny; p->nz = nz; p->dir = dir; p->bc = bc; p->P = P;
+    p->dtype = dtype; p->mode = mode;
+    p->n = n; p->m = n / P; p->nlines = (int)((long long)nx * ny * nz / n);
+    return p;
+}
+
+// The operators (host preprocessing and upload), the kernel configuration for this device, the
+// host entry points' streams and events, and the AUTO variant; destroys p on failure.
+tds_status finish_plan(tds_plan *p, tds_plan **out) {
+    const int n = p->n, P = p->P;
+    const tds_dtype dtype = p->dtype;
     tds_status s = build_plan(p);
     if (s != TDS_OK) { tds_plan_destroy(p); return s; }
 
@@ -261,6 +249,85 @@ tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_dir dir, 
     tds_plan_set_variant(p, TDS_VARIANT_AUTO);
     *out = p;
     return TDS_OK;
+}
+
+
+} // namespace
+
+extern "C" {
+
+const char *tds_status_string(tds_status s) {
+    switch (s) {
+    case TDS_OK: return "ok";
+    case TDS_ERR_ARG: return "invalid argument";
+    case TDS_ERR_SHAPE: return "shape rule violated";
+    case TDS_ERR_ALIAS: return "input and output overlap";
+    case TDS_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case TDS_ERR_CUDA: return "CUDA error";
+    case TDS_ERR_TIMEOUT: return "device-side wait timed out";
+    case TDS_ERR_NOMEM: return "out of memory";
+    }
+    return "unknown status";
+}
+
+tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_dir dir, int order,
+                           tds_bc bc, int P, double h, tds_dtype dtype, int sz, tds_reduced mode) {
+    if (!out) return TDS_ERR_ARG;
+    *out = nullptr;
+    if (dir < TDS_DIR_X || dir > TDS_DIR_Z || (order != 1 && order != 2) ||
+        (bc != TDS_BC_PERIODIC && bc != TDS_BC_CLOSED) || (dtype != TDS_F64 && dtype != TDS_F32) ||
+        (mode != TDS_REDUCED_EXACT && mode != TDS_REDUCED_PAPER_DROP) || sz != kSZ ||
+        !(h > 0.0) || !std::isfinite(h) || P < 1)
+        return TDS_ERR_ARG;
+    const tds_status sh = check_shape(nx, ny, nz, dir, P);
+    if (sh != TDS_OK) return sh;
+    tds_plan *p = new_plan(nx, ny, nz, dir, bc, P, dtype, mode);
+    if (!p) return TDS_ERR_NOMEM;
+    p->order = order;
+    p->h = h;
+    return finish_plan(p, out);
+}
+
+tds_status tds_plan_create_band(tds_plan **out, int nx, int ny, int nz, tds_dir dir, const double *a,
+                                const double *b, const double *c, tds_bc bc, int P, tds_dtype dtype,
+                                int sz, tds_reduced mode) {
+    if (!out) return TDS_ERR_ARG;
+    *out = nullptr;
+    if (!a || !b || !c || dir < TDS_DIR_X || dir > TDS_DIR_Z ||
+        (bc != TDS_BC_PERIODIC && bc != TDS_BC_CLOSED) || (dtype != TDS_F64 && dtype != TDS_F32) ||
+        (mode != TDS_REDUCED_EXACT && mode != TDS_REDUCED_PAPER_DROP) || sz != kSZ || P < 1)
+        return TDS_ERR_ARG;
+    const tds_status sh = check_shape(nx, ny, nz, dir, P);
+    if (sh != TDS_OK) return sh;
+    const int n = extent(nx, ny, nz, dir), m = n / P;
+    for (int j = 0; j < n; ++j)
+        if (!std::isfinite(a[j]) || !std::isfinite(b[j]) || !std::isfinite(c[j])) return TDS_ERR_ARG;
+    // chunks that share a class carry the same band: every chunk of a periodic line, the
+    // interior chunks (1 .. P-2) of a closed line
+    auto same = [&](int k, int r) {
+        for (int j = 0; j < m; ++j) {
+            const int x = k * m + j, y = r * m + j;
+            if (a[x] != a[y] || b[x] != b[y] || c[x] != c[y]) return false;
+        }
+        return true;
+    };
+    if (bc == TDS_BC_PERIODIC) {
+        for (int k = 1; k < P; ++k)
+            if (!same(k, 0)) return TDS_ERR_ARG;
+    } else {
+        for (int k = 2; k < P - 1; ++k)
+            if (!same(k, 1)) return TDS_ERR_ARG;
+    }
+    tds_plan *p = new_plan(nx, ny, nz, dir, bc, P, dtype, mode);
+    if (!p) return TDS_ERR_NOMEM;
+    p->band = static_cast<double *>(std::malloc(sizeof(double) * 3 * (size_t)n));
+    if (!p->band) { tds_plan_destroy(p); return TDS_ERR_NOMEM; }
+    std::memcpy(p->band, a, sizeof(double) * n);
+    std::memcpy(p->band + n, b, sizeof(double) * n);
+    std::memcpy(p->band + 2 * n, c, sizeof(double) * n);
+    p->order = 0;
+    p->h = 1.0;
+    return finish_plan(p, out);
 }
 
 tds_status tds_plan_set_variant(tds_plan *p, tds_variant v) {
@@ -349,7 +416,7 @@ tds_status tds_deriv_multi(int count, const tds_plan *const *plans, const int *a
     bool fused = true;
     for (int i = 0; i < count; ++i) {
         const tds_plan *p = plans[i];
-        if (!p || (adjoint[i] != 0 && adjoint[i] != 1)) return TDS_ERR_ARG;
+        if (!p || p->band || (adjoint[i] != 0 && adjoint[i] != 1)) return TDS_ERR_ARG;
         which[i] = adjoint[i];
         // every operator maps the same field shape in the same direction layout
         if (p->nx != p0->nx || p->ny != p0->ny || p->nz != p0->nz || p->dir != p0->dir ||
@@ -399,6 +466,7 @@ tds_status tds_reorder(const void *in, void *out, int nx, int ny, int nz, tds_la
 
 void tds_plan_destroy(tds_plan *p) {
     if (!p) return;
+    std::free(p->band);
     for (cudaEvent_t e : p->ev)
         if (e) cudaEventDestroy(e);
     if (p->copy_in) cudaStreamDestroy(p->copy_in);

@@ -113,6 +113,7 @@ struct tds_plan {
     // input landed, slab computed), created with the plan
     cudaStream_t copy_in, copy_out;
     cudaEvent_t ev[2 + 2 * tds::kHostSlabs];
+    double *band;          // band plan: the caller's band of A (a, b, c; 3 x n), else NULL
     void *dmem;            // one device allocation holding every array of both operators
     void *hmem;            // host copies (reduced coefficients)
 };

@@ -47,7 +47,7 @@ bool overlap(const void *a, const void *b, size_t bytes) {
 
 extern "C" TDS_API tds_status tds_deriv_noalloc(const tds_plan *plan, const void *in, void *out,
                                                 void *stream) {
-    if (!plan || !in || !out) return TDS_ERR_ARG;
+    if (!plan || !in || !out || plan->band) return TDS_ERR_ARG;   // a band plan has no stencil
     if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
         return TDS_ERR_ARG;
     const size_t bytes = (size_t)plan->n * plan->nlines * (plan->dtype == TDS_F64 ? 8 : 4);

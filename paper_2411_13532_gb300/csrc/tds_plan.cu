@@ -77,6 +77,16 @@ void scheme_line(int n, int order, bool periodic, double h, LineOperator &L) {
     }
 }
 
+// A caller-given band (a, b, c of n rows each): no stencil (the solve alone).  On closed lines
+// a[0] and c[n-1] couple to nothing and are dropped.
+void band_line(int n, bool periodic, const double *band, LineOperator &L) {
+    L.a.assign(band, band + n);
+    L.b.assign(band + n, band + 2 * n);
+    L.c.assign(band + 2 * n, band + 3 * n);
+    if (!periodic) { L.a[0] = 0.0; L.c[n - 1] = 0.0; }
+    L.taps.assign((size_t)n * kTaps, 0.0);
+}
+
 // A^T and B^T of a line operator: (A^T)_{J,J-1} = c[J-1], (A^T)_{J,J+1} = a[J+1], and the tap
 // of B^T at offset o in row J is B's tap at offset -o in row J+o.
 void transpose_line(int n, bool periodic, const LineOperator &L, LineOperator &T) {
@@ -316,7 +326,8 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
 tds_status build_plan(tds_plan *p) {
     const bool periodic = (p->bc == TDS_BC_PERIODIC);
     LineOperator L, LT;
-    scheme_line(p->n, p->order, periodic, p->h, L);
+    if (p->band) band_line(p->n, periodic, p->band, L);
+    else scheme_line(p->n, p->order, periodic, p->h, L);
     transpose_line(p->n, periodic, L, LT);
 
     // operators: [0] A^{-1} B, [1] B^T A^{-T} and [2] A^{-1} on the plan's P chunks; [3] A^{-1} B

@@ -179,6 +179,66 @@ def test_solve_every_point(dtype, variant, order, bc):
         assert mx <= TOL[dtype], (P, mx, rms)
 
 
+def random_band(n, P, periodic, seed):
+    """A diagonally dominant band with a uniform interior and its own first / last rows (the
+    structure band plans accept)."""
+    rng = np.random.default_rng(seed)
+    ai, ci = rng.uniform(-0.45, 0.45, 2)
+    bi = 1.0 + rng.uniform(0.0, 0.5)
+    a = np.full(n, ai); b = np.full(n, bi); c = np.full(n, ci)
+    if not periodic:   # distinct closure rows in the first and last chunk
+        k = min(3, n // P)
+        a[:k] = rng.uniform(-0.4, 0.4, k); b[:k] = rng.uniform(1.0, 2.0, k); c[:k] = rng.uniform(-0.4, 0.4, k)
+        a[-k:] = rng.uniform(-0.4, 0.4, k); b[-k:] = rng.uniform(1.0, 2.0, k); c[-k:] = rng.uniform(-0.4, 0.4, k)
+    return a, b, c
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+@pytest.mark.parametrize("variant", ["resident", "streaming"])
+def test_band_plan_solve(dtype, bc, variant):
+    """A caller-given band: every point of tds_solve against the oracle's (cyclic) Thomas solve of
+    the same band, for several chunk counts and directions."""
+    shape = (8, 40, 64)
+    cart = np.random.default_rng(31).uniform(-1, 1, shape)
+    if dtype == "f32":
+        cart = cart.astype(np.float32).astype(np.float64)
+    for direction, Ps in (("x", (1, 2, 8)), ("y", (1, 5)), ("z", (1, 2))):
+        n = {"x": shape[2], "y": shape[1], "z": shape[0]}[direction]
+        for P in Ps:
+            a, b, c = random_band(n, P, bc == "periodic", seed=n + P)
+            plan = tds.Plan(shape, direction, 0, bc, P=P, dtype=TORCH[dtype], variant=variant, band=(a, b, c))
+            y = plan.solve(to_device_layout(cart, direction, dtype))
+            lines = oracle.lines_view(cart, direction)
+            ref = np.stack([oracle.tridiag_solve(a, b, c, d, bc == "periodic") for d in lines])
+            mx, rms = rel_errors(from_device_layout(y, direction, shape), oracle.from_lines_view(ref, direction, shape))
+            assert mx <= TOL[dtype], (direction, P, mx, rms)
+
+
+def test_band_plan_rules():
+    shape = (8, 32, 64)
+    a, b, c = random_band(64, 4, False, seed=1)
+    # a closed line's interior chunks (1 .. P-2) must agree
+    bad = b.copy(); bad[20] += 0.1
+    with pytest.raises(tds.TdsError):
+        tds.Plan(shape, "x", 0, "closed", P=4, band=(a, bad, c))
+    # every chunk of a periodic line must agree
+    with pytest.raises(tds.TdsError):
+        tds.Plan(shape, "x", 0, "periodic", P=4, band=(a, bad, c))
+    # a zero pivot
+    z = b.copy(); z[0] = 0.0
+    with pytest.raises(tds.TdsError):
+        tds.Plan(shape, "x", 0, "closed", P=4, band=(np.zeros(64), z, c))
+    # a band plan has no stencil: the derivative calls are refused
+    plan = tds.Plan(shape, "x", 0, "closed", P=4, band=(a, b, c))
+    x = torch.zeros(plan.numel, dtype=torch.float64, device="cuda")
+    for fn in (plan.deriv, plan.adjoint):
+        with pytest.raises(tds.TdsError):
+            fn(x)
+    with pytest.raises(tds.TdsError):
+        tds.deriv_multi([(plan, False)], x)
+
+
 @pytest.mark.parametrize("width", [16, 8])
 def test_solve_split_groups(width):
     P = WIDTH_P[width]["x"]
