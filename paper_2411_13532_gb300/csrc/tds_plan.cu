@@ -1,11 +1,13 @@
 // tds_plan.cu -- host-side operator preprocessing (Algorithm 4, Sec. 4.2), in FP64.
 //
 // For one derivative operator the planner produces
-//   * the tridiagonal band of A and the stencil taps of B (Eq. cfds and its closures),
-//   * per chunk class the Algorithm 4 arrays f, r, w, s^a, s^c and the row-0 normaliser,
+//   * the tridiagonal band of A and the stencil taps of B (Eq. cfds and its closures), or a
+//     caller-given band (band plans: the solve alone),
+//   * per chunk class the Algorithm 4 arrays f, r, w, s^a, s^c and the row-0 normaliser, the
+//     folded forward records and the rows whose records are constant,
 //   * the reduced chunk-end system and its factorisation (cyclic: Sherman-Morrison),
-// for A^{-1} B and for its transpose B^T A^{-T}.  Everything is uploaded once to the device;
-// the kernels only read it.
+// for A^{-1} B, its transpose B^T A^{-T} and A^{-1}, on the plan's chunks and (SEGMENTED) on the
+// segment partition.  Everything is uploaded once to the device; the kernels only read it.
 #include <cmath>
 #include <cstdlib>
 #include <cstring>

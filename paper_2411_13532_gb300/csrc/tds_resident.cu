@@ -1,17 +1,25 @@
-// tds_resident.cu -- the resident DistD2 kernels (Sec. 4.2): one CTA holds a whole group of 32
-// lines (all P chunks) in shared memory, so the field is read once and written once.
+// tds_resident.cu -- the resident DistD2 kernels (Sec. 4.2): one CTA holds W lines of a group of
+// 32 (W = 32, 16 or 8; all P chunks) in shared memory, so the field is read once and written
+// once.
 //
-// Per group: TMA bulk copies bring the n x 32 tile into shared memory (one mbarrier per chunk,
-// bounded waits); chunk k is swept by 32/V threads, each carrying V adjacent lines; then
+// Per CTA: TMA copies bring the n x W tile into shared memory (one mbarrier per chunk, bounded
+// waits; W = 32 one bulk copy per chunk, W < 32 2-D tensor boxes); chunk k is swept by W/V
+// threads, each carrying V adjacent lines; then
 //   forward  : stencil right-hand side fused into the modified-Thomas forward elimination
 //              (Algorithm 5), in place, accumulating the back-swept row 1 as S = sum pi_j d_j
-//              so that row 0 is decoupled without a separate backward pass;
+//              so that row 0 is decoupled without a separate backward pass; rows whose folded
+//              coefficients have converged take them from registers;
 //   reduced  : the chunk-end system in FP64 (communication phase; decoupled 2x2 boundary
 //              systems when the couplings they ignore are below 2^-64, else the full system);
 //   back-substitution: u_{m-1} = L, u_j = d_j - s^a_j F - s^c_j u_{j+1}, u_0 = F -- the
 //              backward pass and Algorithm 6 in one reverse sweep;
-//   adjoint  : the same on A^T with the identity right-hand side, then x = B^T y in place;
-//   output   : FP32 tiles leave with one TMA bulk store; FP64 tiles with per-thread stores.
+//   modes    : 0 the stencil right-hand side (derivatives; adjoints on periodic lines, whose
+//              operator has the forward form); 1 the closed-line adjoint, the same on A^T with
+//              the identity right-hand side, then x = B^T y in place; 2 the solve alone
+//              (identity right-hand side, the back-substitution written as the output);
+//   output   : FP32 tiles leave with TMA stores; FP64 tiles with per-thread stores.
+// Also here: the persistent pipelined variant, the fused pass over several operators of one
+// input, and the SEGMENTED kernels for lines no CTA can hold.
 //
 // The sweep is written once over storage/arithmetic traits (FP32, FP64).
 #include <cstring>
