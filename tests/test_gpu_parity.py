@@ -156,7 +156,7 @@ def oracle_solve_lines(lines, order, bc, h):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("variant", ["resident", "streaming", "segmented"])
+@pytest.mark.parametrize("variant", ["resident", "pipelined", "streaming", "segmented"])
 @pytest.mark.parametrize("order", [1, 2])
 @pytest.mark.parametrize("bc", ["periodic", "closed"])
 def test_solve_every_point(dtype, variant, order, bc):
