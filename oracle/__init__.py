@@ -8,5 +8,6 @@ passage of the paper it follows.
 from .oracle import (  # noqa: F401
     build, bands, rhs_lines, deriv_lines, deriv_adjoint_lines, tridiag_solve,
     lines_view, from_lines_view, to_layout, from_layout, deriv, deriv_adjoint,
-    layout_lines_count, grid_spacing,
+    layout_lines_count, grid_spacing, transport_term_lines, transport_term,
+    transport_rhs,
 )

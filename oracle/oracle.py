@@ -176,3 +176,34 @@ def deriv_adjoint(cart, direction, order, bc, h=None):
     h = grid_spacing(n, bc) if h is None else h
     out = deriv_adjoint_lines(lines_view(cart, direction), order, bc, h)
     return np.ascontiguousarray(from_lines_view(out, direction, cart.shape))
+
+
+def transport_term_lines(ui, uj, nu, bc, h):
+    """One term group of the skew-symmetric momentum transport equation (Sec. 5, Eq. mom-comps)
+    on lines (L, n) along the derivative direction j:
+        -1/2 (u_j du_i/dx_j + d(u_j u_i)/dx_j) + nu d2u_i/dx_j2,
+    each derivative the compact scheme of ``deriv_lines`` (first: Eq. cfds; second: its order-2
+    counterpart), the products pointwise, all in FP64."""
+    ui = np.ascontiguousarray(ui, dtype=np.float64)
+    uj = np.ascontiguousarray(uj, dtype=np.float64)
+    conv = uj * deriv_lines(ui, 1, bc, h)
+    cons = deriv_lines(uj * ui, 1, bc, h)
+    visc = deriv_lines(ui, 2, bc, h)
+    return -0.5 * (conv + cons) + nu * visc
+
+
+def transport_term(ui, uj, direction, nu, bc, h=None):
+    """``transport_term_lines`` along one direction of Cartesian fields (Cartesian in and out)."""
+    ui = np.ascontiguousarray(ui, dtype=np.float64)
+    uj = np.ascontiguousarray(uj, dtype=np.float64)
+    n = {"x": ui.shape[2], "y": ui.shape[1], "z": ui.shape[0]}[direction]
+    h = grid_spacing(n, bc) if h is None else h
+    out = transport_term_lines(lines_view(ui, direction), lines_view(uj, direction), nu, bc, h)
+    return np.ascontiguousarray(from_lines_view(out, direction, ui.shape))
+
+
+def transport_rhs(u, nu, bc, h=None):
+    """Eq. mom-comps: the right-hand sides of the three momentum components, u = (u_x, u_y, u_z)
+    Cartesian; component i sums the term groups of the three directions j."""
+    dirs = ("x", "y", "z")
+    return [sum(transport_term(u[i], u[j], dirs[j], nu, bc, h) for j in range(3)) for i in range(3)]

@@ -309,3 +309,82 @@ def test_layout_round_trip_and_derivative_consistency(oracle_mod):
     dy = oracle_mod.deriv(cart, "y", 1, "periodic")
     dx_t = oracle_mod.deriv(np.ascontiguousarray(cart.transpose(0, 2, 1)), "x", 1, "periodic")
     assert np.array_equal(dy, dx_t.transpose(0, 2, 1))
+
+
+# --------------------------------------------------- transport equation (Sec. 5, Eq. mom-comps)
+
+def _modes_eval(modes, grids):
+    X, Y, Z = grids
+    out = np.zeros(np.broadcast(X, Y, Z).shape)
+    for amp, (kx, ky, kz), ph in modes:
+        out = out + amp * np.cos(kx * X + ky * Y + kz * Z + ph)
+    return out
+
+
+def _modes_product(ma, mb):
+    """cos(a) cos(b) = (cos(a + b) + cos(a - b)) / 2, term by term."""
+    out = []
+    for a1, k1, p1 in ma:
+        for a2, k2, p2 in mb:
+            out.append((0.5 * a1 * a2, tuple(u + v for u, v in zip(k1, k2)), p1 + p2))
+            out.append((0.5 * a1 * a2, tuple(u - v for u, v in zip(k1, k2)), p1 - p2))
+    return out
+
+
+def _modes_deriv(modes, axis, order, hs):
+    """The periodic compact derivative of a sum of grid modes, from the Fourier symbol alone:
+    D1 cos(t) = -K1 sin(t) = K1 cos(t + pi/2), D2 cos(t) = -K2 cos(t) (any integer wavenumber
+    is an eigenvector of the circulant scheme)."""
+    out = []
+    for amp, k, ph in modes:
+        kk = mod_wavenumber(order, k[axis], hs[axis])
+        out.append((amp * kk, k, ph + np.pi / 2) if order == 1 else (-amp * kk, k, ph))
+    return out
+
+
+def test_transport_rhs_closed_form_fourier(oracle_mod):
+    """Every term of Eq. mom-comps on fields made of a constant plus one 3D Fourier mode each:
+    the expected values use only the closed-form symbols (products expanded into modes)."""
+    nz, ny, nx = 12, 16, 20
+    hs = (2 * np.pi / nx, 2 * np.pi / ny, 2 * np.pi / nz)
+    grids = (np.arange(nx)[None, None, :] * hs[0], np.arange(ny)[None, :, None] * hs[1],
+             np.arange(nz)[:, None, None] * hs[2])
+    spec = [(0.7, 1.3, (2, 1, 3), 0.4), (-0.4, 0.9, (1, 3, 2), 1.1), (0.25, 1.1, (3, 2, 1), -0.6)]
+    modes = [[(c, (0, 0, 0), 0.0), (a, k, p)] for c, a, k, p in spec]
+    u = [_modes_eval(m, grids) for m in modes]
+    nu = 0.03
+    got = oracle_mod.transport_rhs(u, nu, "periodic")
+    for i in range(3):
+        ref = np.zeros((nz, ny, nx))
+        scale = 0.0
+        for j in range(3):
+            conv = u[j] * _modes_eval(_modes_deriv(modes[i], j, 1, hs), grids)
+            cons = _modes_eval(_modes_deriv(_modes_product(modes[j], modes[i]), j, 1, hs), grids)
+            visc = _modes_eval(_modes_deriv(modes[i], j, 2, hs), grids)
+            ref += -0.5 * (conv + cons) + nu * visc
+            scale = max(scale, np.max(np.abs(conv)), np.max(np.abs(cons)), nu * np.max(np.abs(visc)))
+            term = oracle_mod.transport_term(u[i], u[j], "xyz"[j], nu, "periodic")
+            np.testing.assert_allclose(term, -0.5 * (conv + cons) + nu * visc, rtol=0, atol=1e-12 * scale)
+        np.testing.assert_allclose(got[i], ref, rtol=0, atol=1e-12 * scale)
+
+
+@pytest.mark.parametrize("j", ["x", "y", "z"])
+def test_transport_skew_symmetric_energy_identity(oracle_mod, j):
+    """On periodic lines D1 is skew (A symmetric, B antisymmetric, both circulant), so the
+    convective part of each term group conserves energy for ANY fields:
+    <u_i, u_j D1 u_i> + <u_i, D1 (u_j u_i)> = <u_i u_j, D1 u_i> - <D1 u_i, u_j u_i> = 0,
+    and the viscous part is dissipative (<u_i, D2 u_i> < 0 for a non-constant u_i)."""
+    rng = np.random.default_rng(11)
+    shape = (10, 14, 18)
+    ui, uj = rng.uniform(-1, 1, shape), rng.uniform(-1, 1, shape)
+    t0 = oracle_mod.transport_term(ui, uj, j, 0.0, "periodic")
+    conv = uj * oracle_mod.deriv(ui, j, 1, "periodic")
+    bound = 1e-13 * np.sum(np.abs(ui) * (np.abs(conv) + np.abs(t0))) + 1e-300
+    assert abs(np.sum(ui * t0)) <= bound
+    # the same for i = j
+    tj = oracle_mod.transport_term(uj, uj, j, 0.0, "periodic")
+    assert abs(np.sum(uj * tj)) <= 1e-13 * np.sum(np.abs(uj) * (np.abs(uj) * 10 + np.abs(tj)))
+    # the identity is not trivial: the convective half alone carries energy
+    assert abs(np.sum(ui * conv)) > 1e3 * bound
+    t1 = oracle_mod.transport_term(ui, uj, j, 0.5, "periodic")
+    assert np.sum(ui * t1) < -1e3 * bound
