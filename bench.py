@@ -72,6 +72,10 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="time every workload configuration one operator at a time (one JSON line per "
                          "case) instead of the benchmark step")
+    ap.add_argument("--transport", action="store_true",
+                    help="time the momentum-transport right-hand side (Sec. 5) instead of the "
+                         "derivative step: one JSON line")
+    ap.add_argument("--nu", type=float, default=1e-3)
     return ap.parse_args()
 
 
@@ -481,6 +485,176 @@ def run_sweep(args):
         raise RuntimeError("device status after the sweep")
 
 
+# ------------------------------------------------------------------ transport right-hand side
+
+# Field transfers (reads + writes of one N^3 field) per evaluation, Table transport's counting:
+# the paper's GPU implementation and this one (x: the i = j term reads 1 field, the two i != j
+# terms 2, each writes 1; y and z: 3 reorders (1 + 1), the same 8 for the terms, 3
+# accumulations fused with the reorder back to x (read the term, read and write the output).
+PAPER_TRANSFERS = {"abstract_ij": 96, "abstract_ii": 45, "reorder": 12, "accumulate": 18}
+OUR_TRANSFERS = {"term": 3 * 8, "reorder": 6 * 2, "reorder_add": 6 * 3}
+
+
+def transport_fp64_ops_per_point(m):
+    """FP64-pipe operations per point of one fused term kernel: the three sweeps (D1 of u_i,
+    D1 of the product, D2 of u_i), the product (1 multiply) and the epilogues (2 multiplies,
+    2 FMAs)."""
+    return 2 * fp64_ops_per_point("d1", m) + fp64_ops_per_point("d2", m) + 1 + 4
+
+
+def run_transport(args):
+    """The transport right-hand side (three components, nine term groups, six reorders, six
+    accumulations) on an S^3 periodic box, FP64 and FP32: per-launch CUDA events on the
+    launching stream, inputs larger than L2."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_13532_gb300 as tds
+    from paper_2411_13532_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    S, P = args.size, args.P
+    shape = (S, S, S)
+    npts = S ** 3
+    stream = torch.cuda.current_stream(dev)
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    res = {}
+    launches = 0
+    clocks = None
+    e2e = None
+    for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        es = 8 if name == "f64" else 4
+        rhs = tds.TransportRHS(shape, P=P, dtype=dt)
+        u = []
+        for c in range(3):
+            f, _ = inputs.fourier_field(shape, seed=31 + c, kmax=20, noise=1e-3, device=dev)
+            u.append(tds.reorder(f.to(dt).reshape(-1), shape, "cart", "x"))
+            del f
+        out = [torch.empty_like(u[0]) for _ in range(3)]
+        plan = rhs.launch_list(u, args.nu, out)
+        for _ in range(max(args.warmup, 3)):
+            for _, fn in plan:
+                fn()
+        torch.cuda.synchronize()
+        per = {}
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        evs = []
+        with ClockSampler(0) as clk:
+            t0.record(stream)
+            for _ in range(args.steps):
+                for key, fn in plan:
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    fn()
+                    b.record(stream)
+                    evs.append((key, a, b))
+                    launches += 1
+            t1.record(stream)
+            torch.cuda.synchronize()
+        if name == "f64" or clocks is None:
+            clocks = clk.summary()
+        ms = t0.elapsed_time(t1) / args.steps
+        for key, a, b in evs:
+            per.setdefault(key, []).append(a.elapsed_time(b))
+        field = es * npts
+        kern = {}
+        for key, v in sorted(per.items()):
+            avg = sum(v) / len(v)
+            kind = key.split("/")[0]
+            transfers = {"term": 8.0 / 3.0, "reorder": 2.0, "reorder_add": 3.0}[kind]
+            gbs = transfers * field / (avg * 1e-3) / 1e9
+            kern[key] = {"ms": round(avg, 4), "launches_per_eval": len(v) // args.steps,
+                         "alg_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+            if kind == "term":
+                ops = transport_fp64_ops_per_point(S // P) * npts
+                kern[key]["fp64_Gop_s"] = round(ops / (avg * 1e-3) / 1e9, 1)
+        ours = sum(OUR_TRANSFERS.values())
+        paper = sum(PAPER_TRANSFERS.values())
+        term_ms = sum(sum(v) for k, v in per.items() if k.startswith("term")) / args.steps
+        reo_ms = sum(sum(v) for k, v in per.items() if k.startswith("reorder/")) / args.steps
+        acc_ms = sum(sum(v) for k, v in per.items() if k.startswith("reorder_add")) / args.steps
+        res[name] = {
+            "ms_per_eval": round(ms, 3), "gpoints_s": round(npts / (ms * 1e-3) / 1e9, 3),
+            "field_transfers": ours, "paper_field_transfers": paper,
+            "alg_GB_s": round(ours * field / (ms * 1e-3) / 1e9, 1),
+            "hbm_frac": round(ours * field / (ms * 1e-3) / 1e9 / hbm, 4),
+            "paper_count_GB_s": round(paper * field / (ms * 1e-3) / 1e9, 1),
+            "time_share": {"terms": round(term_ms / ms, 4), "reorders": round(reo_ms / ms, 4),
+                           "reorder_add": round(acc_ms / ms, 4)},
+            "reorder_traffic_share": round(OUR_TRANSFERS["reorder"] / ours, 4),
+            "kernels": kern}
+        if name == "f64" and args.e2e_steps > 0:
+            # end to end: the three components from pinned host memory, the three results back
+            hu = [torch.empty(npts, dtype=dt, pin_memory=True) for _ in range(3)]
+            ho = [torch.empty(npts, dtype=dt, pin_memory=True) for _ in range(3)]
+            for h, d in zip(hu, u):
+                h.copy_(d)
+
+            def e2e_step():
+                for h, d in zip(hu, u):
+                    d.copy_(h, non_blocking=True)
+                rhs(u, args.nu, out)
+                for h, d in zip(ho, out):
+                    h.copy_(d, non_blocking=True)
+            e2e_step()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(args.e2e_steps):
+                e2e_step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ems = a.elapsed_time(b) / args.e2e_steps
+            e2e = {"value": round(npts / (ems * 1e-3) / 1e9, 3), "unit": "Gpoints/s",
+                   "h2d_bytes_per_step": 3 * field, "d2h_bytes_per_step": 3 * field,
+                   "ms_per_step": round(ems, 3), "dtype": "f64"}
+            del hu, ho
+        del rhs, u, out, plan
+        torch.cuda.empty_cache()
+    if tds.device_status() != 0:
+        raise RuntimeError("device status after the transport benchmark")
+    # roofline of the dominant kernel (the FP64 term group): FP64 pipe bound
+    t64 = res["f64"]["kernels"]["term/x"]
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    peak = 2 * 152 * sm_mhz * 1e6 / 1e9
+    roofline = {"kernel": "f64/term/x (k_resident_transport)", "bound": "alu",
+                "achieved": t64["fp64_Gop_s"], "peak": round(peak, 1), "unit": "Gop/s (FP64 pipe)",
+                "frac": round(t64["fp64_Gop_s"] / peak, 4),
+                "peak_source": "derived: 2 FP64 ops/clk/SM x 152 SMs x median SM clock",
+                "traffic": None,
+                "f32_term_hbm_frac": res["f32"]["kernels"]["term/x"]["hbm_frac"]}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import numpy as np
+        import oracle
+        oracle.build()
+        n = 64
+        rng = np.random.default_rng(0)
+        u = [rng.uniform(-1, 1, (n, n, n)) for _ in range(3)]
+        t = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t < 10.0:
+            oracle.transport_rhs(u, args.nu, "periodic")
+            reps += 1
+        dtc = time.perf_counter() - t
+        cpu = {"value": round(reps * n ** 3 / dtc / 1e9, 5), "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
+               "sample": "%d evaluations of the FP64 oracle on a %d^3 periodic box, %.1f s" % (reps, n, dtc)}
+    line = {"metric": "momentum-transport RHS evaluations (grid points per second)",
+            "value": res["f64"]["gpoints_s"], "unit": "Gpoints/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": res["f64"]["ms_per_eval"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (f32 in breakdown)", "data": "synthetic",
+            "config": {"workload": "skew-symmetric momentum transport RHS, %d^3 periodic, P=%d, nu=%g"
+                                   % (S, P, args.nu),
+                       "l2": "inputs larger than L2"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "breakdown": res, "cpu_baseline": cpu}
+    print(json.dumps(line))
+
+
 # ------------------------------------------------------------------------ CPU oracle arm
 
 def oracle_sample_step(S, lines_per_dir, rng_seed=0):
@@ -563,6 +737,9 @@ def main():
         return
     if args.sweep:
         run_sweep(args)
+        return
+    if args.transport:
+        run_transport(args)
         return
     if world > 1:
         import torch

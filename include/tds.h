@@ -74,8 +74,8 @@ typedef enum {
 typedef struct tds_plan tds_plan;
 
 /*
- * tds_plan_create -- operator preprocessing (Algorithm 4, Sec. 4.2), in FP64 on the host,
- * "carried out only once for each distinct operation".
+ * tds_plan_create -- operator preprocessing (Algorithm 4, Sec. 4.2), in FP64 on the host; it
+ * depends only on the operator, so a plan is built once and reused for every field.
  *   out   : receives the new plan (set to NULL on error).
  *   nx, ny, nz : Cartesian grid; the line length n is the extent along dir, the number of
  *           lines N is the product of the two others.
@@ -205,6 +205,29 @@ TDS_API tds_status tds_deriv_multi(int count, const tds_plan *const *plans, cons
                            const void *in, void *const *outs, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * tds_transport -- one term group of the skew-symmetric momentum transport equation (Sec. 5,
+ * Eq. mom-comps) along the plans' direction j, with the three operators sharing one read of
+ * the fields (the fused "abstract kernel" of Sec. 5):
+ *     out = -1/2 (u_j * D1 u_i + D1 (u_j u_i)) + nu * D2 u_i
+ * (products pointwise; D1, D2 the first and second compact derivatives of d1, d2).
+ *   d1, d2 : order-1 and order-2 plans (no band) over the same field shape, direction, dtype,
+ *            chunk count P and CTA width, each able to hold its lines in a CTA (a nonzero
+ *            tds_plan_width, whatever the plan's variant); TDS_ERR_ARG otherwise.  Their
+ *            boundary conditions may differ.
+ *   ui, uj : device arrays in the plans' direction layout, 16-byte aligned; the same array
+ *            when i = j.
+ *   nu     : the kinematic viscosity.
+ *   out    : device array in that layout, overwritten; must not overlap ui or uj
+ *            (TDS_ERR_ALIAS).
+ * One kernel, no workspace: HBM sees ui and uj read once and out written once (the result of
+ * each operator is combined in L2).  The three sweeps round like tds_deriv's (FP32 plans:
+ * FP32 storage and sweeps, FP64 chunk-end system); the products and the combination are taken
+ * in the plan's arithmetic type.
+ */
+TDS_API tds_status tds_transport(const tds_plan *d1, const tds_plan *d2, const void *ui, const void *uj,
+                                 double nu, void *out, void *stream);
+
+/*
  * tds_deriv_host -- tds_deriv with the input and the result in HOST memory (not in the paper:
  * the end-to-end form of the call).
  *   host_in  : N*n elements in the plan's direction layout, copied to d_in; NULL when the
@@ -230,8 +253,8 @@ TDS_API tds_status tds_deriv_adjoint_host(const tds_plan *plan, const void *host
 
 /*
  * tds_reorder -- permute a field between the Cartesian layout and the x, y, z direction
- * layouts (Sec. 4.1: "the data layout is specific to a direction in the domain, and it
- * requires reordering"); a pure permutation, bit-exact.
+ * layouts (Sec. 4.1: each derivative direction has its own interleaved layout, so a change of
+ * direction moves the data); a pure permutation, bit-exact.
  *   in, out : device arrays of nx*ny*nz elements, non-overlapping (TDS_ERR_ALIAS), 16-byte
  *             aligned.
  * Shape rules (TDS_ERR_SHAPE): nx % 32 == 0 and ny % 32 == 0 (so that every layout's SZ-row
@@ -239,6 +262,16 @@ TDS_API tds_status tds_deriv_adjoint_host(const tds_plan *plan, const void *host
  */
 TDS_API tds_status tds_reorder(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
                        tds_layout to, tds_dtype dtype, int sz, void *stream);
+
+/*
+ * tds_reorder_add -- out += the reorder of in (the accumulation of Table transport, fused with
+ * the reorder: the transport right-hand side adds each y and z result into the x-layout field
+ * in one pass).  Same arguments and rules as tds_reorder; from == to adds in place of a copy.
+ * Each element of out receives exactly one addition, so the result is bit-exact against
+ * reorder-then-add.
+ */
+TDS_API tds_status tds_reorder_add(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
+                                   tds_layout to, tds_dtype dtype, int sz, void *stream);
 
 /* Free a plan and its device arrays (NULL is a no-op).  Not stream-ordered: the caller makes
  * sure no work that uses the plan is still running. */

@@ -15,8 +15,8 @@ import torch
 from . import _lib
 from ._lib import TdsError  # noqa: F401
 
-__all__ = ["Plan", "deriv", "deriv_adjoint", "deriv_multi", "reorder", "CompactDeriv", "compact_deriv",
-           "device_status", "grid_spacing", "TdsError"]
+__all__ = ["Plan", "deriv", "deriv_adjoint", "deriv_multi", "reorder", "reorder_add", "transport_term",
+           "TransportRHS", "CompactDeriv", "compact_deriv", "device_status", "grid_spacing", "TdsError"]
 
 _TORCH_DTYPES = {torch.float64: "f64", torch.float32: "f32"}
 
@@ -263,6 +263,101 @@ def reorder(x, shape, src, dst, out=None, stream=None):
             _lib.LAYOUTS[src], _lib.LAYOUTS[dst], _lib.DTYPES[_TORCH_DTYPES[x.dtype]], 32,
             _stream_ptr(stream, x.device)), "tds_reorder")
     return out
+
+
+def reorder_add(x, shape, src, dst, out, stream=None):
+    """out += x permuted from layout ``src`` to ``dst`` (one pass; bit-exact against a reorder
+    followed by an add)."""
+    nz, ny, nx = (int(v) for v in shape)
+    if x.dtype not in _TORCH_DTYPES:
+        raise ValueError("reorder_add supports float64 and float32")
+    _check_tensor(x, x.dtype, nx * ny * nz, "input")
+    _check_tensor(out, x.dtype, nx * ny * nz, "out")
+    with torch.cuda.device(x.device):
+        _lib.check(_lib.lib().tds_reorder_add(
+            ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), nx, ny, nz,
+            _lib.LAYOUTS[src], _lib.LAYOUTS[dst], _lib.DTYPES[_TORCH_DTYPES[x.dtype]], 32,
+            _stream_ptr(stream, x.device)), "tds_reorder_add")
+    return out
+
+
+def transport_term(d1, d2, ui, uj, nu, out=None, stream=None):
+    """out = -1/2 (uj * D1 ui + D1 (uj ui)) + nu * D2 ui along the plans' direction, one fused
+    kernel (``tds_transport``); d1 / d2 are order-1 / order-2 plans of one geometry, the fields
+    are in their direction layout (``ui`` may be ``uj``)."""
+    _check_tensor(ui, d1.dtype, d1.numel, "ui")
+    _check_tensor(uj, d1.dtype, d1.numel, "uj")
+    if out is None:
+        out = torch.empty_like(ui)
+    _check_tensor(out, d1.dtype, d1.numel, "out")
+    with torch.cuda.device(d1.device):
+        _lib.check(_lib.lib().tds_transport(d1._handle, d2._handle, ctypes.c_void_p(ui.data_ptr()),
+                                            ctypes.c_void_p(uj.data_ptr()), float(nu),
+                                            ctypes.c_void_p(out.data_ptr()),
+                                            _stream_ptr(stream, d1.device)), "tds_transport")
+    return out
+
+
+class TransportRHS:
+    """Right-hand side of the skew-symmetric momentum transport equation (Sec. 5, Eq. mom-comps)
+    on a periodic (or closed) box, every field in the x-direction layout:
+
+        rhs_i = sum_j [ -1/2 (u_j du_i/dx_j + d(u_j u_i)/dx_j) + nu d2u_i/dx_j2 ]
+
+    One call runs the nine term groups as fused kernels (``transport_term``), reorders the three
+    velocity components x -> y -> z once each (six reorders), and accumulates each y and z result
+    into the x-layout output with ``reorder_add`` (six accumulations): 21 launches.  ``P`` is
+    the chunk count per line (an int, or one per direction x, y, z); ``width`` optionally fixes
+    the lines per resident CTA.  The plans must be able to hold their lines in a CTA.
+    Six temporary fields are allocated with the object.
+    """
+
+    DIRS = ("x", "y", "z")
+
+    def __init__(self, shape, P=1, bc="periodic", dtype=torch.float64, width=None, device=None):
+        self.shape = tuple(int(v) for v in shape)
+        Ps = (P, P, P) if isinstance(P, int) else tuple(int(p) for p in P)
+        self.d1, self.d2 = {}, {}
+        for d, p in zip(self.DIRS, Ps):
+            self.d1[d] = Plan(self.shape, d, 1, bc, P=p, dtype=dtype, width=width, device=device)
+            self.d2[d] = Plan(self.shape, d, 2, bc, P=p, dtype=dtype, width=width, device=device)
+            for pl in (self.d1[d], self.d2[d]):
+                if not pl.width:
+                    raise ValueError("the %s lines do not fit a resident CTA" % d)
+        self.dtype, self.device = dtype, self.d1["x"].device
+        numel = self.d1["x"].numel
+        self._a = [torch.empty(numel, dtype=dtype, device=self.device) for _ in range(3)]
+        self._b = [torch.empty(numel, dtype=dtype, device=self.device) for _ in range(3)]
+
+    def launch_list(self, u, nu, out, stream=None):
+        """The 21 launches of one evaluation, in order, as (label, callable) pairs."""
+        if len(u) != 3 or len(out) != 3:
+            raise ValueError("u and out hold the three velocity components")
+        a, b, sh, d1, d2 = self._a, self._b, self.shape, self.d1, self.d2
+        L = []
+        # x: the terms land in the output directly
+        for i in range(3):
+            L.append(("term/x", lambda i=i: transport_term(d1["x"], d2["x"], u[i], u[0], nu, out[i], stream)))
+        # y: reorder the components, the terms into b, accumulate into the output
+        for i in range(3):
+            L.append(("reorder/x-y", lambda i=i: reorder(u[i], sh, "x", "y", a[i], stream)))
+        for i in range(3):
+            L.append(("term/y", lambda i=i: transport_term(d1["y"], d2["y"], a[i], a[1], nu, b[i], stream)))
+            L.append(("reorder_add/y-x", lambda i=i: reorder_add(b[i], sh, "y", "x", out[i], stream)))
+        # z: the components from their y copies (a row permutation) into b, the terms into a
+        for i in range(3):
+            L.append(("reorder/y-z", lambda i=i: reorder(a[i], sh, "y", "z", b[i], stream)))
+        for i in range(3):
+            L.append(("term/z", lambda i=i: transport_term(d1["z"], d2["z"], b[i], b[2], nu, a[i], stream)))
+            L.append(("reorder_add/z-x", lambda i=i: reorder_add(a[i], sh, "z", "x", out[i], stream)))
+        return L
+
+    def __call__(self, u, nu, out=None, stream=None):
+        if out is None:
+            out = [torch.empty_like(u[0]) for _ in range(3)]
+        for _, fn in self.launch_list(u, nu, out, stream):
+            fn()
+        return out
 
 
 def device_status():

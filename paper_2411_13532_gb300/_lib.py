@@ -31,9 +31,11 @@ SIGNATURES = [
     ("tds_deriv_adjoint", _i, [_vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_solve", _i, [_vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_deriv_multi", _i, [_i, ctypes.POINTER(_vp), _ip, _vp, ctypes.POINTER(_vp), _vp, _sz, _vp]),
+    ("tds_transport", _i, [_vp, _vp, _vp, _vp, _d, _vp, _vp]),
     ("tds_deriv_host", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_deriv_adjoint_host", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_reorder", _i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
+    ("tds_reorder_add", _i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
     ("tds_plan_destroy", None, [_vp]),
     ("tds_status_string", ctypes.c_char_p, [_i]),
     ("tds_device_status", _i, []),

@@ -439,6 +439,22 @@ tds_status tds_deriv_multi(int count, const tds_plan *const *plans, const int *a
     return TDS_OK;
 }
 
+tds_status tds_transport(const tds_plan *d1, const tds_plan *d2, const void *ui, const void *uj, double nu,
+                         void *out, void *stream) {
+    if (!d1 || !d2 || !ui || !uj || !out || d1->band || d2->band || d1->order != 1 || d2->order != 2)
+        return TDS_ERR_ARG;
+    // one geometry: the same field in the same direction layout, cut the same way
+    if (d1->nx != d2->nx || d1->ny != d2->ny || d1->nz != d2->nz || d1->dir != d2->dir ||
+        d1->dtype != d2->dtype || d1->P != d2->P || d1->width != d2->width)
+        return TDS_ERR_ARG;
+    // the fused kernel is resident: a CTA must hold its lines of a group
+    if (!d1->resident_smem || !d2->resident_smem) return TDS_ERR_ARG;
+    if (!aligned(ui, 16) || !aligned(uj, 16) || !aligned(out, 16)) return TDS_ERR_ARG;
+    const size_t bytes = (size_t)d1->n * d1->nlines * elem_size(d1->dtype);
+    if (overlaps(out, bytes, ui, bytes) || overlaps(out, bytes, uj, bytes)) return TDS_ERR_ALIAS;
+    return launch_resident_transport(d1, d2, ui, uj, nu, out, static_cast<cudaStream_t>(stream));
+}
+
 tds_status tds_deriv_host(const tds_plan *p, const void *host_in, void *host_out, void *d_in,
                           void *d_out, void *ws, size_t ws_bytes, void *stream) {
     return run_host(p, 0, host_in, host_out, d_in, d_out, ws, ws_bytes, stream);
@@ -462,6 +478,21 @@ tds_status tds_reorder(const void *in, void *out, int nx, int ny, int nz, tds_la
     if (overlaps(in, bytes, out, bytes)) return TDS_ERR_ALIAS;
     return launch_reorder(in, out, nx, ny, nz, from, to, elem_size(dtype),
                           static_cast<cudaStream_t>(stream));
+}
+
+tds_status tds_reorder_add(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
+                           tds_layout to, tds_dtype dtype, int sz, void *stream) {
+    if (!in || !out || sz != kSZ || (dtype != TDS_F64 && dtype != TDS_F32) ||
+        from < TDS_LAYOUT_CART || from > TDS_LAYOUT_Z || to < TDS_LAYOUT_CART || to > TDS_LAYOUT_Z)
+        return TDS_ERR_ARG;
+    if (!aligned(in, 16) || !aligned(out, 16)) return TDS_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || nx % kSZ || ny % kSZ || nz > 65535 || ny > 65535 ||
+        (long long)nx * ny * nz > (1ll << 40))
+        return TDS_ERR_SHAPE;
+    const size_t bytes = (size_t)nx * ny * nz * elem_size(dtype);
+    if (overlaps(in, bytes, out, bytes)) return TDS_ERR_ALIAS;
+    return launch_reorder_add(in, out, nx, ny, nz, from, to, elem_size(dtype),
+                              static_cast<cudaStream_t>(stream));
 }
 
 void tds_plan_destroy(tds_plan *p) {

@@ -135,6 +135,10 @@ tds_status launch_resident(const tds_plan *p, int which, const void *in, void *o
 // width and shared memory of plans[0]) of one input into outs[i].
 tds_status launch_resident_multi(const tds_plan *const *plans, const int *which, int count, const void *in,
                                  void *const *outs, cudaStream_t st);
+// One transport term (resident, the width and shared memory of d1): out = -1/2 (uj * D1 ui +
+// D1 (uj ui)) + nu * D2 ui with d1 / d2 the first / second derivative plans of one geometry.
+tds_status launch_resident_transport(const tds_plan *d1, const tds_plan *d2, const void *ui, const void *uj,
+                                     double nu, void *out, cudaStream_t st);
 tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *out,
                             cudaStream_t st);
 size_t segmented_ws_bytes(const tds_plan *p);
@@ -147,6 +151,9 @@ tds_status launch_reduced_only(const tds_plan *p, const double *rhs, double *x,
                                cudaStream_t st);
 tds_status launch_reorder(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
                           tds_layout to, size_t elem, cudaStream_t st);
+// out += the reorder of in (the accumulation of a direction's result into another layout).
+tds_status launch_reorder_add(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
+                              tds_layout to, size_t elem, cudaStream_t st);
 tds_status read_device_status();
 tds_status launch_selftest_wait(double seconds, cudaStream_t st);
 

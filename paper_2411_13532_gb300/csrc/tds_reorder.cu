@@ -8,12 +8,28 @@
 // consecutive y at fixed (x, z).  So:
 //   Cartesian <-> y <-> z        : a permutation of whole rows (both sides coalesced);
 //   x <-> {Cartesian, y, z}      : a 32 x 32 (x, y) tile transpose through shared memory.
+// The ADD forms accumulate, out += reorder(in): the transport right-hand side (Sec. 5) adds the
+// y and z terms back into the x-layout result with one pass each (Table transport counts a
+// separate reorder and accumulation).
 #include "tds_internal.h"
 
 namespace tds {
 namespace {
 
 constexpr int R = kSZ;  // row length
+
+// One 16-byte vector of T stored at dst, or added to what dst holds (ADD).
+template <typename T, bool ADD>
+__device__ __forceinline__ void put16(T *dst, float4 v) {
+    if (ADD) {
+        const float4 o = *reinterpret_cast<const float4 *>(dst);
+        T *e = reinterpret_cast<T *>(&v);
+        const T *f = reinterpret_cast<const T *>(&o);
+#pragma unroll
+        for (int u = 0; u < 16 / (int)sizeof(T); ++u) e[u] += f[u];
+    }
+    *reinterpret_cast<float4 *>(dst) = v;
+}
 
 // Offset of the row holding x = 32*xb .. 32*xb+31 at (y, z) in a layout whose rows run in x.
 __device__ __forceinline__ size_t xrun_row(tds_layout L, int xb, int y, int z, int nx, int ny,
@@ -38,7 +54,7 @@ __device__ __forceinline__ size_t xlayout_row(int x, int yb, int z, int nx, int 
 constexpr int kRowsY = 8;
 constexpr int kVecPerThread = 4;
 
-template <typename T>
+template <typename T, bool ADD>
 __global__ void __launch_bounds__(256) k_rows(const T *__restrict__ in, T *__restrict__ out, int nx,
                                              int ny, int nz, tds_layout from, tds_layout to) {
     constexpr int vpr = R * sizeof(T) / 16;      // 16-byte vectors per row
@@ -62,7 +78,7 @@ __global__ void __launch_bounds__(256) k_rows(const T *__restrict__ in, T *__res
         }
 #pragma unroll
         for (int u = 0; u < kVecPerThread; ++u)
-            if (dst[u] != (size_t)-1) *reinterpret_cast<float4 *>(out + dst[u]) = v[u];
+            if (dst[u] != (size_t)-1) put16<T, ADD>(out + dst[u], v[u]);
     }
 }
 
@@ -73,7 +89,7 @@ __global__ void __launch_bounds__(256) k_rows(const T *__restrict__ in, T *__res
 // grid (nx/32, ny/32, ceil(nz/kTilesZ)), 256 threads.  to_x selects the direction.
 constexpr int kTilesZ = 4;
 
-template <typename T>
+template <typename T, bool ADD>
 __global__ void __launch_bounds__(256) k_transpose(const T *__restrict__ in, T *__restrict__ out,
                                                   int nx, int ny, int nz, tds_layout other,
                                                   int to_x) {
@@ -107,23 +123,26 @@ __global__ void __launch_bounds__(256) k_transpose(const T *__restrict__ in, T *
             for (int u = 0; u < epv; ++u) e[u] = tile[q][vg * epv + u][i];
             T *dst = to_x ? out + xlayout_row(xb * R + i, yb, z, nx, ny)
                           : out + xrun_row(other, xb, yb * R + i, z, nx, ny, nz);
-            reinterpret_cast<float4 *>(dst)[vg] = v;
+            put16<T, ADD>(dst + vg * epv, v);
         }
     }
 }
 
-template <typename T>
+// from == to only with ADD (a plain copy is a memcpy): the identity row permutation of the
+// Cartesian layout touches every element once, whatever layout the arrays hold.
+template <typename T, bool ADD>
 tds_status launch_t(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
                     tds_layout to, cudaStream_t st) {
     const T *src = static_cast<const T *>(in);
     T *dst = static_cast<T *>(out);
+    if (from == to) from = to = TDS_LAYOUT_CART;
     if (from != TDS_LAYOUT_X && to != TDS_LAYOUT_X) {
         dim3 grid((unsigned)((ny + kRowsY - 1) / kRowsY), (unsigned)nz);
-        k_rows<T><<<grid, 256, 0, st>>>(src, dst, nx, ny, nz, from, to);
+        k_rows<T, ADD><<<grid, 256, 0, st>>>(src, dst, nx, ny, nz, from, to);
     } else {
         dim3 grid((unsigned)(nx / R), (unsigned)(ny / R), (unsigned)((nz + kTilesZ - 1) / kTilesZ));
         const int to_x = (to == TDS_LAYOUT_X);
-        k_transpose<T><<<grid, 256, 0, st>>>(src, dst, nx, ny, nz, to_x ? from : to, to_x);
+        k_transpose<T, ADD><<<grid, 256, 0, st>>>(src, dst, nx, ny, nz, to_x ? from : to, to_x);
     }
     return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
 }
@@ -137,8 +156,14 @@ tds_status launch_reorder(const void *in, void *out, int nx, int ny, int nz, tds
         return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess
                    ? TDS_OK : TDS_ERR_CUDA;
     }
-    return elem == 8 ? launch_t<double>(in, out, nx, ny, nz, from, to, st)
-                     : launch_t<float>(in, out, nx, ny, nz, from, to, st);
+    return elem == 8 ? launch_t<double, false>(in, out, nx, ny, nz, from, to, st)
+                     : launch_t<float, false>(in, out, nx, ny, nz, from, to, st);
+}
+
+tds_status launch_reorder_add(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
+                              tds_layout to, size_t elem, cudaStream_t st) {
+    return elem == 8 ? launch_t<double, true>(in, out, nx, ny, nz, from, to, st)
+                     : launch_t<float, true>(in, out, nx, ny, nz, from, to, st);
 }
 
 } // namespace tds

@@ -836,6 +836,112 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_multi(const __g
     }
 }
 
+// One term group of the skew-symmetric momentum transport right-hand side (Sec. 5, Eq.
+// mom-comps), the "abstract kernel" that reads its fields once for three operators:
+//   out = -1/2 (u_j * D1 u_i + D1 (u_j u_i)) + nu * D2 u_i
+// along the plans' direction j, all fields in that direction's layout (u_i == u_j when i = j).
+// Each CTA sweeps its W lines three times (D1 of u_i; D1 of the product, formed in shared memory
+// after the tile lands; D2 of u_i), re-loading the tile from L2 between the sweeps, and folds
+// the combination into per-thread epilogues whose read-modify-writes of `out` hit L2: HBM sees
+// the input fields read once and `out` written once.
+struct TransportArgs {
+    DevOp op1, op2;   // first and second derivative on one geometry
+    double nu;
+};
+
+template <typename Tr>
+__global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_transport(const __grid_constant__ TransportArgs ta,
+                                                                           const __grid_constant__ MultiMaps mm,
+                                                                           const typename Tr::S *__restrict__ ui,
+                                                                           const typename Tr::S *__restrict__ uj,
+                                                                           typename Tr::S *__restrict__ out) {
+    using S = typename Tr::S;
+    using A = typename Tr::A;
+    constexpr int W = Tr::W;
+    constexpr int parts = kSZ / W;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int failed;
+    const int n = ta.op1.n, m = ta.op1.m, P = ta.op1.P;
+    const int k = threadIdx.x / W, c = threadIdx.x % W;
+    const long long g = blockIdx.x / parts;
+    const int x0 = (int)(blockIdx.x % parts) * W;
+    const int y0 = (int)(g * n);                                // < 2^31, checked by the host
+    const size_t gofs = (size_t)g * n * kSZ + x0;
+    S *tile = reinterpret_cast<S *>(smem);
+    S *xs = reinterpret_cast<S *>(smem + tile_bytes_of(n, sizeof(S), W));
+    double *ends = reinterpret_cast<double *>(smem + tile_bytes_of(n, sizeof(S), W) + xs_bytes_of(sizeof(S), W));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ends + (size_t)2 * P * W);
+    const uint32_t chunk_bytes = (uint32_t)((size_t)m * W * sizeof(S));
+    if constexpr (W < kSZ) {
+        if ((smem_u32(tile) & 127u) != 0) {   // see k_resident
+            if (threadIdx.x == 0) atomicExch(&g_device_status, (int)TDS_ERR_CUDA);
+            return;
+        }
+    }
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int q = 0; q < P; ++q) mbar_init(&bars[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // this thread's rows: tile row (k m + j) W + c, field element gofs + (k m + j) 32 + c
+    const size_t ot = (size_t)k * m * W + c, ob = gofs + (size_t)k * m * kSZ + c;
+    for (int o = 0; o < 3; ++o) {
+        const DevOp &op = (o == 2) ? ta.op2 : ta.op1;
+        const uint32_t par = (uint32_t)(o & 1);
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < P; ++q) {
+                mbar_expect_tx(&bars[q], chunk_bytes);
+                if constexpr (W == kSZ) {
+                    bulk_g2s(tile + (size_t)q * m * W, ui + gofs + (size_t)q * m * kSZ, chunk_bytes, &bars[q]);
+                } else {
+                    for (int r = q * m; r < (q + 1) * m; r += mm.box_rows)
+                        tma_load_2d(tile + (size_t)r * W, &mm.in, x0, y0 + r, &bars[q]);
+                }
+            }
+        }
+        // every row of the line enters the sweep (stencil halos and closure rows included), so
+        // every chunk has to land; for the product, each thread scales its own rows first
+        bool ok = true;
+        for (int q = 0; q < P; ++q) ok = mbar_wait(&bars[q], par) && ok;
+        if (!ok) atomicExch(&failed, 1);
+        if (o == 1 && ok) {
+#pragma unroll 4
+            for (int j = 0; j < m; ++j)
+                tile[ot + (size_t)j * W] = tile[ot + (size_t)j * W] * __ldg(uj + ob + (size_t)j * kSZ);
+        }
+        __syncthreads();
+        int unsafe = 0;
+        Pack<A, 1> hb[2], ha[2];
+        if (!failed) read_halo<Tr, 1, false>(op, TileView<S>{tile, 0, n, nullptr}, xs, k, c, hb, ha, unsafe);
+        __syncthreads();
+        if (failed) {
+            for (int q = threadIdx.x; q < P; q += blockDim.x) mbar_wait(&bars[q], par);
+            if (threadIdx.x == 0) record_timeout();
+            return;
+        }
+        group_sweep<Tr, 1, 0>(op, tile, xs, ends, k, c, hb, ha, unsafe);
+        // epilogue on this thread's rows (the sweep leaves them in the tile)
+        if (o == 0) {
+            const A h = A(-0.5);
+#pragma unroll 4
+            for (int j = 0; j < m; ++j)
+                out[ob + (size_t)j * kSZ] = h * __ldg(uj + ob + (size_t)j * kSZ) * A(tile[ot + (size_t)j * W]);
+        } else {
+            const A wgt = (o == 1) ? A(-0.5) : A(ta.nu);
+#pragma unroll 4
+            for (int j = 0; j < m; ++j) {
+                S *po = out + ob + (size_t)j * kSZ;
+                *po = mad(wgt, A(tile[ot + (size_t)j * W]), A(*po));
+            }
+        }
+        // every thread is done with the tile, the scratch rows and `ends` before the next
+        // sweep's copies (async proxy) overwrite them
+        fence_async_smem();
+        __syncthreads();
+    }
+}
+
 // Persistent variant: each CTA walks units (W lines of a group) blockIdx.x, +gridDim.x, ...
 // through `nbuf` tile buffers; the TMA copies of a unit are issued `nbuf` units ahead, so HBM
 // reads stay in flight while the threads sweep.
@@ -1274,6 +1380,44 @@ tds_status launch_resident_multi(const tds_plan *const *plans, const int *which,
     return W == 16 ? launch_multi_t<TrF32w<16>>(ma, mm, in, smem, st)
          : W == 8  ? launch_multi_t<TrF32w<8>>(ma, mm, in, smem, st)
                    : launch_multi_t<TrF32>(ma, mm, in, smem, st);
+}
+
+namespace {
+template <typename Tr>
+tds_status launch_transport_t(const TransportArgs &ta, const MultiMaps &mm, const void *ui, const void *uj,
+                              void *out, int smem, cudaStream_t st) {
+    using S = typename Tr::S;
+    auto kern = k_resident_transport<Tr>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return TDS_ERR_CUDA;
+    const unsigned grid = (unsigned)((long long)ta.op1.ngroups * (kSZ / Tr::W));
+    kern<<<grid, ta.op1.P * Tr::W, smem, st>>>(ta, mm, static_cast<const S *>(ui), static_cast<const S *>(uj),
+                                                static_cast<S *>(out));
+    return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
+}
+} // namespace
+
+tds_status launch_resident_transport(const tds_plan *d1, const tds_plan *d2, const void *ui, const void *uj,
+                                     double nu, void *out, cudaStream_t st) {
+    TransportArgs ta;
+    MultiMaps mm;
+    std::memset(&ta, 0, sizeof(ta));
+    std::memset(&mm, 0, sizeof(mm));
+    ta.op1 = d1->op[0];
+    ta.op2 = d2->op[0];
+    ta.nu = nu;
+    mm.box_rows = d1->box_rows;
+    if (d1->width < kSZ &&
+        !encode_rows(&mm.in, ui, d1->dtype, (long long)d1->n * (d1->nlines / kSZ), d1->width, d1->box_rows))
+        return TDS_ERR_CUDA;
+    const int W = d1->width, smem = d1->resident_smem;
+    if (d1->dtype == TDS_F64)
+        return W == 16 ? launch_transport_t<TrF64w<16>>(ta, mm, ui, uj, out, smem, st)
+             : W == 8  ? launch_transport_t<TrF64w<8>>(ta, mm, ui, uj, out, smem, st)
+                       : launch_transport_t<TrF64>(ta, mm, ui, uj, out, smem, st);
+    return W == 16 ? launch_transport_t<TrF32w<16>>(ta, mm, ui, uj, out, smem, st)
+         : W == 8  ? launch_transport_t<TrF32w<8>>(ta, mm, ui, uj, out, smem, st)
+                   : launch_transport_t<TrF32>(ta, mm, ui, uj, out, smem, st);
 }
 
 namespace {

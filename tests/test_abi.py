@@ -83,6 +83,8 @@ def test_null_pointer_errors_need_no_gpu(L):
     sz = ctypes.c_size_t()
     assert L.tds_workspace_bytes(None, ctypes.byref(sz)) == _lib.ERR_ARG
     assert L.tds_reorder(None, None, 32, 32, 1, 0, 1, 0, 32, None) == _lib.ERR_ARG
+    assert L.tds_reorder_add(None, None, 32, 32, 1, 0, 1, 0, 32, None) == _lib.ERR_ARG
+    assert L.tds_transport(None, None, None, None, 0.1, None, None) == _lib.ERR_ARG
     assert L.tds_plan_set_width(None, 32) == _lib.ERR_ARG
     w = ctypes.c_int()
     assert L.tds_plan_width(None, ctypes.byref(w)) == _lib.ERR_ARG
@@ -99,3 +101,10 @@ def test_reorder_shape_errors_need_no_gpu(L):
                          32, None) == _lib.ERR_SHAPE
     assert L.tds_reorder(ctypes.c_void_p(a16), ctypes.c_void_p(a16 + 8), 32, 32, 1, 0, 1, 0,
                          32, None) == _lib.ERR_ARG  # misaligned out
+    # the accumulating form follows the same rules
+    assert L.tds_reorder_add(ctypes.c_void_p(a16), ctypes.c_void_p(a16 + 4096), 48, 32, 2, 0, 1, 0,
+                             32, None) == _lib.ERR_SHAPE
+    assert L.tds_reorder_add(ctypes.c_void_p(a16), ctypes.c_void_p(a16 + 8), 32, 32, 1, 0, 1, 0,
+                             32, None) == _lib.ERR_ARG
+    assert L.tds_reorder_add(ctypes.c_void_p(a16), ctypes.c_void_p(a16), 32, 32, 1, 1, 1, 0,
+                             32, None) == _lib.ERR_ALIAS
