@@ -625,7 +625,8 @@ def run_transport(args):
                 "achieved": t64["fp64_Gop_s"], "peak": round(peak, 1), "unit": "Gop/s (FP64 pipe)",
                 "frac": round(t64["fp64_Gop_s"] / peak, 4),
                 "peak_source": "derived: 2 FP64 ops/clk/SM x 152 SMs x median SM clock",
-                "traffic": None,
+                "traffic": traffic_from_profiles("f64_transport_term_%d" % S),
+                "alg_bytes_per_launch": 3 * 8 * npts,
                 "f32_term_hbm_frac": res["f32"]["kernels"]["term/x"]["hbm_frac"]}
     cpu = None
     if not args.no_cpu_baseline:
