@@ -9,5 +9,6 @@ from .oracle import (  # noqa: F401
     build, bands, rhs_lines, deriv_lines, deriv_adjoint_lines, tridiag_solve,
     lines_view, from_lines_view, to_layout, from_layout, deriv, deriv_adjoint,
     layout_lines_count, grid_spacing, transport_term_lines, transport_term,
-    transport_rhs,
+    transport_rhs, filter_lines, filter_adjoint_lines, interp_lines, interp_adjoint_lines,
+    apply_op, FILTER, INTERP,
 )

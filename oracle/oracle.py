@@ -207,3 +207,43 @@ def transport_rhs(u, nu, bc, h=None):
     Cartesian; component i sums the term groups of the three directions j."""
     dirs = ("x", "y", "z")
     return [sum(transport_term(u[i], u[j], dirs[j], nu, bc, h) for j in range(3)) for i in range(3)]
+
+
+FILTER, INTERP = 3, 4   # operator codes of the oracle's band builder (see tds_oracle.c)
+
+
+def filter_lines(lines, alpha_f, bc):
+    """The fourth-order tridiagonal compact filter (Lele 1992, App. C.2) of every line."""
+    return _lines_call(_load().tdso_deriv_lines, lines, FILTER, bc, alpha_f)
+
+
+def filter_adjoint_lines(lines, alpha_f, bc):
+    """Transpose of ``filter_lines``."""
+    return _lines_call(_load().tdso_deriv_adjoint_lines, lines, FILTER, bc, alpha_f)
+
+
+def interp_lines(lines):
+    """Sixth-order compact interpolation from the nodes to the mid-points x_i + h/2 (Lele 1992,
+    App. C.1), cyclic lines."""
+    return _lines_call(_load().tdso_deriv_lines, lines, INTERP, "periodic", 1.0)
+
+
+def interp_adjoint_lines(lines):
+    """Transpose of ``interp_lines``: the interpolation from the mid-points back to the nodes."""
+    return _lines_call(_load().tdso_deriv_adjoint_lines, lines, INTERP, "periodic", 1.0)
+
+
+def apply_op(cart, direction, op, bc, param=None, adjoint=False):
+    """One of the line operators along a direction of a Cartesian field: op 1 / 2 (derivatives,
+    param = h or None for the default spacing), 3 (filter, param = alpha_f) or 4 (mid-point
+    interpolation, cyclic lines)."""
+    cart = np.ascontiguousarray(cart, dtype=np.float64)
+    n = {"x": cart.shape[2], "y": cart.shape[1], "z": cart.shape[0]}[direction]
+    if op in (1, 2) and param is None:
+        param = grid_spacing(n, bc)
+    if op == INTERP:
+        param = 1.0
+    fn = _load().tdso_deriv_adjoint_lines if adjoint else _load().tdso_deriv_lines
+    out = _lines_call(fn, lines_view(cart, direction), op, bc, param)
+    return np.ascontiguousarray(from_lines_view(out, direction, cart.shape))
+

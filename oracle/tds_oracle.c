@@ -27,6 +27,24 @@
  *                     i=1:  f''0/10 + f''1 + f''2/10 = (6/5)(f0 - 2 f1 + f2)/h^2
  *                     i=n-2, n-1: mirror images
  *
+ * Other compact operators of the same tridiagonal form (the paper notes that compact schemes
+ * also give interpolations and filters, citing Lele 1992; it prints neither, so these are
+ * the standard members of Lele's families, stated here in full).  The slot h then carries
+ * the operator's parameter:
+ *   order 3, filter (Lele 1992, App. C.2, tridiagonal fourth-order member), h = alpha_f with
+ *     |alpha_f| < 1/2:
+ *       alpha_f g[i-1] + g[i] + alpha_f g[i+1]
+ *         = a0 f[i] + (a1/2)(f[i+1] + f[i-1]) + (a2/2)(f[i+2] + f[i-2]),
+ *       a0 = 5/8 + 3 alpha_f/4, a1 = 1/2 + alpha_f, a2 = -1/8 + alpha_f/4
+ *     (transfer function 1 at k = 0, 0 at the grid's odd-even mode); closed lines keep the
+ *     end values (g[0] = f[0], g[n-1] = f[n-1]) and use the second-order member at rows 1
+ *     and n-2 (a0 = a1 = 1/2 + alpha_f, a2 = 0);
+ *   order 4, mid-point interpolation (Lele 1992, App. C.1, sixth-order member), cyclic
+ *     lines only, h unused: g[i] approximates f at x[i] + h/2,
+ *       alpha g[i-1] + g[i] + alpha g[i+1] = (a/2)(f[i] + f[i+1]) + (b/2)(f[i-1] + f[i+2]),
+ *       alpha = 3/10, a = 3/2, b = 1/10;
+ *     its transpose (the adjoint) is the interpolation from mid-points back to the nodes.
+ *
  * Band convention: row i of A is a[i]*u[i-1] + b[i]*u[i] + c[i]*u[i+1]; for cyclic
  * lines a[0] multiplies u[n-1] and c[n-1] multiplies u[0].  Row i of B is stored as 7
  * taps B7[7*i + 3 + o] multiplying f[i+o], o = -3..3 (indices taken modulo n on cyclic
@@ -38,13 +56,50 @@
 #define TAPS 7
 #define MID 3
 
-/* Interior and closure coefficients, order 1 or 2, grid spacing h.  Returns 0 on
- * success, -1 on invalid arguments. */
+/* The filter and the mid-point interpolation (orders 3 and 4 above). */
+static int other_bands(int n, int order, int periodic, double param,
+                       double *a, double *b, double *c, double *B7)
+{
+    if (order == 3) {
+        const double af = param;
+        if (!(af > -0.5 && af < 0.5)) return -1;
+        const double a0 = 5.0 / 8.0 + 0.75 * af, a1 = 0.5 + af, a2 = -1.0 / 8.0 + 0.25 * af;
+        for (int i = 0; i < n; ++i) {
+            a[i] = af; b[i] = 1.0; c[i] = af;
+            double *r = B7 + (size_t)TAPS * i + MID;
+            r[-2] = 0.5 * a2; r[-1] = 0.5 * a1; r[0] = a0; r[1] = 0.5 * a1; r[2] = 0.5 * a2;
+        }
+        if (periodic) return 0;
+        for (int e = 0; e < 2; ++e) {
+            const int i0 = e ? n - 1 : 0, i1 = e ? n - 2 : 1;
+            double *r0 = B7 + (size_t)TAPS * i0 + MID, *r1 = B7 + (size_t)TAPS * i1 + MID;
+            for (int o = -MID; o <= MID; ++o) { r0[o] = 0.0; r1[o] = 0.0; }
+            a[i0] = 0.0; c[i0] = 0.0;
+            r0[0] = 1.0;
+            r1[-1] = 0.5 * (0.5 + af); r1[0] = 0.5 + af; r1[1] = 0.5 * (0.5 + af);
+        }
+        return 0;
+    }
+    /* order 4 */
+    if (!periodic) return -1;
+    const double alpha = 3.0 / 10.0, ha = 0.5 * 1.5, hb = 0.5 * (1.0 / 10.0);
+    for (int i = 0; i < n; ++i) {
+        a[i] = alpha; b[i] = 1.0; c[i] = alpha;
+        double *r = B7 + (size_t)TAPS * i + MID;
+        r[-1] = hb; r[0] = ha; r[1] = ha; r[2] = hb;
+    }
+    return 0;
+}
+
+/* Interior and closure coefficients: order 1 or 2 with grid spacing h, or the operators of
+ * orders 3 and 4 with their parameter in h.  Returns 0 on success, -1 on invalid arguments. */
 int tdso_bands(int n, int order, int periodic, double h,
                double *a, double *b, double *c, double *B7)
 {
-    if (n < 5 || (order != 1 && order != 2) || !(h > 0.0)) return -1;
+    if (n < 5 || order < 1 || order > 4) return -1;
     memset(B7, 0, sizeof(double) * (size_t)TAPS * (size_t)n);
+    if (order >= 3) return other_bands(n, order, periodic, h, a, b, c, B7);
+    if (!(h > 0.0)) return -1;
     double alpha, t1, t2, t0;
     if (order == 1) {
         /* Eq. cfds: a/(2h) on f[i+1]-f[i-1], b/(4h) on f[i+2]-f[i-2] */

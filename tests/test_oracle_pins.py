@@ -388,3 +388,136 @@ def test_transport_skew_symmetric_energy_identity(oracle_mod, j):
     assert abs(np.sum(ui * conv)) > 1e3 * bound
     t1 = oracle_mod.transport_term(ui, uj, j, 0.5, "periodic")
     assert np.sum(ui * t1) < -1e3 * bound
+
+
+# ------------------------------------- compact filter and mid-point interpolation (Lele 1992)
+# The coefficients are pinned by their defining conditions, evaluated on the oracle's own band
+# rows in exact rational arithmetic: a filter row keeps polynomials up to its order and removes
+# the grid's odd-even mode; the interpolation row is exact at the mid-point through degree 5.
+# The solved operators are pinned against their Fourier symbols (from the same rows) and against
+# dense LU.
+
+AF = 0.375   # a dyadic filter parameter: the coefficients are then exact binary fractions
+
+
+def _filter_row_residual(o, n, bc, i, p, x0):
+    """Row i of the filter, alpha g[i-1] + g[i] + alpha g[i+1] = sum B7 f, on f = g = (x - x0)^p."""
+    a, b, c, B7 = o.bands(n, o.FILTER, bc, AF)
+    def f(j): return Fraction(j) ** p if p > 0 else Fraction(1)
+    lhs = Fraction(b[i]) * f(i - x0)
+    if i > 0 or bc == "periodic": lhs += Fraction(a[i]) * f(i - 1 - x0)
+    if i < n - 1 or bc == "periodic": lhs += Fraction(c[i]) * f(i + 1 - x0)
+    rhs = sum(Fraction(B7[i, t]) * f(i + t - 3 - x0) for t in range(7) if B7[i, t] != 0.0)
+    return lhs - rhs
+
+
+@pytest.mark.parametrize("row,deg", [("mid", 3), (1, 1), (-2, 1), (0, 99), (-1, 99)])
+def test_filter_rows_keep_polynomials_to_their_order(oracle_mod, row, deg):
+    n = 16
+    i = n // 2 if row == "mid" else row % n
+    for p in range(0, min(deg, 6) + 1):
+        assert _filter_row_residual(oracle_mod, n, "closed", i, p, i) == 0, (row, p)
+    if deg < 99:   # exactly that order: the next even degree is not kept
+        assert _filter_row_residual(oracle_mod, n, "closed", i, deg + 1, i) != 0
+    a, b, c, B7 = oracle_mod.bands(n, oracle_mod.FILTER, "closed", AF)
+    if row in (0, -1):   # the end values are kept: g = f with no coupling
+        assert a[i] == 0 and c[i] == 0 and b[i] == 1 and B7[i, 3] == 1 and np.count_nonzero(B7[i]) == 1
+    else:                # the right-hand side of the row removes the odd-even mode
+        assert sum(Fraction(B7[i, t]) * (-1) ** t for t in range(7)) == 0
+        assert a[i] == AF and c[i] == AF
+
+
+def _symbol(o, op, n, bc, param, k, shift=0.0):
+    """Fourier symbol of the uniform row of an operator from the oracle's band: the factor that
+    maps cos(k x_j + phi) to cos(k (x_j + shift h) + phi) (real for symmetric rows)."""
+    a, b, c, B7 = o.bands(n, op, bc, param)
+    i = n // 2
+    th = 2 * np.pi * k / n
+    num = sum(B7[i, t] * np.exp(1j * th * (t - 3 - shift)) for t in range(7))
+    den = a[i] * np.exp(-1j * th) + b[i] + c[i] * np.exp(1j * th)
+    return num / den
+
+
+@pytest.mark.parametrize("n", [16, 64])
+def test_filter_transfer_function_on_fourier_modes(oracle_mod, n):
+    x = np.arange(n) * 2 * np.pi / n
+    for k in [0, 1, 3, n // 4, n // 2 - 1, n // 2]:
+        phi = 0.3 * k + 0.1
+        f = np.cos(k * x + phi)
+        T = _symbol(oracle_mod, oracle_mod.FILTER, n, "periodic", AF, k)
+        assert abs(T.imag) <= 1e-15
+        got = oracle_mod.filter_lines(f[None, :], AF, "periodic")[0]
+        np.testing.assert_allclose(got, T.real * f, rtol=0, atol=1e-13)
+        if k == 0:
+            assert abs(T.real - 1.0) <= 1e-15
+        if k == n // 2:   # the odd-even mode is removed
+            assert np.max(np.abs(got)) <= 1e-14
+
+
+@pytest.mark.parametrize("n", [16, 33])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+def test_filter_matches_dense_lu_and_adjoint(oracle_mod, n, bc):
+    rng = np.random.default_rng(n + 3 * (bc == "closed"))
+    A, B = dense(oracle_mod, n, oracle_mod.FILTER, bc, AF)
+    f = rng.uniform(-1, 1, (4, n))
+    ref = np.linalg.solve(A, B @ f.T).T
+    np.testing.assert_allclose(oracle_mod.filter_lines(f, AF, bc), ref, rtol=0, atol=1e-14)
+    refT = (B.T @ np.linalg.solve(A.T, f.T)).T
+    np.testing.assert_allclose(oracle_mod.filter_adjoint_lines(f, AF, bc), refT, rtol=0, atol=1e-14)
+    if bc == "periodic":   # A and B symmetric circulant: the filter is its own transpose
+        np.testing.assert_allclose(refT, ref, rtol=0, atol=1e-14)
+
+
+def test_interp_row_exact_at_the_midpoint_through_degree_5(oracle_mod):
+    n = 16
+    a, b, c, B7 = oracle_mod.bands(n, oracle_mod.INTERP, "periodic", 1.0)
+    i = n // 2
+    half = Fraction(1, 2)
+
+    def residual(p):
+        def f(x): return x ** p if p > 0 else Fraction(1)
+        # g[j] sits at x_j + 1/2 (units of h, around x_i = 0)
+        lhs = Fraction(a[i]) * f(-1 + half) + Fraction(b[i]) * f(half) + Fraction(c[i]) * f(1 + half)
+        rhs = sum(Fraction(B7[i, t]) * f(Fraction(t - 3)) for t in range(7) if B7[i, t] != 0.0)
+        return lhs - rhs
+    # alpha = 3/10 and b/2 = 1/20 are not binary fractions: exact up to their rounding
+    for p in range(6):
+        assert abs(float(residual(p))) <= 1e-15 * 2.5 ** p, p
+    assert abs(float(residual(6))) > 1e-3
+
+
+@pytest.mark.parametrize("n", [16, 48])
+def test_interp_transfer_function_and_dense_lu(oracle_mod, n):
+    x = np.arange(n) * 2 * np.pi / n
+    h = 2 * np.pi / n
+    for k in [0, 1, 2, n // 4, n // 2 - 1]:
+        phi = 0.7 - 0.2 * k
+        T = _symbol(oracle_mod, oracle_mod.INTERP, n, "periodic", 1.0, k, shift=0.5)
+        assert abs(T.imag) <= 1e-15
+        got = oracle_mod.interp_lines(np.cos(k * x + phi)[None, :])[0]
+        np.testing.assert_allclose(got, T.real * np.cos(k * (x + h / 2) + phi), rtol=0, atol=1e-13)
+        # the transpose takes mid-point data back to the nodes with the same factor
+        back = oracle_mod.interp_adjoint_lines(np.cos(k * (x + h / 2) + phi)[None, :])[0]
+        np.testing.assert_allclose(back, T.real * np.cos(k * x + phi), rtol=0, atol=1e-13)
+    rng = np.random.default_rng(n)
+    A, B = dense(oracle_mod, n, oracle_mod.INTERP, "periodic", 1.0)
+    f = rng.uniform(-1, 1, (3, n))
+    np.testing.assert_allclose(oracle_mod.interp_lines(f), np.linalg.solve(A, B @ f.T).T, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(oracle_mod.interp_adjoint_lines(f), (B.T @ np.linalg.solve(A.T, f.T)).T,
+                               rtol=0, atol=1e-14)
+
+
+def test_interp_sixth_order_and_closed_lines_refused(oracle_mod):
+    errs = []
+    for n in (32, 64, 128):
+        h = 2 * np.pi / n
+        x = np.arange(n) * h
+        f = np.sin(x) + 0.5 * np.cos(2 * x + 0.3)
+        ex = np.sin(x + h / 2) + 0.5 * np.cos(2 * (x + h / 2) + 0.3)
+        errs.append(np.max(np.abs(oracle_mod.interp_lines(f[None, :])[0] - ex)))
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 5.7 < math.log2(e0 / e1) < 6.3, errs
+    with pytest.raises(ValueError):
+        oracle_mod.bands(16, oracle_mod.INTERP, "closed", 1.0)
+    with pytest.raises(ValueError):
+        oracle_mod.bands(16, oracle_mod.FILTER, "periodic", 0.5)
