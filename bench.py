@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="time every workload configuration one operator at a time (one JSON line per "
                          "case) instead of the benchmark step")
+    ap.add_argument("--sweep-match", default="",
+                    help="with --sweep: only the cases whose label contains this text")
     ap.add_argument("--transport", action="store_true",
                     help="time the momentum-transport right-hand side (Sec. 5) instead of the "
                          "derivative step: one JSON line")
@@ -425,6 +427,8 @@ SWEEP_CASES = [
     ("256 x 262144 D1 x periodic P=64", (1, 256, 262144), "x", (1,), ("periodic",), (64,), ("f64",), "deriv"),
     ("512^3 solve A x = d, x periodic/closed P=8 FP64/FP32", (512, 512, 512), "x", (1, 2),
      ("periodic", "closed"), (8,), ("f64", "f32"), "solve"),
+    ("512^3 compact filter (alpha_f 0.45) and mid-point interpolation, x, P=8 FP64/FP32", (512, 512, 512),
+     "x", ("filter", "interp"), ("periodic",), (8,), ("f64", "f32"), "deriv"),
 ]
 
 
@@ -443,6 +447,8 @@ def run_sweep(args):
     TD = {"f64": torch.float64, "f32": torch.float32}
     reps = max(args.steps, 5)
     for label, shape, dirs, orders, bcs, Ps, dts, kind in SWEEP_CASES:
+        if args.sweep_match not in label:
+            continue
         npts = shape[0] * shape[1] * shape[2]
         for dname in dts:
             dt = TD[dname]
@@ -452,7 +458,8 @@ def run_sweep(args):
                 for order in orders:
                     for bc in bcs:
                         for P in Ps:
-                            plan = tds.Plan(shape, direc, order, bc, P=P, dtype=dt)
+                            plan = tds.Plan(shape, direc, order, bc, P=P, dtype=dt,
+                                            alpha_f=0.45 if order == "filter" else None)
                             ws = plan.workspace()
                             fn = {"adjoint": lambda: plan.adjoint(x, y, ws), "solve": lambda: plan.solve(x, y, ws),
                                   "deriv": lambda: plan.deriv(x, y, ws)}[kind]
@@ -473,7 +480,8 @@ def run_sweep(args):
                             gbs = 2 * es * npts / (ms * 1e-3) / 1e9
                             print(json.dumps({
                                 "case": label, "dtype": dname,
-                                "op": {"adjoint": "D%dT", "solve": "A%d^-1", "deriv": "D%d"}[kind] % order,
+                                "op": (order if isinstance(order, str) else
+                                       {"adjoint": "D%dT", "solve": "A%d^-1", "deriv": "D%d"}[kind] % order),
                                 "dir": direc, "bc": bc, "P": P, "variant": plan.variant, "width": plan.width,
                                 "ms": round(ms, 4), "gpoints_s": round(npts / (ms * 1e-3) / 1e9, 2),
                                 "alg_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),

@@ -101,6 +101,34 @@ TDS_API tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_d
                            tds_reduced mode);
 
 /*
+ * tds_plan_create_filter -- a plan whose operator is the compact filter g = A^{-1} B f (the paper
+ * notes, citing Lele 1992, that compact schemes also give filters; it prints none, so this is
+ * the fourth-order tridiagonal member of Lele's family):
+ *     alpha_f g[i-1] + g[i] + alpha_f g[i+1]
+ *       = a0 f[i] + (a1/2)(f[i+1] + f[i-1]) + (a2/2)(f[i+2] + f[i-2]),
+ *     a0 = 5/8 + 3 alpha_f/4, a1 = 1/2 + alpha_f, a2 = -1/8 + alpha_f/4,
+ * which keeps polynomials through degree 3 and removes the grid's odd-even mode; on closed lines
+ * the end values are kept and rows 1 and n-2 use the second-order member (a0 = a1 = 1/2 + alpha_f,
+ * a2 = 0).  alpha_f must lie in (-1/2, 1/2) (TDS_ERR_ARG); values near 1/2 filter least.  Every
+ * other argument, rule and error is that of tds_plan_create; tds_deriv applies the filter,
+ * tds_deriv_adjoint its transpose (on periodic lines the filter itself).
+ */
+TDS_API tds_status tds_plan_create_filter(tds_plan **out, int nx, int ny, int nz, tds_dir dir, double alpha_f,
+                                          tds_bc bc, int P, tds_dtype dtype, int sz, tds_reduced mode);
+
+/*
+ * tds_plan_create_interp -- a plan whose operator is the sixth-order compact interpolation from
+ * the nodes to the mid-points of a periodic line (Lele 1992's family, as for the filter):
+ *     3/10 g[i-1] + g[i] + 3/10 g[i+1] = 3/4 (f[i] + f[i+1]) + 1/20 (f[i-1] + f[i+2]),
+ * g[i] approximating f at x_i + h/2.  Lines are cyclic (a closed line has one mid-point fewer
+ * than nodes, which this layout does not represent).  tds_deriv interpolates to the mid-points;
+ * tds_deriv_adjoint applies the transpose, which is the interpolation from mid-points (g[i] at
+ * x_i + h/2) back to the nodes.  Arguments, rules and errors as tds_plan_create.
+ */
+TDS_API tds_status tds_plan_create_interp(tds_plan **out, int nx, int ny, int nz, tds_dir dir, int P,
+                                          tds_dtype dtype, int sz, tds_reduced mode);
+
+/*
  * tds_plan_create_band -- a plan for the batched tridiagonal solve A x = d with a caller-given
  * band (Algorithms 4-6 solve any such system; not restricted to the compact schemes), e.g. the
  * implicit systems of ADI schemes.  Row j of every line is

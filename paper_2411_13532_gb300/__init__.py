@@ -46,14 +46,18 @@ class Plan:
     Creation runs the operator preprocessing (Algorithm 4) on the host and uploads it to the
     current (or given) CUDA device.  With ``band=(a, b, c)`` (n values each) the plan is the
     batched tridiagonal solve of that band instead (``tds_plan_create_band``; ``order`` and ``h``
-    are ignored and only ``solve`` is available).
+    are ignored and only ``solve`` is available).  ``order="filter"`` (with ``alpha_f``) makes the
+    fourth-order compact filter and ``order="interp"`` the sixth-order interpolation to the
+    mid-points of periodic lines (``tds_plan_create_filter`` / ``tds_plan_create_interp``;
+    ``deriv`` applies them, ``adjoint`` their transposes).
     """
 
     def __init__(self, shape, direction, order, bc, P=1, h=None, dtype=torch.float64,
-                 mode="exact", variant="auto", width=None, device=None, band=None):
+                 mode="exact", variant="auto", width=None, device=None, band=None, alpha_f=None):
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
-        self.direction, self.order, self.bc, self.P = direction, int(order), bc, int(P)
+        kind = {"filter": 3, "interp": 4}.get(order, order)
+        self.direction, self.order, self.bc, self.P = direction, int(kind), bc, int(P)
         self.n = {"x": nx, "y": ny, "z": nz}[direction]
         self.h = float(grid_spacing(self.n, bc) if h is None else h)
         self.dtype = dtype
@@ -63,7 +67,21 @@ class Plan:
         L = _lib.lib()
         h_ = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            if band is None:
+            if self.order == 3:
+                if alpha_f is None:
+                    raise ValueError("a filter plan needs alpha_f")
+                self.alpha_f = float(alpha_f)
+                _lib.check(L.tds_plan_create_filter(ctypes.byref(h_), nx, ny, nz, _lib.DIRS[direction],
+                                                    self.alpha_f, _lib.BCS[bc], self.P,
+                                                    _lib.DTYPES[_TORCH_DTYPES[dtype]], 32,
+                                                    _lib.MODES[mode]), "tds_plan_create_filter")
+            elif self.order == 4:
+                if bc != "periodic":
+                    raise ValueError("the mid-point interpolation needs periodic lines")
+                _lib.check(L.tds_plan_create_interp(ctypes.byref(h_), nx, ny, nz, _lib.DIRS[direction],
+                                                    self.P, _lib.DTYPES[_TORCH_DTYPES[dtype]], 32,
+                                                    _lib.MODES[mode]), "tds_plan_create_interp")
+            elif band is None:
                 _lib.check(L.tds_plan_create(ctypes.byref(h_), nx, ny, nz, _lib.DIRS[direction],
                                              self.order, _lib.BCS[bc], self.P, self.h,
                                              _lib.DTYPES[_TORCH_DTYPES[dtype]], 32,

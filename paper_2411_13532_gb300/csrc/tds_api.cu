@@ -236,6 +236,7 @@ tds_status finish_plan(tds_plan *p, tds_plan **out) {
         const int v = std::atoi(e);
         if (v == 1 || v == 2 || (v == 4 && dtype == TDS_F32)) p->lanes = v;
     }
+    if (p->order == 4) p->lanes = 1;   // the half-point stencil forms run one line per thread
     if (cudaStreamCreateWithFlags(&p->copy_in, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&p->copy_out, cudaStreamNonBlocking) != cudaSuccess) {
         tds_plan_destroy(p);
@@ -285,6 +286,40 @@ tds_status tds_plan_create(tds_plan **out, int nx, int ny, int nz, tds_dir dir, 
     if (!p) return TDS_ERR_NOMEM;
     p->order = order;
     p->h = h;
+    return finish_plan(p, out);
+}
+
+tds_status tds_plan_create_filter(tds_plan **out, int nx, int ny, int nz, tds_dir dir, double alpha_f,
+                                  tds_bc bc, int P, tds_dtype dtype, int sz, tds_reduced mode) {
+    if (!out) return TDS_ERR_ARG;
+    *out = nullptr;
+    if (dir < TDS_DIR_X || dir > TDS_DIR_Z || (bc != TDS_BC_PERIODIC && bc != TDS_BC_CLOSED) ||
+        (dtype != TDS_F64 && dtype != TDS_F32) ||
+        (mode != TDS_REDUCED_EXACT && mode != TDS_REDUCED_PAPER_DROP) || sz != kSZ ||
+        !(alpha_f > -0.5 && alpha_f < 0.5) || P < 1)
+        return TDS_ERR_ARG;
+    const tds_status sh = check_shape(nx, ny, nz, dir, P);
+    if (sh != TDS_OK) return sh;
+    tds_plan *p = new_plan(nx, ny, nz, dir, bc, P, dtype, mode);
+    if (!p) return TDS_ERR_NOMEM;
+    p->order = 3;
+    p->h = alpha_f;   // the filter's parameter takes the grid spacing's place
+    return finish_plan(p, out);
+}
+
+tds_status tds_plan_create_interp(tds_plan **out, int nx, int ny, int nz, tds_dir dir, int P,
+                                  tds_dtype dtype, int sz, tds_reduced mode) {
+    if (!out) return TDS_ERR_ARG;
+    *out = nullptr;
+    if (dir < TDS_DIR_X || dir > TDS_DIR_Z || (dtype != TDS_F64 && dtype != TDS_F32) ||
+        (mode != TDS_REDUCED_EXACT && mode != TDS_REDUCED_PAPER_DROP) || sz != kSZ || P < 1)
+        return TDS_ERR_ARG;
+    const tds_status sh = check_shape(nx, ny, nz, dir, P);
+    if (sh != TDS_OK) return sh;
+    tds_plan *p = new_plan(nx, ny, nz, dir, TDS_BC_PERIODIC, P, dtype, mode);
+    if (!p) return TDS_ERR_NOMEM;
+    p->order = 4;
+    p->h = 1.0;
     return finish_plan(p, out);
 }
 

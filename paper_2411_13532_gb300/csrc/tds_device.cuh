@@ -131,9 +131,14 @@ __device__ __forceinline__ T stencil(const DevOp &op, int J, const T (&w)[kTaps]
         for (int o = 0; o < kTaps; ++o) s += T(op.edge[e][o]) * w[o];
         return s;
     }
-    const T t1 = T(op.tap[4]), t2 = T(op.tap[5]);
-    if (op.symmetric > 0) return T(op.tap[3]) * w[3] + t1 * (w[4] + w[2]) + t2 * (w[5] + w[1]);
-    return t1 * (w[4] - w[2]) + t2 * (w[5] - w[1]);
+    // uniform interior rows: taps at offsets 0, +1, +2 and the form of op.symmetric
+    const T t0 = T(op.tap[3]), t1 = T(op.tap[4]), t2 = T(op.tap[5]);
+    switch (op.symmetric) {
+    case 1: return t0 * w[3] + t1 * (w[4] + w[2]) + t2 * (w[5] + w[1]);   // symmetric
+    case 2: return t1 * (w[3] + w[4]) + t2 * (w[2] + w[5]);              // nodes -> mid-points
+    case 3: return t0 * (w[2] + w[3]) + t1 * (w[1] + w[4]);              // mid-points -> nodes
+    default: return t1 * (w[4] - w[2]) + t2 * (w[5] - w[1]);             // antisymmetric
+    }
 }
 
 template <typename T>

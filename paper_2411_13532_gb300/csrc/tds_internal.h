@@ -43,7 +43,9 @@ struct DevOp {
     int adjoint;    // how the sweep runs: 0 stencil right-hand side (A^{-1} B, and B^T A^{-T} on
                     // periodic lines); 1 identity right-hand side on A^T, then the B^T taps
                     // (the adjoint on closed lines); 2 identity right-hand side, no taps (A^{-1})
-    int symmetric;  // interior taps: +1 symmetric (order 2), -1 antisymmetric (order 1)
+    int symmetric;  // interior taps: -1 antisymmetric (first derivative), +1 symmetric (second
+                    // derivative, filter), +2 pairs about +1/2 (nodes -> mid-points), +3 pairs
+                    // about -1/2 (mid-points -> nodes)
     int ncls;       // chunk classes (first / interior / last differ on closed lines)
     int cls_first, cls_mid, cls_last;
     const double *row64;  // [kNumRowArrays][ncls*m]

@@ -79,6 +79,41 @@ void scheme_line(int n, int order, bool periodic, double h, LineOperator &L) {
     }
 }
 
+// The other compact operators of the same tridiagonal form (the paper notes that compact
+// schemes give interpolations and filters too, after Lele 1992, without printing them; these
+// are the standard members of Lele's families):
+//   order 3, filter with parameter alpha_f (|alpha_f| < 1/2), the fourth-order tridiagonal
+//     member: alpha_f g[i-1] + g[i] + alpha_f g[i+1] = a0 f[i] + (a1/2)(f[i+1] + f[i-1])
+//     + (a2/2)(f[i+2] + f[i-2]), a0 = 5/8 + 3 alpha_f/4, a1 = 1/2 + alpha_f,
+//     a2 = -1/8 + alpha_f/4; closed lines keep the end values and use the second-order member
+//     (a0 = a1 = 1/2 + alpha_f) at rows 1 and n-2;
+//   order 4, interpolation from the nodes to the mid-points x_i + h/2, the sixth-order member,
+//     cyclic lines: 3/10 g[i-1] + g[i] + 3/10 g[i+1] = 3/4 (f[i] + f[i+1]) + 1/20 (f[i-1] + f[i+2]).
+void other_line(int n, int order, bool periodic, double alpha_f, LineOperator &L) {
+    L.a.assign(n, 0.0); L.b.assign(n, 1.0); L.c.assign(n, 0.0);
+    L.taps.assign((size_t)n * kTaps, 0.0);
+    for (int J = 0; J < n; ++J) {
+        double *t = &L.taps[(size_t)J * kTaps + 3];
+        if (order == 3) {
+            const double a0 = 5.0 / 8.0 + 0.75 * alpha_f, a1 = 0.5 + alpha_f, a2 = -1.0 / 8.0 + 0.25 * alpha_f;
+            L.a[J] = alpha_f; L.c[J] = alpha_f;
+            t[-2] = 0.5 * a2; t[-1] = 0.5 * a1; t[0] = a0; t[1] = 0.5 * a1; t[2] = 0.5 * a2;
+        } else {
+            L.a[J] = 0.3; L.c[J] = 0.3;
+            t[-1] = 0.05; t[0] = 0.75; t[1] = 0.75; t[2] = 0.05;
+        }
+    }
+    if (periodic) return;   // order 4 plans are cyclic (checked at creation)
+    for (int e = 0; e < 2; ++e) {
+        const int J0 = e ? n - 1 : 0, J1 = e ? n - 2 : 1;
+        double *t0 = &L.taps[(size_t)J0 * kTaps + 3], *t1 = &L.taps[(size_t)J1 * kTaps + 3];
+        for (int o = -3; o <= 3; ++o) { t0[o] = 0.0; t1[o] = 0.0; }
+        L.a[J0] = 0.0; L.c[J0] = 0.0;
+        t0[0] = 1.0;
+        t1[-1] = 0.5 * (0.5 + alpha_f); t1[0] = 0.5 + alpha_f; t1[1] = 0.5 * (0.5 + alpha_f);
+    }
+}
+
 // A caller-given band (a, b, c of n rows each): no stencil (the solve alone).  On closed lines
 // a[0] and c[n-1] couple to nothing and are dropped.
 void band_line(int n, bool periodic, const double *band, LineOperator &L) {
@@ -166,7 +201,8 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
     op.n = n; op.m = m; op.P = P; op.nlines = p->nlines; op.ngroups = p->nlines / kSZ;
     const bool fwd_form = (which == 0) || (which == 1 && periodic);
     op.periodic = periodic; op.adjoint = fwd_form ? 0 : which;
-    op.symmetric = (p->order == 2) ? 1 : -1;
+    // interior stencil form: the interpolation's transpose pairs its taps about -1/2
+    op.symmetric = (p->order == 1) ? -1 : (p->order == 4) ? (which == 1 ? 3 : 2) : 1;
 
     // chunk classes: cyclic lines have one; closed lines distinguish first / interior / last
     int reps[3];
@@ -329,6 +365,7 @@ tds_status build_plan(tds_plan *p) {
     const bool periodic = (p->bc == TDS_BC_PERIODIC);
     LineOperator L, LT;
     if (p->band) band_line(p->n, periodic, p->band, L);
+    else if (p->order >= 3) other_line(p->n, p->order, periodic, p->h, L);
     else scheme_line(p->n, p->order, periodic, p->h, L);
     transpose_line(p->n, periodic, L, LT);
 

@@ -149,14 +149,28 @@ __device__ __forceinline__ Pack<typename Tr::A, V> zero_a() {
     return r;
 }
 
+// Forms of the uniform interior stencil (taps t0, t1, t2 at offsets 0, +1, +2 of the row):
+//   kAnti: t1 (v[j+1] - v[j-1]) + t2 (v[j+2] - v[j-2])              (first derivative)
+//   kSym : t0 v[j] + t1 (v[j+1] + v[j-1]) + t2 (v[j+2] + v[j-2])     (second derivative, filter)
+//   kHalfFwd: t1 (v[j] + v[j+1]) + t2 (v[j-1] + v[j+2])              (nodes -> mid-points)
+//   kHalfBwd: t0 (v[j-1] + v[j]) + t1 (v[j-2] + v[j+1])              (its transpose)
+// (the plan's op.symmetric: -1, 1, 2, 3).
+constexpr int kAnti = 0, kSym = 1, kHalfFwd = 2, kHalfBwd = 3;
+
+template <typename A, int FORM>
+__device__ __forceinline__ A interior_rhs(A t0, A t1, A t2, A w0, A w1, A w2, A w3, A w4) {
+    if (FORM == kSym) return mad(t0, w2, mad(t1, w3 + w1, t2 * (w4 + w0)));
+    if (FORM == kHalfFwd) return mad(t1, w2 + w3, t2 * (w1 + w4));
+    if (FORM == kHalfBwd) return mad(t0, w1 + w2, t1 * (w0 + w3));
+    return mad(t1, w3 - w1, t2 * (w4 - w0));
+}
+
 // Interior stencil (offsets -2..2) of V lines from the window w[i] = v[J - 2 + i].
-template <typename A, int V, bool SYM>
+template <typename A, int V, int FORM>
 __device__ __forceinline__ void istencil(A t0, A t1, A t2, const Pack<A, V> (&w)[5], A (&s)[V]) {
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-        if (SYM) s[i] = t0 * w[2].v[i] + t1 * (w[3].v[i] + w[1].v[i]) + t2 * (w[4].v[i] + w[0].v[i]);
-        else s[i] = t1 * (w[3].v[i] - w[1].v[i]) + t2 * (w[4].v[i] - w[0].v[i]);
-    }
+    for (int i = 0; i < V; ++i)
+        s[i] = interior_rhs<A, FORM>(t0, t1, t2, w[0].v[i], w[1].v[i], w[2].v[i], w[3].v[i], w[4].v[i]);
 }
 
 // Closure-row stencil (offsets -3..3, closed lines) from w[i] = v[J - 3 + i]; e indexes the
@@ -241,9 +255,9 @@ __device__ __forceinline__ void fwd_row(const DevOp &op, int cls, int j, typenam
 }
 
 // Interior row of the forward pass with f folded into the coefficients:
-// d_j = c1 (v[j+1] -+ v[j-1]) + c2 (v[j+2] -+ v[j-2]) (+ c0 v[j]) - g d_{j-1}, one FMA on the
-// recurrence; ACC: S += pi_j d_j (rows past the plan's cut-off skip it).
-template <typename Tr, int V, bool SYM, bool ACC>
+// d_j = (the FORM's stencil with taps c0, c1, c2) - g d_{j-1}, one FMA on the recurrence;
+// ACC: S += pi_j d_j (rows past the plan's cut-off skip it).
+template <typename Tr, int V, int FORM, bool ACC>
 __device__ __forceinline__ void fwd_irow_c(const DevOp &op, int cls, int j, typename Tr::S *row,
                                            const Pack<typename Tr::A, V> (&w)[5],
                                            Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S,
@@ -254,8 +268,7 @@ __device__ __forceinline__ void fwd_irow_c(const DevOp &op, int cls, int j, type
     if (ACC) p = Tr::pi(op, cls, j);
 #pragma unroll
     for (int i = 0; i < V; ++i) {
-        A base = SYM ? mad(c0, w[2].v[i], mad(c1, w[3].v[i] + w[1].v[i], c2 * (w[4].v[i] + w[0].v[i])))
-                     : mad(c1, w[3].v[i] - w[1].v[i], c2 * (w[4].v[i] - w[0].v[i]));
+        const A base = interior_rhs<A, FORM>(c0, c1, c2, w[0].v[i], w[1].v[i], w[2].v[i], w[3].v[i], w[4].v[i]);
         dprev.v[i] = mad(-g, dprev.v[i], base);
         if (ACC) S.v[i] = mad(p, dprev.v[i], S.v[i]);
     }
@@ -263,18 +276,18 @@ __device__ __forceinline__ void fwd_irow_c(const DevOp &op, int cls, int j, type
 }
 
 // The same with the row's own record from the plan.
-template <typename Tr, int V, bool SYM, bool ACC>
+template <typename Tr, int V, int FORM, bool ACC>
 __device__ __forceinline__ void fwd_irow(const DevOp &op, int cls, int j, typename Tr::S *row,
                                          const Pack<typename Tr::A, V> (&w)[5],
                                          Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S) {
     typename Tr::A c0, c1, c2, g;
     Tr::ifw(op, cls, j, c0, c1, c2, g);
-    fwd_irow_c<Tr, V, SYM, ACC>(op, cls, j, row, w, dprev, S, c0, c1, c2, g);
+    fwd_irow_c<Tr, V, FORM, ACC>(op, cls, j, row, w, dprev, S, c0, c1, c2, g);
 }
 
 // Interior forward rows [jb, je) reading v[j+2] from the tile (inside the chunk); CONST: every
 // row has the class's constant record (k0..kg), else each row loads its own.
-template <typename Tr, int V, bool SYM, bool ACC, bool CONST>
+template <typename Tr, int V, int FORM, bool ACC, bool CONST>
 __device__ __forceinline__ void fwd_irows(const DevOp &op, int cls, typename Tr::S *row, int jb, int je,
                                           Pack<typename Tr::A, V> (&w)[5], Pack<typename Tr::A, V> &dprev,
                                           Pack<typename Tr::A, V> &S, int &unsafe, typename Tr::A k0 = 0,
@@ -282,8 +295,8 @@ __device__ __forceinline__ void fwd_irows(const DevOp &op, int cls, typename Tr:
 #pragma unroll 4
     for (int j = jb; j < je; ++j) {
         w[4] = Tr::template ld_in<V>(op, row + (size_t)(j + 2) * Tr::W, unsafe);
-        if (CONST) fwd_irow_c<Tr, V, SYM, ACC>(op, cls, j, row, w, dprev, S, k0, k1, k2, kg);
-        else fwd_irow<Tr, V, SYM, ACC>(op, cls, j, row, w, dprev, S);
+        if (CONST) fwd_irow_c<Tr, V, FORM, ACC>(op, cls, j, row, w, dprev, S, k0, k1, k2, kg);
+        else fwd_irow<Tr, V, FORM, ACC>(op, cls, j, row, w, dprev, S);
 #pragma unroll
         for (int i = 0; i < 4; ++i) w[i] = w[i + 1];
     }
@@ -291,7 +304,7 @@ __device__ __forceinline__ void fwd_irows(const DevOp &op, int cls, typename Tr:
 
 // Forward rows [jb, je): the part inside the class's constant-record run [lo, hi) with the
 // record in registers, the rest with per-row records.
-template <typename Tr, int V, bool SYM, bool ACC>
+template <typename Tr, int V, int FORM, bool ACC>
 __device__ __forceinline__ void fwd_span(const DevOp &op, int cls, typename Tr::S *row, int jb, int je,
                                          Pack<typename Tr::A, V> (&w)[5], Pack<typename Tr::A, V> &dprev,
                                          Pack<typename Tr::A, V> &S, int &unsafe) {
@@ -301,16 +314,16 @@ __device__ __forceinline__ void fwd_span(const DevOp &op, int cls, typename Tr::
     const int b = (hi < a) ? a : (hi > je ? je : hi);
     typename Tr::A k0, k1, k2, kg;
     Tr::kf(op, cls, k0, k1, k2, kg);
-    fwd_irows<Tr, V, SYM, ACC, false>(op, cls, row, jb, a, w, dprev, S, unsafe);
-    fwd_irows<Tr, V, SYM, ACC, true>(op, cls, row, a, b, w, dprev, S, unsafe, k0, k1, k2, kg);
-    fwd_irows<Tr, V, SYM, ACC, false>(op, cls, row, b, je, w, dprev, S, unsafe);
+    fwd_irows<Tr, V, FORM, ACC, false>(op, cls, row, jb, a, w, dprev, S, unsafe);
+    fwd_irows<Tr, V, FORM, ACC, true>(op, cls, row, a, b, w, dprev, S, unsafe, k0, k1, k2, kg);
+    fwd_irows<Tr, V, FORM, ACC, false>(op, cls, row, b, je, w, dprev, S, unsafe);
 }
 
 // Interior rows [jb, je) of a stencil sweep over this chunk, in place: w[0..3] holds
 // v[j-2..j+1] on entry; v[j+2] is read from the tile while inside the chunk (rows ahead of the
 // window are not yet overwritten), then from the halo `ha`.  FWD: forward elimination rows
 // (input values); else B^T rows (mid values, result written as output).
-template <typename Tr, int V, bool SYM, bool FWD>
+template <typename Tr, int V, int FORM, bool FWD>
 __device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typename Tr::S *row, int jb, int je,
                                                Pack<typename Tr::A, V> (&w)[5],
                                                const Pack<typename Tr::A, V> (&ha)[2],
@@ -324,14 +337,14 @@ __device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typenam
         // rows before the pi cut-off accumulate S, the rest do not
         const int jp = Tr::jpi(op, cls);
         const int j1 = (jp < jb) ? jb : (jp > jm ? jm : jp);
-        fwd_span<Tr, V, SYM, true>(op, cls, row, jb, j1, w, dprev, S, unsafe);
-        fwd_span<Tr, V, SYM, false>(op, cls, row, j1, jm, w, dprev, S, unsafe);
+        fwd_span<Tr, V, FORM, true>(op, cls, row, jb, j1, w, dprev, S, unsafe);
+        fwd_span<Tr, V, FORM, false>(op, cls, row, j1, jm, w, dprev, S, unsafe);
     } else {
 #pragma unroll 4
         for (int j = jb; j < jm; ++j) {
             w[4] = Tr::template ld_mid<V>(row + (size_t)(j + 2) * Tr::W);
             A sv[V];
-            istencil<A, V, SYM>(t0, t1, t2, w, sv);
+            istencil<A, V, FORM>(t0, t1, t2, w, sv);
             Pack<A, V> x;
 #pragma unroll
             for (int i = 0; i < V; ++i) x.v[i] = sv[i];
@@ -345,11 +358,11 @@ __device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typenam
         if (FWD) {
             // FP64 sweeps skip S on these rows past the pi cut-off too (measured: the FP32
             // sweeps run faster with the uniform row)
-            if (sizeof(A) == 4 || j < Tr::jpi(op, cls)) fwd_irow<Tr, V, SYM, true>(op, cls, j, row, w, dprev, S);
-            else fwd_irow<Tr, V, SYM, false>(op, cls, j, row, w, dprev, S);
+            if (sizeof(A) == 4 || j < Tr::jpi(op, cls)) fwd_irow<Tr, V, FORM, true>(op, cls, j, row, w, dprev, S);
+            else fwd_irow<Tr, V, FORM, false>(op, cls, j, row, w, dprev, S);
         } else {
             A sv[V];
-            istencil<A, V, SYM>(t0, t1, t2, w, sv);
+            istencil<A, V, FORM>(t0, t1, t2, w, sv);
             Pack<A, V> x;
 #pragma unroll
             for (int i = 0; i < V; ++i) x.v[i] = sv[i];
@@ -419,8 +432,16 @@ __device__ __forceinline__ void stencil_sweep(const DevOp &op, int k, int cls, t
         w[2] = FWD ? Tr::template ld_in<V>(op, row, unsafe) : Tr::template ld_mid<V>(row);
         w[3] = FWD ? Tr::template ld_in<V>(op, row + Tr::W, unsafe) : Tr::template ld_mid<V>(row + Tr::W);
     }
-    if (op.symmetric > 0) sweep_interior<Tr, V, true, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
-    else sweep_interior<Tr, V, false, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
+    if (op.symmetric == 1) {
+        sweep_interior<Tr, V, kSym, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
+    } else if (op.symmetric < 0) {
+        sweep_interior<Tr, V, kAnti, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
+    } else if constexpr (FWD && V == 1) {
+        // the half-point forms belong to the mid-point interpolation and its transpose: cyclic
+        // lines only (forward form) and one line per thread (the planner fixes both)
+        if (op.symmetric == 2) sweep_interior<Tr, V, kHalfFwd, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
+        else sweep_interior<Tr, V, kHalfBwd, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
+    }
     // the last 4 rows of a closed line: scratch rows 7..13 hold v[n-7..n-1]
     if (last_edge)
         sweep_edge<Tr, V, FWD>(op, cls, row, m - 4, kEdgeRows, xs + (size_t)kTaps * Tr::W, c, 0, kTaps, dprev, S);
