@@ -870,7 +870,7 @@ struct TransportArgs {
     double nu;
 };
 
-template <typename Tr>
+template <typename Tr, int V>
 __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_transport(const __grid_constant__ TransportArgs ta,
                                                                            const __grid_constant__ MultiMaps mm,
                                                                            const typename Tr::S *__restrict__ ui,
@@ -879,11 +879,12 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_transport(const
     using S = typename Tr::S;
     using A = typename Tr::A;
     constexpr int W = Tr::W;
+    constexpr int tpc = W / V;
     constexpr int parts = kSZ / W;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int failed;
     const int n = ta.op1.n, m = ta.op1.m, P = ta.op1.P;
-    const int k = threadIdx.x / W, c = threadIdx.x % W;
+    const int k = threadIdx.x / tpc, c = (threadIdx.x % tpc) * V;
     const long long g = blockIdx.x / parts;
     const int x0 = (int)(blockIdx.x % parts) * W;
     const int y0 = (int)(g * n);                                // < 2^31, checked by the host
@@ -905,7 +906,7 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_transport(const
         fence_mbar_init();
     }
     __syncthreads();
-    // this thread's rows: tile row (k m + j) W + c, field element gofs + (k m + j) 32 + c
+    // this thread's rows: tile row (k m + j) W + c, field element gofs + (k m + j) 32 + c (V lines)
     const size_t ot = (size_t)k * m * W + c, ob = gofs + (size_t)k * m * kSZ + c;
     for (int o = 0; o < 3; ++o) {
         const DevOp &op = (o == 2) ? ta.op2 : ta.op1;
@@ -928,32 +929,47 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_transport(const
         if (!ok) atomicExch(&failed, 1);
         if (o == 1 && ok) {
 #pragma unroll 4
-            for (int j = 0; j < m; ++j)
-                tile[ot + (size_t)j * W] = tile[ot + (size_t)j * W] * __ldg(uj + ob + (size_t)j * kSZ);
+            for (int j = 0; j < m; ++j) {
+                Pack<S, V> t = ldv<S, V>(tile + ot + (size_t)j * W);
+                const Pack<S, V> q = ldv<S, V>(uj + ob + (size_t)j * kSZ);
+#pragma unroll
+                for (int i = 0; i < V; ++i) t.v[i] = t.v[i] * q.v[i];
+                stv<S, V>(tile + ot + (size_t)j * W, t);
+            }
         }
         __syncthreads();
         int unsafe = 0;
-        Pack<A, 1> hb[2], ha[2];
-        if (!failed) read_halo<Tr, 1, false>(op, TileView<S>{tile, 0, n, nullptr}, xs, k, c, hb, ha, unsafe);
+        Pack<A, V> hb[2], ha[2];
+        if (!failed) read_halo<Tr, V, false>(op, TileView<S>{tile, 0, n, nullptr}, xs, k, c, hb, ha, unsafe);
         __syncthreads();
         if (failed) {
             for (int q = threadIdx.x; q < P; q += blockDim.x) mbar_wait(&bars[q], par);
             if (threadIdx.x == 0) record_timeout();
             return;
         }
-        group_sweep<Tr, 1, 0>(op, tile, xs, ends, k, c, hb, ha, unsafe);
+        group_sweep<Tr, V, 0>(op, tile, xs, ends, k, c, hb, ha, unsafe);
         // epilogue on this thread's rows (the sweep leaves them in the tile)
         if (o == 0) {
             const A h = A(-0.5);
 #pragma unroll 4
-            for (int j = 0; j < m; ++j)
-                out[ob + (size_t)j * kSZ] = h * __ldg(uj + ob + (size_t)j * kSZ) * A(tile[ot + (size_t)j * W]);
+            for (int j = 0; j < m; ++j) {
+                const Pack<S, V> r = ldv<S, V>(tile + ot + (size_t)j * W);
+                const Pack<S, V> q = ldv<S, V>(uj + ob + (size_t)j * kSZ);
+                Pack<S, V> x;
+#pragma unroll
+                for (int i = 0; i < V; ++i) x.v[i] = S(h * A(q.v[i]) * A(r.v[i]));
+                stv<S, V>(out + ob + (size_t)j * kSZ, x);
+            }
         } else {
             const A wgt = (o == 1) ? A(-0.5) : A(ta.nu);
 #pragma unroll 4
             for (int j = 0; j < m; ++j) {
+                const Pack<S, V> r = ldv<S, V>(tile + ot + (size_t)j * W);
                 S *po = out + ob + (size_t)j * kSZ;
-                *po = mad(wgt, A(tile[ot + (size_t)j * W]), A(*po));
+                Pack<S, V> x = ldv<S, V>(po);
+#pragma unroll
+                for (int i = 0; i < V; ++i) x.v[i] = S(mad(wgt, A(r.v[i]), A(x.v[i])));
+                stv<S, V>(po, x);
             }
         }
         // every thread is done with the tile, the scratch rows and `ends` before the next
@@ -1404,17 +1420,32 @@ tds_status launch_resident_multi(const tds_plan *const *plans, const int *which,
 }
 
 namespace {
-template <typename Tr>
-tds_status launch_transport_t(const TransportArgs &ta, const MultiMaps &mm, const void *ui, const void *uj,
+template <typename Tr, int V>
+tds_status launch_transport_v(const TransportArgs &ta, const MultiMaps &mm, const void *ui, const void *uj,
                               void *out, int smem, cudaStream_t st) {
     using S = typename Tr::S;
-    auto kern = k_resident_transport<Tr>;
+    auto kern = k_resident_transport<Tr, V>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return TDS_ERR_CUDA;
     const unsigned grid = (unsigned)((long long)ta.op1.ngroups * (kSZ / Tr::W));
-    kern<<<grid, ta.op1.P * Tr::W, smem, st>>>(ta, mm, static_cast<const S *>(ui), static_cast<const S *>(uj),
-                                                static_cast<S *>(out));
+    kern<<<grid, ta.op1.P * Tr::W / V, smem, st>>>(ta, mm, static_cast<const S *>(ui), static_cast<const S *>(uj),
+                                                    static_cast<S *>(out));
     return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
+}
+
+// lanes: lines per thread as in launch_resident (whole-group CTAs only: FP32 1, 2 or 4, FP64 1
+// or 2); a CTA keeps at least one warp
+template <typename Tr>
+tds_status launch_transport_t(const TransportArgs &ta, const MultiMaps &mm, const void *ui, const void *uj,
+                              void *out, int smem, int lanes, cudaStream_t st) {
+    if constexpr (Tr::W == kSZ) {
+        const int threads = ta.op1.P * Tr::W;
+        if constexpr (sizeof(typename Tr::S) == 4) {
+            if (lanes == 4 && threads / 4 >= 32) return launch_transport_v<Tr, 4>(ta, mm, ui, uj, out, smem, st);
+        }
+        if (lanes >= 2 && threads / 2 >= 32) return launch_transport_v<Tr, 2>(ta, mm, ui, uj, out, smem, st);
+    }
+    return launch_transport_v<Tr, 1>(ta, mm, ui, uj, out, smem, st);
 }
 } // namespace
 
@@ -1431,14 +1462,14 @@ tds_status launch_resident_transport(const tds_plan *d1, const tds_plan *d2, con
     if (d1->width < kSZ &&
         !encode_rows(&mm.in, ui, d1->dtype, (long long)d1->n * (d1->nlines / kSZ), d1->width, d1->box_rows))
         return TDS_ERR_CUDA;
-    const int W = d1->width, smem = d1->resident_smem;
+    const int W = d1->width, smem = d1->resident_smem, L = d1->lanes;
     if (d1->dtype == TDS_F64)
-        return W == 16 ? launch_transport_t<TrF64w<16>>(ta, mm, ui, uj, out, smem, st)
-             : W == 8  ? launch_transport_t<TrF64w<8>>(ta, mm, ui, uj, out, smem, st)
-                       : launch_transport_t<TrF64>(ta, mm, ui, uj, out, smem, st);
-    return W == 16 ? launch_transport_t<TrF32w<16>>(ta, mm, ui, uj, out, smem, st)
-         : W == 8  ? launch_transport_t<TrF32w<8>>(ta, mm, ui, uj, out, smem, st)
-                   : launch_transport_t<TrF32>(ta, mm, ui, uj, out, smem, st);
+        return W == 16 ? launch_transport_t<TrF64w<16>>(ta, mm, ui, uj, out, smem, L, st)
+             : W == 8  ? launch_transport_t<TrF64w<8>>(ta, mm, ui, uj, out, smem, L, st)
+                       : launch_transport_t<TrF64>(ta, mm, ui, uj, out, smem, L, st);
+    return W == 16 ? launch_transport_t<TrF32w<16>>(ta, mm, ui, uj, out, smem, L, st)
+         : W == 8  ? launch_transport_t<TrF32w<8>>(ta, mm, ui, uj, out, smem, L, st)
+                   : launch_transport_t<TrF32>(ta, mm, ui, uj, out, smem, L, st);
 }
 
 namespace {
