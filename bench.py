@@ -761,7 +761,7 @@ def run_reference(args, rank, world):
             # bounded: a worker that died would otherwise leave the map waiting for ever
             return sum(pool.map_async(_oracle_step_worker, tasks).get(timeout=600))
         for k in range(args.warmup):
-            step(-1 - k)
+            step(args.steps + k)   # seeds apart from the timed steps
         t = time.perf_counter()
         pts = 0
         for k in range(args.steps):
