@@ -8,7 +8,9 @@
 //   forward  : stencil right-hand side fused into the modified-Thomas forward elimination
 //              (Algorithm 5), in place, accumulating the back-swept row 1 as S = sum pi_j d_j
 //              so that row 0 is decoupled without a separate backward pass; rows whose folded
-//              coefficients have converged take them from registers;
+//              coefficients have converged take them from registers; the uniform interior
+//              stencil has one of four forms (antisymmetric, symmetric, and the two half-point
+//              forms of the mid-point interpolation and its transpose);
 //   reduced  : the chunk-end system in FP64 (communication phase; decoupled 2x2 boundary
 //              systems when the couplings they ignore are below 2^-64, else the full system);
 //   back-substitution: u_{m-1} = L, u_j = d_j - s^a_j F - s^c_j u_{j+1}, u_0 = F -- the
@@ -19,7 +21,8 @@
 //              (identity right-hand side, the back-substitution written as the output);
 //   output   : FP32 tiles leave with TMA stores; FP64 tiles with per-thread stores.
 // Also here: the persistent pipelined variant, the fused pass over several operators of one
-// input, and the SEGMENTED kernels for lines no CTA can hold.
+// input, the fused term group of the transport equation (three sweeps and their combination),
+// and the SEGMENTED kernels for lines no CTA can hold.
 //
 // The sweep is written once over storage/arithmetic traits (FP32, FP64).
 #include <cstring>
