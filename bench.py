@@ -89,17 +89,24 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def file_hash(path):
-    with open(path, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:12]
+def code_fingerprint(path):
+    """sha256[:12] of a C/C++/CUDA source with its comments and whitespace removed: the counters
+    of a capture stay valid across edits that do not touch the code."""
+    import re
+    with open(path) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    text = re.sub(r"\s+", "", text)
+    return hashlib.sha256(text.encode()).hexdigest()[:12]
 
 
 def traffic_from_profiles(kernel_key):
-    """DRAM bytes per launch from profiles/traffic.txt: lines '<key> <bytes> <src-hash>'.
-    None if absent or if the kernel source changed since the capture."""
+    """DRAM bytes per launch from profiles/traffic.txt: lines '<key> <bytes> <code fingerprint>'.
+    None if absent or if the kernel code changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
-        cur = file_hash(KERNEL_SRC)
+        cur = code_fingerprint(KERNEL_SRC)
         with open(path) as fh:
             for line in fh:
                 parts = line.split()
