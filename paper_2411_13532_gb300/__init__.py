@@ -377,6 +377,54 @@ class TransportRHS:
             fn()
         return out
 
+    def call_host(self, host_u, host_out, nu, u, out, stream=None):
+        """One evaluation from pinned host memory to pinned host memory, the copies overlapped
+        with the kernels: component i is copied in on an input stream and its x term group starts
+        as soon as it has landed (i = 0, 1, 2 in turn); each result is copied out on an output
+        stream as soon as its last accumulation (the z group) is done.  ``u`` / ``out`` are the
+        device buffers (x layout).  Ordered on ``stream`` (default: the current stream): the call
+        returns at once, and the host results are complete once that stream has reached the end
+        of the call."""
+        if len(host_u) != 3 or len(host_out) != 3 or len(u) != 3 or len(out) != 3:
+            raise ValueError("three velocity components in and three results out")
+        for h in list(host_u) + list(host_out):
+            if h.is_cuda or not h.is_pinned() or h.dtype != self.dtype or h.numel() != self.d1["x"].numel:
+                raise ValueError("host buffers must be pinned CPU tensors of the field's dtype and size")
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if not hasattr(self, "_copy_in"):
+            self._copy_in = torch.cuda.Stream(self.device)
+            self._copy_out = torch.cuda.Stream(self.device)
+        cin, cout = self._copy_in, self._copy_out
+        start = torch.cuda.Event()
+        start.record(st)
+        landed = []
+        with torch.cuda.stream(cin):
+            cin.wait_event(start)              # the device inputs are free to overwrite
+            for h, d in zip(host_u, u):
+                d.copy_(h, non_blocking=True)
+                d.record_stream(cin)
+                e = torch.cuda.Event()
+                e.record(cin)
+                landed.append(e)
+        steps = self.launch_list(u, nu, out, st)
+        done = 0
+        for idx, (label, fn) in enumerate(steps):
+            if label == "term/x":              # x group i needs components i and 0
+                st.wait_event(landed[idx])
+            fn()
+            if label == "reorder_add/z-x":     # result `done` is final
+                e = torch.cuda.Event()
+                e.record(st)
+                with torch.cuda.stream(cout):
+                    cout.wait_event(e)
+                    host_out[done].copy_(out[done], non_blocking=True)
+                    out[done].record_stream(cout)
+                done += 1
+        fin = torch.cuda.Event()
+        fin.record(cout)
+        st.wait_event(fin)                     # the call is ordered on `stream`
+        return host_out
+
 
 def device_status():
     """Read and clear the device-side status word (0 = no bounded wait gave up)."""
