@@ -78,6 +78,10 @@ def parse():
                     help="time the momentum-transport right-hand side (Sec. 5) instead of the "
                          "derivative step: one JSON line")
     ap.add_argument("--nu", type=float, default=1e-3)
+    ap.add_argument("--nsweep", action="store_true",
+                    help="the single-rank sweep over the line length n = 32..8192 (one JSON line per "
+                         "case): first derivative along x, 2^30 points, P = 1 and 8, FP64 and FP32, "
+                         "against a device copy of the same bytes")
     return ap.parse_args()
 
 
@@ -500,6 +504,63 @@ def run_sweep(args):
         raise RuntimeError("device status after the sweep")
 
 
+# ----------------------------------------------------------- line-length sweep (single rank)
+
+def run_nsweep(args):
+    """The paper's single-rank sweep (Sec. 5: runtime against line length, normalised by a STREAM
+    copy) on one GB300: D1 along x on 2^30 points cut into lines of n = 32..8192, P = 1 (one rank)
+    and P = 8, FP64 and FP32; each time is the median of 5 launches with a 2x-L2 write between
+    them, beside a device-to-device copy of the same bytes (the copy stand-in)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_13532_gb300 as tds
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(2 * 135 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    peaks, kind = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    total = 2 ** 30
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(5):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    for dname, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        x = (torch.rand(total, dtype=dt, device=dev) - 0.5) * 2
+        y = torch.empty_like(x)
+        copy_ms = timed(lambda: y.copy_(x))
+        for n in (32, 64, 128, 256, 512, 1024, 2048, 4096, 8192):
+            shape = (total // (n * 1024), 1024, n)
+            for P in (1, 8):
+                plan = tds.Plan(shape, "x", 1, "periodic", P=P, dtype=dt)
+                ws = plan.workspace()
+                ms = timed(lambda: plan.deriv(x, y, ws))
+                gbs = 2 * x.element_size() * total / (ms * 1e-3) / 1e9
+                print(json.dumps({"sweep": "line length", "dtype": dname, "n": n, "lines": total // n, "P": P,
+                                  "variant": plan.variant, "width": plan.width, "ms": round(ms, 4),
+                                  "gpoints_s": round(total / (ms * 1e-3) / 1e9, 2),
+                                  "alg_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                                  "copy_ms": round(copy_ms, 4), "time_over_copy": round(ms / copy_ms, 3),
+                                  "peak_source": kind}), flush=True)
+                del plan, ws
+        del x, y
+        torch.cuda.empty_cache()
+    if tds.device_status() != 0:
+        raise RuntimeError("device status after the line-length sweep")
+
+
 # ------------------------------------------------------------------ transport right-hand side
 
 # Field transfers (reads + writes of one N^3 field) per evaluation, Table transport's counting:
@@ -800,6 +861,9 @@ def main():
         return
     if args.transport:
         run_transport(args)
+        return
+    if args.nsweep:
+        run_nsweep(args)
         return
     if world > 1:
         import torch

@@ -150,13 +150,13 @@ TDS_API tds_status tds_plan_create_band(tds_plan **out, int nx, int ny, int nz, 
 /* Choose the kernel pipeline of a plan (tuning and test hook; call before first use, not
  * concurrently with a call that uses the plan).  TDS_ERR_ARG if the plan cannot run the
  * requested variant (a resident group larger than one CTA's shared memory).  AUTO picks
- * RESIDENT when the lines fit in a CTA (P <= 16) unless, in FP64, its CTAs would leave fewer
- * than 6 warps per SM (few chunks, large tiles) while the chunk splits into at least two
- * segments; then
- * SEGMENTED (segments of 64 up to the cap, 128 rows FP64 / 256 FP32, dividing the chunk length);
- * else STREAMING.  The
- * adjoint of a SEGMENTED plan runs on the segment partition on periodic lines, else resident
- * when the lines fit in a CTA, else through the streaming pipeline. */
+ * RESIDENT when the lines fit in a CTA (one thread per line and chunk, at most 512 per CTA)
+ * unless, in FP64, its CTAs would leave fewer than 6 warps per SM (few chunks, large tiles)
+ * while the chunk splits into at least two segments; then SEGMENTED (segments of 64 up to the
+ * cap, 128 rows FP64 / 256 FP32, dividing the chunk length); else STREAMING.  An FP32 RESIDENT
+ * choice may run on finer chunks (tds_plan_run_chunks).  The adjoint of a SEGMENTED plan runs
+ * on the segment partition on periodic lines, else resident when the lines fit in a CTA, else
+ * through the streaming pipeline. */
 TDS_API tds_status tds_plan_set_variant(tds_plan *plan, tds_variant variant);
 
 /* Lines of a group held by one CTA of the RESIDENT variant: 32 (the whole group, one bulk
@@ -165,7 +165,7 @@ TDS_API tds_status tds_plan_set_variant(tds_plan *plan, tds_variant variant);
  * A layout choice only: every width gives the same result.  tds_plan_create picks the largest
  * width that lets two CTAs share an SM.  TDS_ERR_ARG when the width is not 32, 16 or 8, the tile
  * does not fit in one CTA's shared memory, fewer than two warps would remain per CTA (widths
- * below 32), or the plan cannot run resident (P > 16).  Not part of the method (Sec. 4.1 fixes
+ * below 32), or the plan cannot run resident (more than 512 threads: P x lines > 512).  Not part of the method (Sec. 4.1 fixes
  * the 32-line group; its split over CTAs is a GPU layout decision). */
 TDS_API tds_status tds_plan_set_width(tds_plan *plan, int lines);
 
@@ -176,6 +176,15 @@ TDS_API tds_status tds_plan_set_width(tds_plan *plan, int lines);
 TDS_API tds_status tds_plan_info(const tds_plan *plan, int *n, int *nlines, int *P, int *variant,
                          int *smem_bytes);
 TDS_API tds_status tds_plan_width(const tds_plan *plan, int *lines);
+
+/* tds_plan_run_chunks -- the chunks per line the plan's kernels run with: P, or P x 2^k when the
+ * AUTO variant of an FP32 plan (EXACT mode, no band) found that one-warp-per-chunk resident CTAs
+ * would leave fewer than 8 warps per SM and runs the same operator on finer chunks of at least 64
+ * rows instead (results equal to rounding: the reduced system over all chunk ends is solved
+ * exactly; the partition is not part of the method's result).  A variant or width set by the
+ * caller runs on the plan's own P chunks.  tds_plan_info and tds_plan_width describe the kernels
+ * that run. */
+TDS_API tds_status tds_plan_run_chunks(const tds_plan *plan, int *chunks);
 
 /* Bytes of device workspace tds_deriv / tds_deriv_adjoint need with this plan (0 is
  * possible).  The workspace must be 256-byte aligned; its contents need no initialisation

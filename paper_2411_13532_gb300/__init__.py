@@ -112,6 +112,8 @@ class Plan:
         w_ = ctypes.c_int()
         _lib.check(L.tds_plan_width(h_, ctypes.byref(w_)), "tds_plan_width")
         self.width = w_.value   # lines per resident CTA (0: cannot run resident)
+        _lib.check(L.tds_plan_run_chunks(h_, ctypes.byref(w_)), "tds_plan_run_chunks")
+        self.run_chunks = w_.value   # chunks per line the kernels run with (P, or finer under AUTO)
         self.numel = nx * ny * nz
 
     def __del__(self):

@@ -28,6 +28,7 @@ SIGNATURES = [
     ("tds_plan_set_width", _i, [_vp, _i]),
     ("tds_plan_info", _i, [_vp, _ip, _ip, _ip, _ip, _ip]),
     ("tds_plan_width", _i, [_vp, _ip]),
+    ("tds_plan_run_chunks", _i, [_vp, _ip]),
     ("tds_workspace_bytes", _i, [_vp, ctypes.POINTER(_sz)]),
     ("tds_deriv", _i, [_vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_deriv_adjoint", _i, [_vp, _vp, _vp, _vp, _sz, _vp]),

@@ -23,6 +23,7 @@ bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p
 size_t elem_size(tds_dtype dt) { return dt == TDS_F64 ? 8 : 4; }
 
 size_t ws_need(const tds_plan *p) {
+    if (p->sub) return ws_need(p->sub);
     if (p->variant == TDS_VARIANT_STREAMING) return streaming_ws_bytes(p);
     if (p->variant == TDS_VARIANT_SEGMENTED) {
         // the adjoint of a segmented plan runs the streaming pipeline
@@ -32,12 +33,23 @@ size_t ws_need(const tds_plan *p) {
     return 0;
 }
 
+// The plan whose kernels run for p: its finer-chunk plan when AUTO chose one (see make_sub).
+const tds_plan *eff(const tds_plan *p) { return (p && p->sub) ? p->sub : p; }
+
+// Warps per SM that the plan's resident CTAs leave (one line per thread): CTAs per SM by shared
+// memory times warps per CTA.
+int resident_warps_per_sm(const tds_plan *p) {
+    if (!p->resident_smem) return 0;
+    const int ctas = (int)((size_t)p->smem_sm / ((size_t)p->resident_smem + 1024));
+    return ctas * (p->P * p->width / 32);
+}
+
 // Whether the resident kernel can run with w lines per CTA; two: and leave room for a second CTA
 // on the SM.  Below 32 lines a CTA keeps at least two warps, its rows move as TMA tensor boxes
 // (row coordinates below 2^31, 128-byte aligned box destinations).
 bool resident_width_ok(const tds_plan *p, int w, bool two) {
     if (w != 32 && w != 16 && w != 8) return false;
-    if (p->P > kMaxResidentP) return false;
+    if ((long long)p->P * w > kMaxResidentP * kSZ) return false;   // one thread per line and chunk
     const size_t sm = resident_smem_bytes(p->n, p->P, p->dtype, w);
     if (sm > (size_t)p->smem_optin) return false;
     if (two && 2 * (sm + 1024) > (size_t)p->smem_sm) return false;
@@ -89,6 +101,7 @@ tds_status check_call(const tds_plan *p, const void *in, const void *out, const 
 // The plan's variant on device buffers (arguments already checked).  which: 0 the derivative,
 // 1 its adjoint, 2 the solve alone (resident when the lines fit a CTA, else streaming).
 tds_status launch(const tds_plan *p, int which, const void *in, void *out, void *ws, cudaStream_t st) {
+    if (p->sub) return launch(p->sub, which, in, out, ws, st);
     if (which == 2) {
         if (p->variant != TDS_VARIANT_STREAMING && p->resident_smem) return launch_resident(p, 2, in, out, st);
         return launch_streaming(p, 2, in, out, ws, st);
@@ -116,7 +129,8 @@ tds_status run(const tds_plan *p, int which, const void *in, void *out, void *ws
 // Groups are independent and contiguous (group g occupies elements [g n 32, (g+1) n 32)), so
 // the slab runs on the buffers offset by g0 n 32 elements.
 tds_plan slab_of(const tds_plan *p, int g0, int g1) {
-    tds_plan q = *p;
+    tds_plan q = *eff(p);
+    q.sub = nullptr;
     q.nlines = (g1 - g0) * kSZ;
     for (DevOp *o : {&q.op[0], &q.op[1], &q.op[2], &q.seg, &q.seg_adj}) {
         o->nlines = q.nlines;
@@ -252,6 +266,33 @@ tds_status finish_plan(tds_plan *p, tds_plan **out) {
     return TDS_OK;
 }
 
+// AUTO, FP32: when the plan's resident CTAs would leave fewer than 8 warps per SM (long chunks:
+// one warp per chunk and few CTAs per SM, e.g. P = 1 with 512- or 1024-point lines), the same
+// operator on finer chunks, P x 2^k (chunks of at least 64 rows), runs in its place.  The result
+// is the same to rounding: the reduced system over all chunk ends is solved exactly (EXACT mode
+// only; the paper-drop approximation depends on the chunks).  Measured, FP32 D1 on 2^30 points:
+// n = 512, P = 1: 0.60 -> 0.91 of the copy rate; n = 1024, P = 1: 0.26 -> 0.82.
+void make_sub(tds_plan *p) {
+    if (p->sub) { tds_plan_destroy(p->sub); p->sub = nullptr; }
+    if (p->is_sub || p->dtype != TDS_F32 || p->mode != TDS_REDUCED_EXACT || p->band ||
+        p->variant != TDS_VARIANT_RESIDENT || resident_warps_per_sm(p) >= 8)
+        return;
+    for (int s = 2; p->m % s == 0 && p->m / s >= 64 && p->P * s * 8 <= kMaxResidentP * kSZ; s *= 2) {
+        tds_plan *c = new_plan(p->nx, p->ny, p->nz, p->dir, p->bc, p->P * s, p->dtype, p->mode);
+        if (!c) return;
+        c->order = p->order;
+        c->h = p->h;
+        c->is_sub = true;
+        tds_plan *done = nullptr;
+        if (finish_plan(c, &done) != TDS_OK) return;   // finish_plan destroyed c
+        if (done->variant == TDS_VARIANT_RESIDENT && resident_warps_per_sm(done) >= 8) {
+            p->sub = done;
+            return;
+        }
+        tds_plan_destroy(done);
+    }
+}
+
 
 } // namespace
 
@@ -367,6 +408,7 @@ tds_status tds_plan_create_band(tds_plan **out, int nx, int ny, int nz, tds_dir 
 
 tds_status tds_plan_set_variant(tds_plan *p, tds_variant v) {
     if (!p) return TDS_ERR_ARG;
+    const bool autov = (v == TDS_VARIANT_AUTO);
     if (v == TDS_VARIANT_AUTO) {
         // resident unless, for FP64 sweeps (bound by the FP64 pipe, which needs warps), its CTAs
         // would leave fewer than 6 warps per SM (few chunks, large tiles) while the lines split
@@ -390,11 +432,22 @@ tds_status tds_plan_set_variant(tds_plan *p, tds_variant v) {
         v != TDS_VARIANT_SEGMENTED)
         return TDS_ERR_ARG;
     p->variant = v;
+    // AUTO may hand the work to finer chunks; a variant the caller fixes runs on the plan's own
+    if (autov) {
+        make_sub(p);
+    } else if (p->sub) {
+        tds_plan_destroy(p->sub);
+        p->sub = nullptr;
+    }
     return TDS_OK;
 }
 
 tds_status tds_plan_set_width(tds_plan *p, int lines) {
     if (!p || !resident_width_ok(p, lines, false)) return TDS_ERR_ARG;
+    if (p->sub) {   // a width the caller fixes applies to the plan's own chunks
+        tds_plan_destroy(p->sub);
+        p->sub = nullptr;
+    }
     p->width = lines;
     p->resident_smem = (int)resident_smem_bytes(p->n, p->P, p->dtype, lines);
     p->box_rows = resident_box_rows(p->n, p->m, p->dtype, lines);
@@ -402,11 +455,12 @@ tds_status tds_plan_set_width(tds_plan *p, int lines) {
     return TDS_OK;
 }
 
-tds_status tds_plan_info(const tds_plan *p, int *n, int *nlines, int *P, int *variant, int *smem) {
-    if (!p) return TDS_ERR_ARG;
-    if (n) *n = p->n;
-    if (nlines) *nlines = p->nlines;
-    if (P) *P = p->P;
+tds_status tds_plan_info(const tds_plan *q, int *n, int *nlines, int *P, int *variant, int *smem) {
+    if (!q) return TDS_ERR_ARG;
+    if (n) *n = q->n;
+    if (nlines) *nlines = q->nlines;
+    if (P) *P = q->P;
+    const tds_plan *p = eff(q);   // the kernels that run
     if (variant) *variant = (int)p->variant;
     if (smem)
         *smem = p->variant == TDS_VARIANT_RESIDENT ? p->resident_smem
@@ -415,9 +469,15 @@ tds_status tds_plan_info(const tds_plan *p, int *n, int *nlines, int *P, int *va
     return TDS_OK;
 }
 
+tds_status tds_plan_run_chunks(const tds_plan *p, int *chunks) {
+    if (!p || !chunks) return TDS_ERR_ARG;
+    *chunks = eff(p)->P;
+    return TDS_OK;
+}
+
 tds_status tds_plan_width(const tds_plan *p, int *lines) {
     if (!p || !lines) return TDS_ERR_ARG;
-    *lines = p->width;
+    *lines = eff(p)->width;
     return TDS_OK;
 }
 
@@ -444,13 +504,18 @@ tds_status tds_solve(const tds_plan *p, const void *d, void *x, void *ws, size_t
 tds_status tds_deriv_multi(int count, const tds_plan *const *plans, const int *adjoint, const void *in,
                            void *const *outs, void *ws, size_t ws_bytes, void *stream) {
     if (count < 1 || count > kMaxMulti || !plans || !adjoint || !outs) return TDS_ERR_ARG;
-    const tds_plan *p0 = plans[0];
-    if (!p0) return TDS_ERR_ARG;
+    if (!plans[0]) return TDS_ERR_ARG;
+    const tds_plan *run_plans[kMaxMulti];   // the plans whose kernels run
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i]) return TDS_ERR_ARG;
+        run_plans[i] = eff(plans[i]);
+    }
+    const tds_plan *p0 = run_plans[0];
     const size_t bytes = (size_t)p0->n * p0->nlines * elem_size(p0->dtype);
     int which[kMaxMulti];
     bool fused = true;
     for (int i = 0; i < count; ++i) {
-        const tds_plan *p = plans[i];
+        const tds_plan *p = run_plans[i];
         if (!p || p->band || (adjoint[i] != 0 && adjoint[i] != 1)) return TDS_ERR_ARG;
         which[i] = adjoint[i];
         // every operator maps the same field shape in the same direction layout
@@ -466,9 +531,9 @@ tds_status tds_deriv_multi(int count, const tds_plan *const *plans, const int *a
                 p->width == p0->width && p->op[which[i]].adjoint == 0;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (fused) return launch_resident_multi(plans, which, count, in, outs, st);
+    if (fused) return launch_resident_multi(run_plans, which, count, in, outs, st);
     for (int i = 0; i < count; ++i) {
-        const tds_status s = launch(plans[i], which[i], in, outs[i], ws, st);
+        const tds_status s = launch(run_plans[i], which[i], in, outs[i], ws, st);
         if (s != TDS_OK) return s;
     }
     return TDS_OK;
@@ -478,6 +543,8 @@ tds_status tds_transport(const tds_plan *d1, const tds_plan *d2, const void *ui,
                          void *out, void *stream) {
     if (!d1 || !d2 || !ui || !uj || !out || d1->band || d2->band || d1->order != 1 || d2->order != 2)
         return TDS_ERR_ARG;
+    d1 = eff(d1);   // the plans whose kernels run
+    d2 = eff(d2);
     // one geometry: the same field in the same direction layout, cut the same way
     if (d1->nx != d2->nx || d1->ny != d2->ny || d1->nz != d2->nz || d1->dir != d2->dir ||
         d1->dtype != d2->dtype || d1->P != d2->P || d1->width != d2->width)
@@ -532,6 +599,7 @@ tds_status tds_reorder_add(const void *in, void *out, int nx, int ny, int nz, td
 
 void tds_plan_destroy(tds_plan *p) {
     if (!p) return;
+    tds_plan_destroy(p->sub);
     std::free(p->band);
     for (cudaEvent_t e : p->ev)
         if (e) cudaEventDestroy(e);

@@ -13,7 +13,8 @@ namespace tds {
 constexpr int kSZ = 32;           // lines per group: one warp lane per line (Sec. 4.1, SZ=32)
 constexpr int kTaps = 7;          // stencil offsets -3..3 (closure rows reach 3 points in)
 constexpr int kEdgeRows = 4;      // closed lines: rows 0..3 and n-4..n-1 carry their own taps
-constexpr int kMaxResidentP = 16; // resident kernel: one warp per chunk, at most 16 warps
+constexpr int kMaxResidentP = 16; // resident kernels: at most 16 x 32 = 512 threads per CTA (one per
+                                   // line and chunk: P x lines <= 512)
 constexpr int kHostSlabs = 8;     // host entry points: copies and compute pipelined over 8 slabs
 constexpr int kMaxMulti = 4;      // operators one fused pass (tds_deriv_multi) may compute
 
@@ -116,6 +117,9 @@ struct tds_plan {
     cudaStream_t copy_in, copy_out;
     cudaEvent_t ev[2 + 2 * tds::kHostSlabs];
     double *band;          // band plan: the caller's band of A (a, b, c; 3 x n), else NULL
+    tds_plan *sub;         // AUTO, FP32: the same operator on finer chunks (P x 2^k), run in this
+                           // plan's place when this plan's resident CTAs would be too thin; NULL
+    bool is_sub;           // this plan is another plan's `sub` (it gets none of its own)
     void *dmem;            // one device allocation holding every array of both operators
     void *hmem;            // host copies (reduced coefficients)
 };

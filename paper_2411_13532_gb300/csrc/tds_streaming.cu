@@ -1,5 +1,5 @@
 // tds_streaming.cu -- the three-kernel DistD2 pipeline through global memory (Sec. 4.2), for
-// lines no resident CTA can hold and segments cannot split (or P > 16): decoupling
+// lines no resident CTA can hold and segments cannot split (or P x 8 > 512): decoupling
 // (Algorithm 5) writes the intermediate to `out` and the chunk ends to the workspace, the
 // reduced chunk-end system is solved one thread per line in FP64, and the substitution
 // (Algorithm 6) finishes `out` in place.  This is the paper's own phase order (backward pass

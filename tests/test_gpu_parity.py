@@ -616,3 +616,37 @@ def test_device_wait_timeout_is_reported_and_context_survives():
     y = tds.Plan(shape, "x", 1, "periodic", P=2).deriv(to_device_layout(cart, "x", "f64"))
     mx, _ = rel_errors(from_device_layout(y, "x", shape), oracle.deriv(cart, "x", 1, "periodic"))
     assert mx <= 1e-12
+
+
+@pytest.mark.parametrize("n", [256, 512, 1024])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+def test_fp32_thin_plans_run_on_finer_chunks(n, bc):
+    """AUTO FP32 plans whose one-warp-per-chunk CTAs would be thin run on finer chunks: the same
+    operator to rounding.  Every point against the oracle (derivative, adjoint, solve, host entry
+    point, fused pass), and a fixed variant keeps the plan's own chunks."""
+    shape = (2, 32, n)
+    cart = np.random.default_rng(n).uniform(-1, 1, shape).astype(np.float32).astype(np.float64)
+    h = oracle.grid_spacing(n, bc)
+    auto = tds.Plan(shape, "x", 1, bc, P=1, h=h, dtype=torch.float32)
+    fixed = tds.Plan(shape, "x", 1, bc, P=1, h=h, dtype=torch.float32, variant="resident")
+    assert auto.variant == "resident" and auto.run_chunks > 1 and fixed.run_chunks == 1
+    assert auto.P == 1
+    x = to_device_layout(cart, "x", "f32")
+    for plan in (auto, fixed):
+        mx, _ = rel_errors(from_device_layout(plan.deriv(x), "x", shape), oracle.deriv(cart, "x", 1, bc, h))
+        assert mx <= TOL["f32"], (plan.run_chunks, mx)
+        mx, _ = rel_errors(from_device_layout(plan.adjoint(x), "x", shape),
+                           oracle.deriv_adjoint(cart, "x", 1, bc, h))
+        assert mx <= TOL["f32"], (plan.run_chunks, "adjoint", mx)
+        lines = oracle.lines_view(cart, "x")
+        ref = oracle.from_lines_view(oracle_solve_lines(lines, 1, bc, h), "x", shape)
+        mx, _ = rel_errors(from_device_layout(plan.solve(x), "x", shape), ref)
+        assert mx <= TOL["f32"], (plan.run_chunks, "solve", mx)
+    # host entry point and fused pass run the finer chunks too (bitwise the device call)
+    host_out = torch.empty(auto.numel, dtype=torch.float32).pin_memory()
+    auto.deriv_host(x.cpu().pin_memory(), host_out, torch.empty_like(x), torch.empty_like(x))
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(host_out, auto.deriv(x).cpu())
+    d2 = tds.Plan(shape, "x", 2, bc, P=1, h=h, dtype=torch.float32)
+    outs = tds.deriv_multi([(auto, False), (d2, False)], x)
+    assert torch.equal(outs[0], auto.deriv(x)) and torch.equal(outs[1], d2.deriv(x))

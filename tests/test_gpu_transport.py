@@ -238,3 +238,17 @@ def test_transport_rhs_host_entry_matches_device_call(dtype):
             assert torch.equal(a, b)
     with pytest.raises(ValueError):
         rhs.call_host([torch.empty(5)] * 3, ho, NU, ud, od)
+
+
+def test_transport_rhs_fp32_with_finer_chunk_plans():
+    """FP32 x lines of 512 points with P = 1 run on finer chunks (AUTO); the transport term
+    kernel follows the plans' choice: every point against the oracle."""
+    shape = (8, 32, 512)
+    rhs = tds.TransportRHS(shape, P=(1, 1, 2), dtype=torch.float32)
+    assert rhs.d1["x"].run_chunks > 1 and rhs.d1["x"].run_chunks == rhs.d2["x"].run_chunks
+    u = rand_fields(shape, 3, "f32", seed=4)
+    out = rhs([to_device_layout(f, "x", "f32") for f in u], NU)
+    ref = oracle.transport_rhs(u, NU, "periodic")
+    for i in range(3):
+        mx, rms = rel_errors(from_device_layout(out[i], "x", shape), ref[i])
+        assert mx <= TOL["f32"], (i, mx, rms)
