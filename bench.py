@@ -453,10 +453,34 @@ def run_sweep(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     flush = torch.empty(2 * 135 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
-    peaks, kind = load_peaks()
+    peaks, peak_kind = load_peaks()
     hbm = float(peaks["hbm_gbs"])
     TD = {"f64": torch.float64, "f32": torch.float32}
     reps = max(args.steps, 5)
+    import numpy as np
+    import oracle
+    oracle.build()
+
+    def oracle_rate(n, order, bc, kind):
+        """The FP64 oracle (one core) on a sample of about 2^21 points of whole lines of this
+        case: points per second."""
+        nl = max(1, 2 ** 21 // n)
+        lines = np.random.default_rng(n).uniform(-1, 1, (nl, n))
+        h = oracle.grid_spacing(n, bc)
+        t = time.perf_counter()
+        if order == "filter":
+            oracle.filter_lines(lines, 0.45, bc)
+        elif order == "interp":
+            oracle.interp_lines(lines)
+        elif kind == "adjoint":
+            oracle.deriv_adjoint_lines(lines, order, bc, h)
+        elif kind == "solve":
+            a, b, c, _ = oracle.bands(n, order, bc, h)
+            for d in lines:
+                oracle.tridiag_solve(a, b, c, d, bc == "periodic")
+        else:
+            oracle.deriv_lines(lines, order, bc, h)
+        return nl * n / (time.perf_counter() - t) / 1e9
     for label, shape, dirs, orders, bcs, Ps, dts, kind in SWEEP_CASES:
         if args.sweep_match not in label:
             continue
@@ -496,7 +520,10 @@ def run_sweep(args):
                                 "dir": direc, "bc": bc, "P": P, "variant": plan.variant, "width": plan.width,
                                 "ms": round(ms, 4), "gpoints_s": round(npts / (ms * 1e-3) / 1e9, 2),
                                 "alg_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
-                                "peak_source": kind}), flush=True)
+                                "hbm_frac_nominal_7900": round(gbs / 7900.0, 4), "peak_source": peak_kind,
+                                "oracle_gpoints_s_1core": round(oracle_rate(shape[{"x": 2, "y": 1, "z": 0}[direc]],
+                                                                            order, bc, kind), 5)}),
+                                  flush=True)
                             del plan, ws
             del x, y
             torch.cuda.empty_cache()
