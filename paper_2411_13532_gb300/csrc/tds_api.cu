@@ -1,5 +1,13 @@
 // tds_api.cu -- the extern "C" entry points of libtds (declared and documented in tds.h):
 // argument and shape validation, variant selection, and the launches.
+//
+// Plan configuration, in finish_plan / tds_plan_set_variant:
+//   width   : lines per resident CTA (32, 16, 8): FP32 the largest, FP64 the smallest that leaves
+//             room for two CTAs per SM;
+//   variant : AUTO = resident when the lines fit a CTA, unless FP64 CTAs would leave < 6 warps per
+//             SM (then segmented); segmented when they do not fit; else streaming;
+//   sub     : AUTO, FP32, resident CTAs with < 8 warps per SM: a finer-chunk copy of the plan runs in
+//             its place (make_sub); every entry point launches through eff(plan).
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
