@@ -152,7 +152,8 @@ TDS_API tds_status tds_plan_create_band(tds_plan **out, int nx, int ny, int nz, 
  * requested variant (a resident group larger than one CTA's shared memory).  AUTO picks
  * RESIDENT when the lines fit in a CTA (one thread per line and chunk, at most 512 per CTA)
  * unless, in FP64, its CTAs would leave fewer than 6 warps per SM (few chunks, large tiles)
- * while the chunk splits into at least two segments; then SEGMENTED (segments of 64 up to the
+ * or, in FP32, the lines need 8-line CTAs, while the chunk splits into at least two segments;
+ * then SEGMENTED (segments of 64 up to the
  * cap, 128 rows FP64 / 256 FP32, dividing the chunk length); else STREAMING.  An FP32 RESIDENT
  * choice may run on finer chunks (tds_plan_run_chunks).  The adjoint of a SEGMENTED plan runs
  * on the segment partition on periodic lines, else resident when the lines fit in a CTA, else

@@ -422,13 +422,17 @@ tds_status tds_plan_set_variant(tds_plan *p, tds_variant v) {
         // would leave fewer than 6 warps per SM (few chunks, large tiles) while the lines split
         // into at least two segments (one warp per segment keeps more warps per SM; measured:
         // 256^3 P = 1, 3 warps per SM, segmented 26 % faster; P = 2, 6 warps per SM, resident
-        // 7 % faster).  FP32 sweeps stay resident: the FP32 segmented variant reads its input
-        // twice.  Then segmented, else streaming.
+        // 7 % faster).  FP32 sweeps stay resident (thin FP32 plans run on finer chunks instead,
+        // make_sub), except lines long enough to need 8-line CTAs (n above ~1800): their
+        // segments read the input ~1.2 times (k_seg_ends), which beats the few, narrow resident
+        // CTAs (measured at n = 2048: 1.52x against 1.73x the time of a copy).  Then segmented,
+        // else streaming.
         bool thin = false;
         if (p->dtype == TDS_F64 && p->resident_smem && p->seg.P >= 2) {
             const int ctas = (int)((size_t)p->smem_sm / ((size_t)p->resident_smem + 1024));
             thin = ctas * (p->P * p->width / 32) < 6;
         }
+        if (p->dtype == TDS_F32 && p->resident_smem && p->width == 8 && p->seg.P >= 2) thin = true;
         v = (p->resident_smem && !thin) ? TDS_VARIANT_RESIDENT
           : p->seg.P ? TDS_VARIANT_SEGMENTED
           : p->resident_smem ? TDS_VARIANT_RESIDENT : TDS_VARIANT_STREAMING;

@@ -323,8 +323,11 @@ def test_segmented_is_chosen_for_long_lines():
     assert tds.Plan((8, 32, 256), "x", 1, "periodic", P=1).variant == "segmented"   # 3 warps / SM
     assert tds.Plan((8, 32, 256), "x", 1, "periodic", P=2).variant == "resident"    # 6 warps / SM
     assert tds.Plan((1, 32, 512), "x", 1, "periodic", P=2).variant == "segmented"   # 2 warps / SM
-    # FP32 stays resident (its segmented variant reads the input twice)
+    # FP32 stays resident (thin plans run on finer chunks) ...
     assert tds.Plan((1, 32, 512), "x", 1, "periodic", P=1, dtype=torch.float32).variant == "resident"
+    # ... unless the lines need 8-line CTAs: segments read the input about 1.2 times
+    assert tds.Plan((1, 32, 2048), "x", 1, "periodic", P=8, dtype=torch.float32).variant == "segmented"
+    assert tds.Plan((1, 32, 1024), "x", 1, "periodic", P=8, dtype=torch.float32).variant == "resident"
     # a single 64-row segment per line: resident
     assert tds.Plan((8, 32, 64), "x", 1, "periodic", P=1).variant == "resident"
     # chunks too short for 64-row segments fall back to streaming
