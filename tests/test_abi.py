@@ -98,6 +98,7 @@ def test_null_pointer_errors_need_no_gpu(L):
     assert L.tds_plan_set_width(None, 32) == _lib.ERR_ARG
     w = ctypes.c_int()
     assert L.tds_plan_width(None, ctypes.byref(w)) == _lib.ERR_ARG
+    assert L.tds_plan_run_chunks(None, ctypes.byref(w)) == _lib.ERR_ARG
     L.tds_plan_destroy(None)
 
 
