@@ -1,8 +1,9 @@
 /*
  * tds.h -- C ABI of the GB300 compact finite-difference derivative library (libtds.so).
  *
- * The library computes batched sixth-order compact finite-difference derivatives along one
- * direction of a 3D field with the DistD2 algorithm (Sec. 4.2 of Akkurt et al., "A
+ * The library computes batched sixth-order compact finite-difference derivatives (and the
+ * tridiagonal solve alone, compact filters and interpolations, and the transport-equation
+ * right-hand side built on them) along one direction of a 3D field with the DistD2 algorithm (Sec. 4.2 of Akkurt et al., "A
  * Distributed-memory Tridiagonal Solver Based on a Specialised Data Structure Optimised for
  * CPU and GPU Architectures"): the stencil right-hand side (Eq. cfds) is fused into a
  * modified-Thomas decoupling sweep over P chunks per line (Algorithm 5), a reduced system
@@ -66,9 +67,9 @@ typedef enum {
     TDS_VARIANT_STREAMING = 2,  /* decouple / reduced / substitute as three kernels         */
     TDS_VARIANT_PIPELINED = 3,  /* persistent CTAs, each sweeping many groups through
                                    several on-chip tile buffers filled ahead by TMA         */
-    TDS_VARIANT_SEGMENTED = 4   /* lines too long for one CTA: segments of 64..256 rows that
-                                   subdivide the chunks, one CTA each, in two kernels (the
-                                   adjoint of such a plan runs STREAMING)                   */
+    TDS_VARIANT_SEGMENTED = 4   /* segments of 64..256 rows that subdivide the chunks, one
+                                   warp each, in two kernels: lines too long for one CTA,
+                                   and plans whose resident CTAs would be too thin          */
 } tds_variant;
 
 typedef struct tds_plan tds_plan;
@@ -153,8 +154,8 @@ TDS_API tds_status tds_plan_create_band(tds_plan **out, int nx, int ny, int nz, 
  * RESIDENT when the lines fit in a CTA (one thread per line and chunk, at most 512 per CTA)
  * unless, in FP64, its CTAs would leave fewer than 6 warps per SM (few chunks, large tiles)
  * or, in FP32, the lines need 8-line CTAs, while the chunk splits into at least two segments;
- * then SEGMENTED (segments of 64 up to the
- * cap, 128 rows FP64 / 256 FP32, dividing the chunk length); else STREAMING.  An FP32 RESIDENT
+ * then SEGMENTED (segments of 64 up to the cap, 128 rows FP64 / 256 FP32, dividing the chunk
+ * length); else STREAMING.  An FP32 RESIDENT
  * choice may run on finer chunks (tds_plan_run_chunks).  The adjoint of a SEGMENTED plan runs
  * on the segment partition on periodic lines, else resident when the lines fit in a CTA, else
  * through the streaming pipeline. */
@@ -163,11 +164,13 @@ TDS_API tds_status tds_plan_set_variant(tds_plan *plan, tds_variant variant);
 /* Lines of a group held by one CTA of the RESIDENT variant: 32 (the whole group, one bulk
  * copy per chunk), 16 or 8 (the group is split over 32/lines CTAs whose rows move as 2-D TMA
  * tensor boxes, so that several CTAs share an SM and one CTA's copies overlap another's sweep).
- * A layout choice only: every width gives the same result.  tds_plan_create picks the largest
- * width that lets two CTAs share an SM.  TDS_ERR_ARG when the width is not 32, 16 or 8, the tile
- * does not fit in one CTA's shared memory, fewer than two warps would remain per CTA (widths
- * below 32), or the plan cannot run resident (more than 512 threads: P x lines > 512).  Not part of the method (Sec. 4.1 fixes
- * the 32-line group; its split over CTAs is a GPU layout decision). */
+ * A layout choice only: every width gives the same result.  tds_plan_create picks, among the
+ * widths that let two CTAs share an SM, the largest for FP32 and the smallest for FP64.
+ * TDS_ERR_ARG when the width is not 32, 16 or 8, the tile does not fit in one CTA's shared
+ * memory, fewer than two warps would remain per CTA (widths below 32), or the CTA would need
+ * more than 512 threads (P x lines > 512).  A width set here also drops the finer chunks of
+ * tds_plan_run_chunks.  Not part of the method (Sec. 4.1 fixes the 32-line group; its split
+ * over CTAs is a GPU layout decision). */
 TDS_API tds_status tds_plan_set_width(tds_plan *plan, int lines);
 
 /* Describe a plan: line length n, lines N, chunks P, the variant it will run, and the
