@@ -930,14 +930,37 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_transport(const
         bool ok = true;
         for (int q = 0; q < P; ++q) ok = mbar_wait(&bars[q], par) && ok;
         if (!ok) atomicExch(&failed, 1);
+        // FP64: the per-thread global accesses below go in batches of kB rows, every load of a
+        // batch issued before its first use (measured 1.5 % faster); FP32 keeps one row at a
+        // time (the batch's registers would cost it a CTA per SM)
+        constexpr int kB = 8;
         if (o == 1 && ok) {
-#pragma unroll 4
-            for (int j = 0; j < m; ++j) {
-                Pack<S, V> t = ldv<S, V>(tile + ot + (size_t)j * W);
-                const Pack<S, V> q = ldv<S, V>(uj + ob + (size_t)j * kSZ);
+            if constexpr (sizeof(S) == 8) {
+                for (int j0 = 0; j0 < m; j0 += kB) {
+                    const int nb = (m - j0 < kB) ? m - j0 : kB;
+                    Pack<S, V> q[kB];
 #pragma unroll
-                for (int i = 0; i < V; ++i) t.v[i] = t.v[i] * q.v[i];
-                stv<S, V>(tile + ot + (size_t)j * W, t);
+                    for (int b = 0; b < kB; ++b)
+                        if (b < nb) q[b] = ldv<S, V>(uj + ob + (size_t)(j0 + b) * kSZ);
+#pragma unroll
+                    for (int b = 0; b < kB; ++b) {
+                        if (b < nb) {
+                            Pack<S, V> t = ldv<S, V>(tile + ot + (size_t)(j0 + b) * W);
+#pragma unroll
+                            for (int i = 0; i < V; ++i) t.v[i] = t.v[i] * q[b].v[i];
+                            stv<S, V>(tile + ot + (size_t)(j0 + b) * W, t);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll 4
+                for (int j = 0; j < m; ++j) {
+                    Pack<S, V> t = ldv<S, V>(tile + ot + (size_t)j * W);
+                    const Pack<S, V> q = ldv<S, V>(uj + ob + (size_t)j * kSZ);
+#pragma unroll
+                    for (int i = 0; i < V; ++i) t.v[i] = t.v[i] * q.v[i];
+                    stv<S, V>(tile + ot + (size_t)j * W, t);
+                }
             }
         }
         __syncthreads();
@@ -951,8 +974,31 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_transport(const
             return;
         }
         group_sweep<Tr, V, 0>(op, tile, xs, ends, k, c, hb, ha, unsafe);
-        // epilogue on this thread's rows (the sweep leaves them in the tile)
-        if (o == 0) {
+        // epilogue on this thread's rows (the sweep leaves them in the tile): o = 0 writes
+        // -1/2 u_j r, the others add their weight times r to what is there
+        if constexpr (sizeof(S) == 8) {
+            const A wgt = (o == 2) ? A(ta.nu) : A(-0.5);
+            const S *srcb = (o == 0) ? uj : out;
+            for (int j0 = 0; j0 < m; j0 += kB) {
+                const int nb = (m - j0 < kB) ? m - j0 : kB;
+                Pack<S, V> q[kB];
+#pragma unroll
+                for (int b = 0; b < kB; ++b)
+                    if (b < nb) q[b] = ldv<S, V>(srcb + ob + (size_t)(j0 + b) * kSZ);
+#pragma unroll
+                for (int b = 0; b < kB; ++b) {
+                    if (b < nb) {
+                        const Pack<S, V> r = ldv<S, V>(tile + ot + (size_t)(j0 + b) * W);
+                        Pack<S, V> x;
+#pragma unroll
+                        for (int i = 0; i < V; ++i)
+                            x.v[i] = (o == 0) ? S(wgt * A(q[b].v[i]) * A(r.v[i]))
+                                              : S(mad(wgt, A(r.v[i]), A(q[b].v[i])));
+                        stv<S, V>(out + ob + (size_t)(j0 + b) * kSZ, x);
+                    }
+                }
+            }
+        } else if (o == 0) {
             const A h = A(-0.5);
 #pragma unroll 4
             for (int j = 0; j < m; ++j) {
