@@ -435,7 +435,7 @@ SWEEP_CASES = [
      "adjoint"),
     ("256^3 D1^T z closed P=4 FP64/FP32", (256, 256, 256), "z", (1,), ("closed",), (4,), ("f64", "f32"), "adjoint"),
     ("1024^3 D1 x,y,z periodic P=8,2", (1024, 1024, 1024), "xyz", (1,), ("periodic",), (8, 2), ("f64",), "deriv"),
-    ("256 x 262144 D1 x periodic P=64", (1, 256, 262144), "x", (1,), ("periodic",), (64,), ("f64",), "deriv"),
+    ("256 x 262144 D1 x periodic P=64", (1, 256, 262144), "x", (1,), ("periodic",), (64,), ("f64", "f32"), "deriv"),
     ("512^3 solve A x = d, x periodic/closed P=8 FP64/FP32", (512, 512, 512), "x", (1, 2),
      ("periodic", "closed"), (8,), ("f64", "f32"), "solve"),
     ("512^3 compact filter (alpha_f 0.45) and mid-point interpolation, x, P=8 FP64/FP32", (512, 512, 512),
