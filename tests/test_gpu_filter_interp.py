@@ -156,7 +156,7 @@ def test_full_size_sampled_lines(dtype, direction):
     n = 512
     lines = sample_lines(fx.numel() // n, 32, seed=11)
     src = gather_lines(fx, direction, shape, lines).double().cpu().numpy()
-    for kind, bc in (("filter", "periodic"), ("interp", "periodic")):
+    for kind, bc in (("filter", "periodic"), ("filter", "closed"), ("interp", "periodic")):
         plan = make_plan(shape, direction, kind, bc, 8, dtype)
         for adjoint in (False, True):
             y = plan.adjoint(fx) if adjoint else plan.deriv(fx)

@@ -178,41 +178,55 @@ def test_transport_rhs_reuse_and_i_equals_j_layout():
 FULL = (512, 512, 512)
 
 
+# FP32 on closed lines with smooth fields: the second derivative's boundary rows take
+# (13 u0 - 27 u1 + 15 u2 - u3) / h^2, whose terms are ~ 1/h^2 times |u| while their sum is ~ |u''|:
+# at 512 points the subtraction cancels about 10 of FP32's 24 bits, so the bar there is 2e-4
+# (measured 9.3e-5); with i.i.d. fields (no cancellation) the usual 1e-5 holds.
+CLOSED_SMOOTH_F32 = 2e-4
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_transport_rhs_full_size_sampled(dtype):
-    """The benchmark's workload (512^3, P = 8, periodic): the right-hand side at sampled points,
-    each from the whole x, y and z lines through the point (the oracle on lines)."""
+@pytest.mark.parametrize("bc,field", [("periodic", "fourier"), ("closed", "fourier"), ("closed", "uniform")])
+def test_transport_rhs_full_size_sampled(dtype, bc, field):
+    """The benchmark's workload (512^3, P = 8; periodic, and closed lines too): the right-hand
+    side at sampled points, each from the whole x, y and z lines through the point (the oracle
+    on lines), the box's corners and faces included."""
     from paper_2411_13532_gb300 import inputs
     shape = FULL
-    rhs = tds.TransportRHS(shape, P=8, dtype=TORCH[dtype])
-    # smooth velocity components: a few 3D Fourier modes plus small noise
-    u = [inputs.fourier_field(shape, seed=21 + c, device="cuda", dtype=TORCH[dtype])[0].reshape(-1)
-         for c in range(3)]
+    rhs = tds.TransportRHS(shape, P=8, bc=bc, dtype=TORCH[dtype])
+    if field == "fourier":   # smooth velocity components: a few 3D Fourier modes plus small noise
+        u = [inputs.fourier_field(shape, seed=21 + c, device="cuda", dtype=TORCH[dtype])[0].reshape(-1)
+             for c in range(3)]
+    else:                    # i.i.d. U(-1, 1), as the closed-line derivative configurations use
+        u = [inputs.uniform_field(shape, seed=21 + c, device="cuda", dtype=TORCH[dtype]).reshape(-1)
+             for c in range(3)]
     ux = [tds.reorder(f, shape, "cart", "x") for f in u]
     out = rhs(ux, NU)
     outc = [tds.reorder(o, shape, "x", "cart").view(shape) for o in out]
     torch.cuda.synchronize()
     rng = np.random.default_rng(3)
-    pts = [tuple(int(v) for v in rng.integers(0, 512, 3)) for _ in range(24)] + [(0, 0, 0), (511, 511, 511)]
+    pts = [tuple(int(v) for v in rng.integers(0, 512, 3)) for _ in range(24)] + [
+        (0, 0, 0), (511, 511, 511), (1, 510, 2), (255, 0, 511), (3, 3, 508)]
     cu = [f.view(shape) for f in u]
     n = 512
     worst = 0.0
     for (z, y, x) in pts:
         lines = {"x": [f[z, y, :] for f in cu], "y": [f[z, :, x] for f in cu], "z": [f[:, y, x] for f in cu]}
         pos = {"x": x, "y": y, "z": z}
-        h = oracle.grid_spacing(n, "periodic")
+        h = oracle.grid_spacing(n, bc)
         for i in range(3):
             val = 0.0
             for j, d in enumerate("xyz"):
                 li = lines[d][i].double().cpu().numpy()[None, :]
                 lj = lines[d][j].double().cpu().numpy()[None, :]
-                val += oracle.transport_term_lines(li, lj, NU, "periodic", h)[0, pos[d]]
+                val += oracle.transport_term_lines(li, lj, NU, bc, h)[0, pos[d]]
             got = float(outc[i][z, y, x])
             worst = max(worst, abs(got - val))
     # normwise scale: the largest |rhs| over the sampled lines' terms
     scale = max(float(o.abs().max()) for o in outc)
-    report("transport_rhs_512", dtype=dtype, max_rel=worst / scale)
-    assert worst / scale <= TOL[dtype]
+    report("transport_rhs_512", dtype=dtype, bc=bc, field=field, max_rel=worst / scale)
+    bar = CLOSED_SMOOTH_F32 if (dtype == "f32" and bc == "closed" and field == "fourier") else TOL[dtype]
+    assert worst / scale <= bar
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
