@@ -662,6 +662,21 @@ def run_transport(args):
         ms = t0.elapsed_time(t1) / args.steps
         for key, a, b in evs:
             per.setdefault(key, []).append(a.elapsed_time(b))
+        # the same evaluation replayed as one CUDA graph (no per-launch host work)
+        g = rhs.graph(u, args.nu, out)
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = g0.elapsed_time(g1) / args.steps
+        launches += 21 * args.steps
+        del g
         field = es * npts
         kern = {}
         for key, v in sorted(per.items()):
@@ -688,7 +703,7 @@ def run_transport(args):
             "time_share": {"terms": round(term_ms / ms, 4), "reorders": round(reo_ms / ms, 4),
                            "reorder_add": round(acc_ms / ms, 4)},
             "reorder_traffic_share": round(OUR_TRANSFERS["reorder"] / ours, 4),
-            "kernels": kern}
+            "kernels": kern, "graph_ms_per_eval": round(graph_ms, 3)}
         if name == "f64" and args.e2e_steps > 0:
             # end to end: the three components from pinned host memory, the three results back
             hu = [torch.empty(npts, dtype=dt, pin_memory=True) for _ in range(3)]

@@ -379,6 +379,20 @@ class TransportRHS:
             fn()
         return out
 
+    def graph(self, u, nu, out):
+        """One evaluation captured as a CUDA graph on the fixed device buffers ``u`` / ``out``
+        (x layout): ``g.replay()`` reruns the 21 launches with a single submission.  The buffers
+        must stay alive, and keep their addresses, for as long as the graph is replayed."""
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            self(u, nu, out, stream=side)          # warm-up outside the capture (kernel attributes)
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        with torch.cuda.graph(g):
+            self(u, nu, out)
+        return g
+
     def call_host(self, host_u, host_out, nu, u, out, stream=None):
         """One evaluation from pinned host memory to pinned host memory, the copies overlapped
         with the kernels: component i is copied in on an input stream and its x term group starts
