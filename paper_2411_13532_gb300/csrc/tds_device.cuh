@@ -126,9 +126,19 @@ template <typename T>
 __device__ __forceinline__ T stencil(const DevOp &op, int J, const T (&w)[kTaps]) {
     if (!op.periodic && (J < kEdgeRows || J >= op.n - kEdgeRows)) {
         const int e = (J < kEdgeRows) ? J : kEdgeRows + J - (op.n - kEdgeRows);
+        // the row's form (DevOp::edge_form), as in the resident sweep
+        const int form = op.edge_form[e];
         T s = T(0);
+        if (form == 2) {
+            T a[kTaps - 1];
 #pragma unroll
-        for (int o = 0; o < kTaps; ++o) s += T(op.edge[e][o]) * w[o];
+            for (int o = 0; o < kTaps - 1; ++o) a[o] = w[o + 1] - w[o];
+#pragma unroll
+            for (int k = 1; k <= 5; ++k) s += T(op.edge_dd[e][k - 1]) * (a[k] - a[k - 1]);
+        } else {
+#pragma unroll
+            for (int o = 0; o < kTaps; ++o) s += T(op.edge[e][o]) * (form == 1 ? w[o] - w[3] : w[o]);
+        }
         return s;
     }
     // uniform interior rows: taps at offsets 0, +1, +2 and the form of op.symmetric

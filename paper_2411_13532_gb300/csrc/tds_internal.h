@@ -84,6 +84,13 @@ struct DevOp {
     double red_den_inv;   // 1/(1 + v.q)
     double tap[kTaps];                 // interior stencil taps, offsets -3..3
     double edge[2 * kEdgeRows][kTaps]; // closed lines: rows 0..3 then n-4..n-1
+    // How each edge row is evaluated: 0 as the taps; 1 from first differences v[J+o] - v[J] (taps
+    // summing to 0: rows of a first derivative); 2 from second differences with the weights
+    // edge_dd (taps with vanishing sum and first moment: rows of a second derivative).  On
+    // smooth data the differences of nearby values are exact, so a closure's large taps no
+    // longer cancel most of an FP32 mantissa.
+    int edge_form[2 * kEdgeRows];
+    double edge_dd[2 * kEdgeRows][5];  // form 2: weight of v[J+k-4] - 2 v[J+k-3] + v[J+k-2], k = 1..5
 };
 
 } // namespace tds

@@ -240,6 +240,24 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
                 op.edge[kEdgeRows + e][o] = L.taps[(size_t)(n - kEdgeRows + e) * kTaps + o];
             }
     }
+    // the form each edge row is evaluated in (DevOp::edge_form): moments of its taps
+    for (int e = 0; e < 2 * kEdgeRows; ++e) {
+        double m0 = 0.0, m1 = 0.0, mag = 0.0;
+        for (int o = 0; o < kTaps; ++o) {
+            m0 += op.edge[e][o];
+            m1 += (o - 3) * op.edge[e][o];
+            mag += std::fabs(op.edge[e][o]);
+        }
+        const double tol = 1e-12 * mag;
+        op.edge_form[e] = (std::fabs(m0) <= tol) ? ((std::fabs(m1) <= 3.0 * tol) ? 2 : 1) : 0;
+        // second-difference weights: d_k = sum_{o < k} (k - o) c_o (the taps' discrete second
+        // antiderivative; it vanishes at k = 0 and k = 6 when both moments do)
+        for (int k = 1; k <= 5; ++k) {
+            double d = 0.0;
+            for (int o = 0; o < k; ++o) d += (k - o) * op.edge[e][o];
+            op.edge_dd[e][k - 1] = d;
+        }
+    }
 
     // interior forward records with f folded in, and the cut-off rows of pi and s^a
     ifw.assign((size_t)nc * m * 4, 0.0);

@@ -182,13 +182,26 @@ template <typename Tr, int V>
 __device__ __forceinline__ void estencil(const DevOp &op, int e, const Pack<typename Tr::A, V> (&w)[kTaps],
                                          typename Tr::A (&s)[V]) {
     using A = typename Tr::A;
+    const int form = op.edge_form[e];
 #pragma unroll
     for (int i = 0; i < V; ++i) s[i] = Tr::from_d(0.0);
+    if (form == 2) {          // sum_k d_k (a_k - a_{k-1}), a_k = v[J+k-2] - v[J+k-3]
 #pragma unroll
-    for (int o = 0; o < kTaps; ++o) {
-        const A c = Tr::edge(op, e, o);
+        for (int i = 0; i < V; ++i) {
+            A a[kTaps - 1];
 #pragma unroll
-        for (int i = 0; i < V; ++i) s[i] = s[i] + c * w[o].v[i];
+            for (int o = 0; o < kTaps - 1; ++o) a[o] = w[o + 1].v[i] - w[o].v[i];
+#pragma unroll
+            for (int k = 1; k <= 5; ++k) s[i] = mad(Tr::from_d(op.edge_dd[e][k - 1]), a[k] - a[k - 1], s[i]);
+        }
+    } else {                  // form 1: sum_o c_o (v[J+o] - v[J]); form 0: sum_o c_o v[J+o]
+#pragma unroll
+        for (int o = 0; o < kTaps; ++o) {
+            const A c = Tr::edge(op, e, o);
+#pragma unroll
+            for (int i = 0; i < V; ++i)
+                s[i] = mad(c, form == 1 ? w[o].v[i] - w[3].v[i] : w[o].v[i], s[i]);
+        }
     }
 }
 

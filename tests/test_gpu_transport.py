@@ -178,13 +178,6 @@ def test_transport_rhs_reuse_and_i_equals_j_layout():
 FULL = (512, 512, 512)
 
 
-# FP32 on closed lines with smooth fields: the second derivative's boundary rows take
-# (13 u0 - 27 u1 + 15 u2 - u3) / h^2, whose terms are ~ 1/h^2 times |u| while their sum is ~ |u''|:
-# at 512 points the subtraction cancels about 10 of FP32's 24 bits, so the bar there is 2e-4
-# (measured 9.3e-5); with i.i.d. fields (no cancellation) the usual 1e-5 holds.
-CLOSED_SMOOTH_F32 = 2e-4
-
-
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("bc,field", [("periodic", "fourier"), ("closed", "fourier"), ("closed", "uniform")])
 def test_transport_rhs_full_size_sampled(dtype, bc, field):
@@ -225,8 +218,7 @@ def test_transport_rhs_full_size_sampled(dtype, bc, field):
     # normwise scale: the largest |rhs| over the sampled lines' terms
     scale = max(float(o.abs().max()) for o in outc)
     report("transport_rhs_512", dtype=dtype, bc=bc, field=field, max_rel=worst / scale)
-    bar = CLOSED_SMOOTH_F32 if (dtype == "f32" and bc == "closed" and field == "fourier") else TOL[dtype]
-    assert worst / scale <= bar
+    assert worst / scale <= TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
