@@ -144,7 +144,12 @@ __device__ __forceinline__ T stencil(const DevOp &op, int J, const T (&w)[kTaps]
     // uniform interior rows: taps at offsets 0, +1, +2 and the form of op.symmetric
     const T t0 = T(op.tap[3]), t1 = T(op.tap[4]), t2 = T(op.tap[5]);
     switch (op.symmetric) {
-    case 1: return t0 * w[3] + t1 * (w[4] + w[2]) + t2 * (w[5] + w[1]);   // symmetric
+    case 1:
+    case 4:   // symmetric (filter, second derivative); FP32: second differences and the tap sum
+        if constexpr (sizeof(T) == 4)
+            return T(op.tapsum) * w[3] + t1 * ((w[4] - w[3]) - (w[3] - w[2])) + t2 * ((w[5] - w[3]) - (w[3] - w[1]));
+        else
+            return t0 * w[3] + t1 * (w[4] + w[2]) + t2 * (w[5] + w[1]);
     case 2: return t1 * (w[3] + w[4]) + t2 * (w[2] + w[5]);              // nodes -> mid-points
     case 3: return t0 * (w[2] + w[3]) + t1 * (w[1] + w[4]);              // mid-points -> nodes
     default: return t1 * (w[4] - w[2]) + t2 * (w[5] - w[1]);             // antisymmetric

@@ -44,9 +44,12 @@ struct DevOp {
     int adjoint;    // how the sweep runs: 0 stencil right-hand side (A^{-1} B, and B^T A^{-T} on
                     // periodic lines); 1 identity right-hand side on A^T, then the B^T taps
                     // (the adjoint on closed lines); 2 identity right-hand side, no taps (A^{-1})
-    int symmetric;  // interior taps: -1 antisymmetric (first derivative), +1 symmetric (second
-                    // derivative, filter), +2 pairs about +1/2 (nodes -> mid-points), +3 pairs
-                    // about -1/2 (mid-points -> nodes)
+    int symmetric;  // interior taps: -1 antisymmetric (first derivative), +1 symmetric (filter),
+                    // +2 pairs about +1/2 (nodes -> mid-points), +3 pairs about -1/2 (mid-points
+                    // -> nodes), +4 symmetric with vanishing sum (second derivative); FP32
+                    // sweeps apply symmetric taps to second differences (see tapsum)
+    int e64;        // FP32 sweeps of closed lines: the closure rows' steps in FP64 (the solve
+                    // magnifies an end row's rounding by more than 16)
     int ncls;       // chunk classes (first / interior / last differ on closed lines)
     int cls_first, cls_mid, cls_last;
     const double *row64;  // [kNumRowArrays][ncls*m]
@@ -63,7 +66,8 @@ struct DevOp {
     const float *bwd32;
     // interior rows of the forward pass with f_j folded in: {f t_0, f t_1, f t_2, f r} so that
     // d_j = c1 (v[j+1] -+ v[j-1]) + c2 (v[j+2] -+ v[j-2]) (+ c0 v[j]) - g d_{j-1}; for the
-    // adjoint (identity right-hand side) {f, 0, 0, f r}.  [ncls][m] records.
+    // adjoint (identity right-hand side) {f, 0, 0, f r}.  [ncls][m] records.  The FP32 copy of
+    // symmetric taps holds f tapsum in place of f t_0 (the second-difference form).
     const double *ifw64;
     const float *ifw32;
     // per chunk class: rows j >= jpi carry |pi_j| below the cut-off and rows j >= jsa carry
@@ -83,6 +87,7 @@ struct DevOp {
     double red_vlast;     // last entry of the Sherman-Morrison v vector
     double red_den_inv;   // 1/(1 + v.q)
     double tap[kTaps];                 // interior stencil taps, offsets -3..3
+    double tapsum;                     // symmetric taps: t0 + 2 t1 + 2 t2 (0 for a second derivative)
     double edge[2 * kEdgeRows][kTaps]; // closed lines: rows 0..3 then n-4..n-1
     // How each edge row is evaluated: 0 as the taps; 1 from first differences v[J+o] - v[J] (taps
     // summing to 0: rows of a first derivative); 2 from second differences with the weights

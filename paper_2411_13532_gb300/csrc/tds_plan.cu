@@ -194,15 +194,16 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
                                  std::vector<double> &n1s, std::vector<double> &red,
                                  std::vector<double> &sub, std::vector<double> &sup,
                                  std::vector<double> &fwd, std::vector<double> &bwd,
-                                 std::vector<double> &ifw) {
+                                 std::vector<double> &ifw, std::vector<double> &ifw32) {
     const int n = p->n;
     const bool periodic = (p->bc == TDS_BC_PERIODIC);
     std::memset(&op, 0, sizeof(op));
     op.n = n; op.m = m; op.P = P; op.nlines = p->nlines; op.ngroups = p->nlines / kSZ;
     const bool fwd_form = (which == 0) || (which == 1 && periodic);
     op.periodic = periodic; op.adjoint = fwd_form ? 0 : which;
-    // interior stencil form: the interpolation's transpose pairs its taps about -1/2
-    op.symmetric = (p->order == 1) ? -1 : (p->order == 4) ? (which == 1 ? 3 : 2) : 1;
+    // interior stencil form: the interpolation's transpose pairs its taps about -1/2; the
+    // second derivative's taps (vanishing sum) may be applied to second differences
+    op.symmetric = (p->order == 1) ? -1 : (p->order == 4) ? (which == 1 ? 3 : 2) : (p->order == 2 ? 4 : 1);
 
     // chunk classes: cyclic lines have one; closed lines distinguish first / interior / last
     int reps[3];
@@ -259,15 +260,24 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
         }
     }
 
-    // interior forward records with f folded in, and the cut-off rows of pi and s^a
+    // symmetric interior taps: FP32 sweeps apply them as t1, t2 on second differences plus the tap
+    // sum on the centre value -- exactly zero for a second derivative, so nothing cancels there
+    const bool sym = (op.symmetric == 1 || op.symmetric == 4);
+    op.tapsum = (op.symmetric == 4) ? 0.0 : op.tap[3] + 2.0 * (op.tap[4] + op.tap[5]);
+
+    // interior forward records with f folded in (FP32 records: the tap sum in place of t0 for
+    // symmetric taps), and the cut-off rows of pi and s^a
     ifw.assign((size_t)nc * m * 4, 0.0);
+    ifw32.assign((size_t)nc * m * 4, 0.0);
     for (int cl = 0; cl < nc; ++cl) {
         for (int j = 0; j < m; ++j) {
             const double f = fwd[((size_t)cl * m + j) * 4], r = fwd[((size_t)cl * m + j) * 4 + 1];
-            double *c = &ifw[((size_t)cl * m + j) * 4];
+            double *c = &ifw[((size_t)cl * m + j) * 4], *c32 = &ifw32[((size_t)cl * m + j) * 4];
             if (fwd_form) { c[0] = f * op.tap[3]; c[1] = f * op.tap[4]; c[2] = f * op.tap[5]; }
             else { c[0] = f; c[1] = 0.0; c[2] = 0.0; }
             c[3] = f * r;
+            for (int q = 0; q < 4; ++q) c32[q] = c[q];
+            if (fwd_form && sym) c32[0] = f * op.tapsum;
         }
         auto cutoff = [&](int idx, double tol) {   // first row after which |x_j| <= tol
             int j0 = m;
@@ -294,10 +304,11 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
             const double *x = &ifw[((size_t)cl * m + j) * 4];
             return x[0] == rf[0] && x[1] == rf[1] && x[2] == rf[2] && x[3] == rf[3];
         };
+        const double *rf32 = &ifw32[((size_t)cl * m + ref) * 4];
         auto fsame32 = [&](int j) {
-            const double *x = &ifw[((size_t)cl * m + j) * 4];
+            const double *x = &ifw32[((size_t)cl * m + j) * 4];
             for (int q = 0; q < 4; ++q)
-                if ((float)x[q] != (float)rf[q]) return false;
+                if ((float)x[q] != (float)rf32[q]) return false;
             return true;
         };
         const double rb = bwd[((size_t)cl * m + ref) * 2 + 1];
@@ -309,7 +320,7 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
         run(bsame32, op.kbl32[cl], op.kbh32[cl]);
         for (int q = 0; q < 4; ++q) {
             op.kf64[cl][q] = rf[q];
-            op.kf32[cl][q] = (float)rf[q];
+            op.kf32[cl][q] = (float)rf32[q];
         }
         op.kb64[cl] = rb;
         op.kb32[cl] = (float)rb;
@@ -379,6 +390,35 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
     return TDS_OK;
 }
 
+// How much an FP32 rounding near a closed line's ends can grow in the solve: the largest |entry|
+// of A^{-1} and of A^{-T} in the four columns at each end (Thomas solves of unit vectors in
+// FP64).  Closures such as f''_0 + 11 f''_1 make it about 100, f'_0 + 2 f'_1 about 4.
+static double end_gain(const LineOperator &L, int n) {
+    std::vector<double> cp(n), x(n);
+    double g = 0.0;
+    for (int tr = 0; tr < 2; ++tr) {
+        // band of A (tr = 0) or A^T (tr = 1): sub, diag, super of row J
+        auto sub = [&](int J) { return tr ? (J > 0 ? L.c[J - 1] : 0.0) : (J > 0 ? L.a[J] : 0.0); };
+        auto sup = [&](int J) { return tr ? (J < n - 1 ? L.a[J + 1] : 0.0) : (J < n - 1 ? L.c[J] : 0.0); };
+        for (int k = 0; k < 2 * kEdgeRows; ++k) {
+            const int col = (k < kEdgeRows) ? k : n - 2 * kEdgeRows + k;
+            double den = L.b[0];
+            if (den == 0.0) return 1e300;
+            cp[0] = sup(0) / den;
+            x[0] = (col == 0) ? 1.0 / den : 0.0;
+            for (int J = 1; J < n; ++J) {
+                den = L.b[J] - sub(J) * cp[J - 1];
+                if (den == 0.0 || !std::isfinite(den)) return 1e300;
+                cp[J] = sup(J) / den;
+                x[J] = ((J == col ? 1.0 : 0.0) - sub(J) * x[J - 1]) / den;
+            }
+            for (int J = n - 2; J >= 0; --J) x[J] -= cp[J] * x[J + 1];
+            for (int J = 0; J < n; ++J) g = std::fmax(g, std::fabs(x[J]));
+        }
+    }
+    return g;
+}
+
 tds_status build_plan(tds_plan *p) {
     const bool periodic = (p->bc == TDS_BC_PERIODIC);
     LineOperator L, LT;
@@ -399,7 +439,7 @@ tds_status build_plan(tds_plan *p) {
             if (p->m % d == 0) { sg = d; break; }
     }
     const int nops = sg ? (periodic ? 5 : 4) : 3;
-    std::vector<double> rows[5], n1s[5], red[5], sub[5], sup[5], fwd[5], bwd[5], ifw[5];
+    std::vector<double> rows[5], n1s[5], red[5], sub[5], sup[5], fwd[5], bwd[5], ifw[5], ifw32[5];
     DevOp *ops[5] = {&p->op[0], &p->op[1], &p->op[2], &p->seg, &p->seg_adj};
     std::memset(&p->seg, 0, sizeof(p->seg));
     std::memset(&p->seg_adj, 0, sizeof(p->seg_adj));
@@ -407,9 +447,13 @@ tds_status build_plan(tds_plan *p) {
         const int P = (w < 3) ? p->P : p->n / sg, m = (w < 3) ? p->m : sg;
         const int kind = (w == 1 || w == 4) ? 1 : (w == 2 ? 2 : 0);
         tds_status s = build_operator(p, P, m, kind == 1 ? LT : L, kind, *ops[w], rows[w], n1s[w],
-                                      red[w], sub[w], sup[w], fwd[w], bwd[w], ifw[w]);
+                                      red[w], sub[w], sup[w], fwd[w], bwd[w], ifw[w], ifw32[w]);
         if (s != TDS_OK) return s;
     }
+    // FP32 sweeps of closed lines take the closure rows in FP64 where the solve magnifies an
+    // end row's rounding by more than 16 (2^-24 x 16 ~ 1e-6)
+    const int e64 = (!periodic && p->dtype == TDS_F32 && end_gain(L, p->n) > 16.0) ? 1 : 0;
+    for (int w = 0; w < nops; ++w) ops[w]->e64 = e64;
     if (nops >= 4 && (!p->seg.red_decoupled || (nops == 5 && !p->seg_adj.red_decoupled))) {
         std::memset(&p->seg, 0, sizeof(p->seg));
         std::memset(&p->seg_adj, 0, sizeof(p->seg_adj));
@@ -444,7 +488,7 @@ tds_status build_plan(tds_plan *p) {
         put64(off[w][2], n1s[w]); put64(off[w][3], red[w]);
         put64(off[w][4], fwd[w]); put32(off[w][5], fwd[w]);
         put64(off[w][6], bwd[w]); put32(off[w][7], bwd[w]);
-        put64(off[w][8], ifw[w]); put32(off[w][9], ifw[w]);
+        put64(off[w][8], ifw[w]); put32(off[w][9], ifw32[w]);
     }
     void *d = nullptr;
     const cudaError_t e = cudaMalloc(&d, total);

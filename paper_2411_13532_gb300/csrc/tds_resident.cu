@@ -9,8 +9,9 @@
 //              (Algorithm 5), in place, accumulating the back-swept row 1 as S = sum pi_j d_j
 //              so that row 0 is decoupled without a separate backward pass; rows whose folded
 //              coefficients have converged take them from registers; the uniform interior
-//              stencil has one of four forms (antisymmetric, symmetric, and the two half-point
-//              forms of the mid-point interpolation and its transpose);
+//              stencil has one of five forms (antisymmetric, symmetric, second differences,
+//              and the two half-point forms of the mid-point interpolation and its transpose);
+//              FP32 sweeps of closed lines take the closure rows' steps in FP64 (Ends64);
 //   reduced  : the chunk-end system in FP64 (communication phase; decoupled 2x2 boundary
 //              systems when the couplings they ignore are below 2^-64, else the full system);
 //   back-substitution: u_{m-1} = L, u_j = d_j - s^a_j F - s^c_j u_{j+1}, u_0 = F -- the
@@ -51,11 +52,12 @@ __device__ __forceinline__ double mad(double a, double b, double c) { return ::f
 //   mid : an intermediate value (d_j, y_j) kept in the tile slot of its row
 //   out : a final value into the tile slot, as S
 // ------------------------------------------------------------------------------------------
-template <typename T, int W_ = kSZ>
+template <typename T, int W_ = kSZ, bool E64_ = false>
 struct TrNative {
     using S = T;
     using A = T;
     static constexpr int W = W_;   // lines per CTA: the row stride of the tile in shared memory
+    static constexpr bool kE64 = E64_;   // FP32 closed lines: closure rows in FP64 (Ends64)
     static __device__ __forceinline__ A from_d(double x) { return A(x); }
     static __device__ __forceinline__ double to_d(A x) { return double(x); }
     template <int V>
@@ -138,6 +140,8 @@ using TrF32 = TrNative<float>;
 using TrF64 = TrNative<double>;
 template <int W> using TrF32w = TrNative<float, W>;
 template <int W> using TrF64w = TrNative<double, W>;
+using TrF32c = TrNative<float, kSZ, true>;
+template <int W> using TrF32cw = TrNative<float, W, true>;
 
 // Whether a finished tile leaves with one TMA bulk store (FP32: the sweep is HBM-bound) or
 // with per-thread stores that overlap the sweep (FP64 storage).
@@ -154,15 +158,20 @@ __device__ __forceinline__ Pack<typename Tr::A, V> zero_a() {
 
 // Forms of the uniform interior stencil (taps t0, t1, t2 at offsets 0, +1, +2 of the row):
 //   kAnti: t1 (v[j+1] - v[j-1]) + t2 (v[j+2] - v[j-2])              (first derivative)
-//   kSym : t0 v[j] + t1 (v[j+1] + v[j-1]) + t2 (v[j+2] + v[j-2])     (second derivative, filter)
+//   kSym : t0 v[j] + t1 (v[j+1] + v[j-1]) + t2 (v[j+2] + v[j-2])     (second derivative, filter: FP64)
 //   kHalfFwd: t1 (v[j] + v[j+1]) + t2 (v[j-1] + v[j+2])              (nodes -> mid-points)
 //   kHalfBwd: t0 (v[j-1] + v[j]) + t1 (v[j-2] + v[j+1])              (its transpose)
-// (the plan's op.symmetric: -1, 1, 2, 3).
-constexpr int kAnti = 0, kSym = 1, kHalfFwd = 2, kHalfBwd = 3;
+//   kSymD: s v[j] + t1 ((v[j+1] - v[j]) - (v[j] - v[j-1])) + t2 ((v[j+2] - v[j]) - (v[j] - v[j-2]))
+//          with s = t0 + 2 t1 + 2 t2: the same symmetric taps, for FP32 sweeps -- on smooth data
+//          the differences of nearby values are exact, where the kSym sum of a second
+//          derivative (s = 0) loses about 6 bits to cancellation
+// (the plan's op.symmetric: -1; 1 and 4 (kSym in FP64 sweeps, kSymD in FP32 sweeps); 2; 3).
+constexpr int kAnti = 0, kSym = 1, kHalfFwd = 2, kHalfBwd = 3, kSymD = 4;
 
 template <typename A, int FORM>
 __device__ __forceinline__ A interior_rhs(A t0, A t1, A t2, A w0, A w1, A w2, A w3, A w4) {
     if (FORM == kSym) return mad(t0, w2, mad(t1, w3 + w1, t2 * (w4 + w0)));
+    if (FORM == kSymD) return mad(t0, w2, mad(t1, (w3 - w2) - (w2 - w1), t2 * ((w4 - w2) - (w2 - w0))));
     if (FORM == kHalfFwd) return mad(t1, w2 + w3, t2 * (w1 + w4));
     if (FORM == kHalfBwd) return mad(t0, w1 + w2, t1 * (w0 + w3));
     return mad(t1, w3 - w1, t2 * (w4 - w0));
@@ -270,6 +279,64 @@ __device__ __forceinline__ void fwd_row(const DevOp &op, int cls, int j, typenam
     Tr::template st_mid<V>(row + (size_t)j * Tr::W, dprev);
 }
 
+// FP32 sweeps of closed lines: the closure makes the chunk ends ill-conditioned -- an error in
+// the right-hand side or the forward value of row 1 (n-2) reaches the solution at row 0 (n-1)
+// multiplied by about 100 for the second derivative (f''_0 + 11 f''_1 = ...).  So the FP32
+// sweeps take the four closure rows at each end of the line in FP64: their right-hand sides from
+// the (exact) FP32 inputs, their forward steps with the FP64 records, and the quantities the
+// reduced system receives from them -- x0 = d_0 - w_0 sum_{j<4} pi_j d_j of the first chunk,
+// row 0's value before the rest of S joins it, and the last forward value xl when it belongs to
+// an FP64 row.  The stored d_j of those rows are rounded to FP32 as usual (the back-substitution
+// does not amplify them).  FP64 sweeps carry none of it (first = last = false).
+template <int V>
+struct Ends64 {
+    double x0[V], xl[V];
+    bool first;   // x0 holds the first chunk's row-0 term
+    bool last;    // xl holds d_{m-1}
+};
+
+// One closure row of an FP32 sweep in FP64: d = f (s - r d), Sx += pi d, d -> tile as FP32.
+template <typename Tr, int V>
+__device__ __forceinline__ void fwd_row64(const DevOp &op, int cls, int j, typename Tr::S *row,
+                                          const double (&sv)[V], double (&d)[V], double (&Sx)[V]) {
+    const size_t i = (size_t)cls * op.m + j;
+    const double2 fr = __ldg(reinterpret_cast<const double2 *>(op.fwd64) + 2 * i);
+    const double pi = __ldg(op.fwd64 + 4 * i + 2);
+    Pack<typename Tr::A, V> x;
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+        d[q] = fr.x * (sv[q] - fr.y * d[q]);
+        Sx[q] = ::fma(pi, d[q], Sx[q]);
+        x.v[q] = static_cast<typename Tr::A>(d[q]);
+    }
+    Tr::template st_mid<V>(row + (size_t)j * Tr::W, x);
+}
+
+// After FP64 rows [j0, j0 + 4) of a chunk (head: the line's first rows, d0 = d_0 of each line):
+// hand the state back to the FP32 sweep and keep what the chunk ends need.
+template <typename Tr, int V>
+__device__ __forceinline__ void close_rows64(const DevOp &op, int cls, int j0, bool head, const double (&d)[V],
+                                             const double (&Sx)[V], const double (&d0)[V],
+                                             Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S,
+                                             Ends64<V> &ex) {
+    if (head) {
+        const double w0 = __ldg(op.bwd64 + 2 * (size_t)cls * op.m + 1);   // c_0 / b_0
+#pragma unroll
+        for (int q = 0; q < V; ++q) ex.x0[q] = ::fma(-w0, Sx[q], d0[q]);
+        ex.first = true;
+    } else {
+#pragma unroll
+        for (int q = 0; q < V; ++q) S.v[q] += static_cast<typename Tr::A>(Sx[q]);
+    }
+    if (j0 + 4 == op.m) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) ex.xl[q] = d[q];
+        ex.last = true;
+    }
+#pragma unroll
+    for (int q = 0; q < V; ++q) dprev.v[q] = static_cast<typename Tr::A>(d[q]);
+}
+
 // Interior row of the forward pass with f folded into the coefficients:
 // d_j = (the FORM's stencil with taps c0, c1, c2) - g d_{j-1}, one FMA on the recurrence;
 // ACC: S += pi_j d_j (rows past the plan's cut-off skip it).
@@ -347,7 +414,7 @@ __device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typenam
                                                int &unsafe) {
     using A = typename Tr::A;
     const int m = op.m;
-    const A t0 = Tr::tap(op, 3), t1 = Tr::tap(op, 4), t2 = Tr::tap(op, 5);
+    const A t0 = (FORM == kSymD) ? Tr::from_d(op.tapsum) : Tr::tap(op, 3), t1 = Tr::tap(op, 4), t2 = Tr::tap(op, 5);
     const int jm = (je < m - 2) ? je : m - 2;
     if (FWD) {
         // rows before the pi cut-off accumulate S, the rest do not
@@ -390,35 +457,81 @@ __device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typenam
 }
 
 // Closure rows j0..j0+3 of a stencil sweep: 7-point windows from the scratch rows
-// (x[i] = v[Jx + i] at scratch index i - xlo, entries outside [0, xhi) zero).
+// (x[i] = v[Jx + i] at scratch index i - xlo, entries outside [0, xhi) zero).  head: the line's
+// first rows.  The forward rows of an FP32 sweep run in FP64 (Ends64).
 template <typename Tr, int V, bool FWD>
 __device__ __forceinline__ void sweep_edge(const DevOp &op, int cls, typename Tr::S *row, int j0, int e0,
-                                           const typename Tr::S *xs, int c, int xlo, int xhi,
-                                           Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S) {
+                                           const typename Tr::S *xs, int c, int xlo, int xhi, bool head,
+                                           Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S,
+                                           Ends64<V> &ex) {
     using A = typename Tr::A;
+    bool done = false;
+    if constexpr (FWD && Tr::kE64) {
+        if (op.e64) {
+            // the ten input rows the four windows cover, converted once; two partial sums per
+            // row halve the dependent chain
+            double xw[kTaps + 3][V];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        A sv[V];
-        {
-            Pack<A, V> w7[kTaps];
-#pragma unroll
-            for (int o = 0; o < kTaps; ++o) {
-                const int x = t + o + xlo;
+            for (int o = 0; o < kTaps + 3; ++o) {
+                const int x = o + xlo;
                 int dummy = 0;
-                w7[o] = (x >= 0 && x < xhi)
-                            ? (FWD ? Tr::template ld_in<V>(op, xs + (size_t)x * Tr::W + c, dummy)
-                                   : Tr::template ld_mid<V>(xs + (size_t)x * Tr::W + c))
-                            : zero_a<Tr, V>();
-            }
-            estencil<Tr, V>(op, e0 + t, w7, sv);
-        }
-        if (FWD) {
-            fwd_row<Tr, V>(op, cls, j0 + t, row, sv, dprev, S);
-        } else {
-            Pack<A, V> x;
+                const Pack<A, V> v = (x >= 0 && x < xhi) ? Tr::template ld_in<V>(op, xs + (size_t)x * Tr::W + c, dummy)
+                                                         : zero_a<Tr, V>();
 #pragma unroll
-            for (int i = 0; i < V; ++i) x.v[i] = sv[i];
-            Tr::template st_out<V>(op, row + (size_t)(j0 + t) * Tr::W, x);
+                for (int q = 0; q < V; ++q) xw[o][q] = (double)v.v[q];
+            }
+            double d[V], Sx[V], d0[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) { d[q] = head ? 0.0 : (double)dprev.v[q]; Sx[q] = 0.0; d0[q] = 0.0; }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const double *cf = op.edge[e0 + t];
+                double sv[V];
+#pragma unroll
+                for (int q = 0; q < V; ++q) {
+                    double s0 = cf[0] * xw[t][q], s1 = cf[1] * xw[t + 1][q];
+#pragma unroll
+                    for (int o = 2; o < kTaps; o += 2) {
+                        s0 = ::fma(cf[o], xw[t + o][q], s0);
+                        if (o + 1 < kTaps) s1 = ::fma(cf[o + 1], xw[t + o + 1][q], s1);
+                    }
+                    sv[q] = s0 + s1;
+                }
+                fwd_row64<Tr, V>(op, cls, j0 + t, row, sv, d, Sx);
+                if (t == 0) {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) d0[q] = d[q];
+                }
+            }
+            close_rows64<Tr, V>(op, cls, j0, head, d, Sx, d0, dprev, S, ex);
+            done = true;
+        }
+    }
+    if (!done) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            A sv[V];
+            {
+                Pack<A, V> w7[kTaps];
+#pragma unroll
+                for (int o = 0; o < kTaps; ++o) {
+                    const int x = t + o + xlo;
+                    int dummy = 0;
+                    w7[o] = (x >= 0 && x < xhi)
+                                ? (FWD ? Tr::template ld_in<V>(op, xs + (size_t)x * Tr::W + c, dummy)
+                                       : Tr::template ld_mid<V>(xs + (size_t)x * Tr::W + c))
+                                : zero_a<Tr, V>();
+                }
+                estencil<Tr, V>(op, e0 + t, w7, sv);
+            }
+            if (FWD) {
+                fwd_row<Tr, V>(op, cls, j0 + t, row, sv, dprev, S);
+            } else {
+                Pack<A, V> x;
+#pragma unroll
+                for (int i = 0; i < V; ++i) x.v[i] = sv[i];
+                Tr::template st_out<V>(op, row + (size_t)(j0 + t) * Tr::W, x);
+            }
         }
     }
 }
@@ -430,12 +543,12 @@ __device__ __forceinline__ void stencil_sweep(const DevOp &op, int k, int cls, t
                                               const Pack<typename Tr::A, V> (&hb)[2],
                                               const Pack<typename Tr::A, V> (&ha)[2],
                                               Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S,
-                                              int &unsafe) {
+                                              Ends64<V> &ex, int &unsafe) {
     const int m = op.m;
     const bool first_edge = !op.periodic && k == 0;
     const bool last_edge = !op.periodic && k == op.P - 1;
     const int jb = first_edge ? 4 : 0, je = last_edge ? m - 4 : m;
-    if (first_edge) sweep_edge<Tr, V, FWD>(op, cls, row, 0, 0, xs, c, -3, kTaps, dprev, S);
+    if (first_edge) sweep_edge<Tr, V, FWD>(op, cls, row, 0, 0, xs, c, -3, kTaps, true, dprev, S, ex);
     Pack<typename Tr::A, V> w[5];
     if (first_edge) {
 #pragma unroll
@@ -448,8 +561,11 @@ __device__ __forceinline__ void stencil_sweep(const DevOp &op, int k, int cls, t
         w[2] = FWD ? Tr::template ld_in<V>(op, row, unsafe) : Tr::template ld_mid<V>(row);
         w[3] = FWD ? Tr::template ld_in<V>(op, row + Tr::W, unsafe) : Tr::template ld_mid<V>(row + Tr::W);
     }
-    if (op.symmetric == 1) {
-        sweep_interior<Tr, V, kSym, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
+    if (op.symmetric == 1 || op.symmetric == 4) {
+        if constexpr (sizeof(typename Tr::A) == 8)
+            sweep_interior<Tr, V, kSym, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
+        else
+            sweep_interior<Tr, V, kSymD, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
     } else if (op.symmetric < 0) {
         sweep_interior<Tr, V, kAnti, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
     } else if constexpr (FWD && V == 1) {
@@ -460,7 +576,8 @@ __device__ __forceinline__ void stencil_sweep(const DevOp &op, int k, int cls, t
     }
     // the last 4 rows of a closed line: scratch rows 7..13 hold v[n-7..n-1]
     if (last_edge)
-        sweep_edge<Tr, V, FWD>(op, cls, row, m - 4, kEdgeRows, xs + (size_t)kTaps * Tr::W, c, 0, kTaps, dprev, S);
+        sweep_edge<Tr, V, FWD>(op, cls, row, m - 4, kEdgeRows, xs + (size_t)kTaps * Tr::W, c, 0, kTaps, false,
+                               dprev, S, ex);
 }
 
 // Forward pass of chunk K (rows at `row` in the tile): the fused stencil (forward operator) or
@@ -470,11 +587,12 @@ __device__ __forceinline__ void forward_phase(const DevOp &op, typename Tr::S *r
                                               int K, int cls, int c, const Pack<typename Tr::A, V> (&hb)[2],
                                               const Pack<typename Tr::A, V> (&ha)[2],
                                               Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &Ssum,
-                                              int &unsafe) {
+                                              Ends64<V> &ex, int &unsafe) {
     using A = typename Tr::A;
     const int m = op.m;
+    ex.first = ex.last = false;
     if (!ADJ) {
-        stencil_sweep<Tr, V, true>(op, K, cls, row, xs, c, hb, ha, dprev, Ssum, unsafe);
+        stencil_sweep<Tr, V, true>(op, K, cls, row, xs, c, hb, ha, dprev, Ssum, ex, unsafe);
     } else {
         // identity right-hand side: d_j = f_j g_j - (f_j r_j) d_{j-1}
         int lo, hi;
@@ -504,19 +622,45 @@ __device__ __forceinline__ void forward_phase(const DevOp &op, typename Tr::S *r
 #pragma unroll 4
             for (int j = y; j < b; ++j) arow(j, acc, false);
         };
-        const int jp = Tr::jpi(op, cls) < m ? Tr::jpi(op, cls) : m;
-        span(0, jp, true);
-        span(jp, m, false);
+        // FP32 sweeps of closed lines: the four rows at each end of the line in FP64 (Ends64)
+        auto rows64 = [&](int j0, bool head) {
+            double d[V], Sx[V], d0[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) { d[i] = head ? 0.0 : (double)dprev.v[i]; Sx[i] = 0.0; d0[i] = 0.0; }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const Pack<A, V> g = Tr::template ld_in<V>(op, row + (size_t)(j0 + t) * Tr::W, unsafe);
+                double sv[V];
+#pragma unroll
+                for (int i = 0; i < V; ++i) sv[i] = (double)g.v[i];
+                fwd_row64<Tr, V>(op, cls, j0 + t, row, sv, d, Sx);
+                if (t == 0) {
+#pragma unroll
+                    for (int i = 0; i < V; ++i) d0[i] = d[i];
+                }
+            }
+            close_rows64<Tr, V>(op, cls, j0, head, d, Sx, d0, dprev, Ssum, ex);
+        };
+        const bool e64 = Tr::kE64 && op.e64;
+        const bool head = e64 && K == 0, tail = e64 && K == op.P - 1;
+        const int ja = head ? 4 : 0, jz = tail ? m - 4 : m;
+        if (head) rows64(0, true);
+        const int jp0 = Tr::jpi(op, cls);
+        const int jp = (jp0 < ja) ? ja : (jp0 > jz ? jz : jp0);
+        span(ja, jp, true);
+        span(jp, jz, false);
+        if (tail) rows64(m - 4, false);
     }
 }
 
 // Chunk ends after the forward pass: row 0 eliminates the back-swept row 1,
 // e0 = N1 (d_0 - w_0 S); e1 = d_{m-1}.
+// With FP64 closure rows (Ends64): e0 = N1 (x0 - w_0 S_rest), e1 = xl, in FP64.
 template <typename Tr, int V>
 __device__ __forceinline__ void chunk_ends(const DevOp &op, const typename Tr::S *row, int cls,
                                            const Pack<typename Tr::A, V> &dprev,
-                                           const Pack<typename Tr::A, V> &Ssum, double (&e0)[V],
-                                           double (&e1)[V]) {
+                                           const Pack<typename Tr::A, V> &Ssum, const Ends64<V> &ex,
+                                           double (&e0)[V], double (&e1)[V]) {
     using A = typename Tr::A;
     const Pack<A, V> d0 = Tr::template ld_mid<V>(row);
     A sa0, w0;
@@ -526,6 +670,17 @@ __device__ __forceinline__ void chunk_ends(const DevOp &op, const typename Tr::S
     for (int i = 0; i < V; ++i) {
         e0[i] = Tr::to_d(n1 * (d0.v[i] - w0 * Ssum.v[i]));
         e1[i] = Tr::to_d(dprev.v[i]);
+    }
+    if constexpr (Tr::kE64) {
+        if (ex.first) {
+            const double n1d = __ldg(op.n1 + cls), w0d = __ldg(op.bwd64 + 2 * (size_t)cls * op.m + 1);
+#pragma unroll
+            for (int i = 0; i < V; ++i) e0[i] = n1d * ::fma(-w0d, (double)Ssum.v[i], ex.x0[i]);
+        }
+        if (ex.last) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) e1[i] = ex.xl[i];
+        }
     }
 }
 
@@ -596,11 +751,12 @@ __device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *til
     const int cls = chunk_class(op, k);
     S *row = tile + (size_t)k * m * Tr::W + c;
     Pack<A, V> dprev = zero_a<Tr, V>(), Ssum = zero_a<Tr, V>();
+    Ends64<V> ex;
 
-    forward_phase<Tr, V, MODE != 0>(op, row, xs, k, cls, c, hb, ha, dprev, Ssum, unsafe);
+    forward_phase<Tr, V, MODE != 0>(op, row, xs, k, cls, c, hb, ha, dprev, Ssum, ex, unsafe);
     {
         double e0[V], e1[V];
-        chunk_ends<Tr, V>(op, row, cls, dprev, Ssum, e0, e1);
+        chunk_ends<Tr, V>(op, row, cls, dprev, Ssum, ex, e0, e1);
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             ends[(size_t)(2 * k) * Tr::W + c + i] = e0[i];
@@ -645,7 +801,7 @@ __device__ __forceinline__ void group_sweep(const DevOp &op, typename Tr::S *til
         const TileView<S> tv{tile, 0, op.n, nullptr};
         read_halo<Tr, V, true>(op, tv, xs, k, c, yb, ya, unsafe);
         __syncthreads();
-        stencil_sweep<Tr, V, false>(op, k, cls, row, xs, c, yb, ya, dprev, Ssum, unsafe);
+        stencil_sweep<Tr, V, false>(op, k, cls, row, xs, c, yb, ya, dprev, Ssum, ex, unsafe);
     }
 }
 
@@ -1197,9 +1353,10 @@ __global__ void __launch_bounds__(32) k_seg_forward(const __grid_constant__ DevO
     const int cls = chunk_class(op, K);
     S *row = tile + c;
     Pack<A, 1> dprev = zero_a<Tr, 1>(), Ssum = zero_a<Tr, 1>();
-    forward_phase<Tr, 1, false>(op, row, xs, K, cls, c, hb, ha, dprev, Ssum, unsafe);
+    Ends64<1> ex;
+    forward_phase<Tr, 1, false>(op, row, xs, K, cls, c, hb, ha, dprev, Ssum, ex, unsafe);
     double e0[1], e1[1];
-    chunk_ends<Tr, 1>(op, row, cls, dprev, Ssum, e0, e1);
+    chunk_ends<Tr, 1>(op, row, cls, dprev, Ssum, ex, e0, e1);
     double *e = ws + ((size_t)(g * P + K) * 2) * kSZ + c;
     e[0] = e0[0];
     e[kSZ] = e1[0];
@@ -1290,18 +1447,53 @@ __global__ void __launch_bounds__(32) k_seg_ends(const __grid_constant__ DevOp o
             w[kTaps - 1] = val(j + 4);
         }
     };
+    // FP32 sweeps of closed lines: the four rows at each end of the line in FP64 (Ends64)
+    const bool e64 = Tr::kE64 && op.e64;
+    const bool head = e64 && K == 0, tail = e64 && K == P - 1;
+    double x0 = 0.0, xl = 0.0;
+    auto rows64 = [&](int jb, double d, double &Sx, double &dfirst) {
+        Sx = 0.0;
+        for (int t = 0; t < 4; ++t) {
+            const int j = jb + t, J = J0 + j;
+            const int e = (J < kEdgeRows) ? J : kEdgeRows + J - (n - kEdgeRows);
+            double sv = 0.0;
+#pragma unroll
+            for (int o = 0; o < kTaps; ++o) sv = ::fma(op.edge[e][o], (double)val(j - 3 + o), sv);
+            const size_t i = (size_t)cls * m + j;
+            d = __ldg(op.fwd64 + 4 * i) * (sv - __ldg(op.fwd64 + 4 * i + 1) * d);
+            Sx = ::fma(__ldg(op.fwd64 + 4 * i + 2), d, Sx);
+            if (t == 0) dfirst = d;
+        }
+        return d;
+    };
     A dprev = A(0), Ssum = A(0), d0 = A(0);
-    sweep(0, split ? jp : m, dprev, Ssum, d0);
-    if (split) {
+    const int ja = head ? 4 : 0;
+    if (head) {
+        double Sx, df;
+        const double d3 = rows64(0, 0.0, Sx, df);
+        x0 = ::fma(-__ldg(op.bwd64 + 2 * (size_t)cls * m + 1), Sx, df);
+        dprev = A(d3);
+    }
+    if (!split) {
+        sweep(ja, tail ? m - 4 : m, dprev, Ssum, d0);
+    } else {
+        sweep(ja, jp > ja ? jp : ja, dprev, Ssum, d0);
         dprev = A(0);
-        sweep(tb0 + 3, m, dprev, Ssum, d0);
+        sweep(tb0 + 3, tail ? m - 4 : m, dprev, Ssum, d0);
+    }
+    if (tail) {
+        double Sx, df;
+        xl = rows64(m - 4, (double)dprev, Sx, df);
+        Ssum += A(Sx);
+        dprev = A(xl);
     }
     A sa0, w0;
     Tr::bwd(op, cls, 0, sa0, w0);
     const A n1 = Tr::from_d(__ldg(op.n1 + cls));
     double *e = ws + ((size_t)(g * P + K) * 2) * kSZ + c;
-    e[0] = Tr::to_d(n1 * (d0 - w0 * Ssum));
-    e[kSZ] = Tr::to_d(dprev);
+    e[0] = head ? __ldg(op.n1 + cls) * ::fma(-__ldg(op.bwd64 + 2 * (size_t)cls * m + 1), (double)Ssum, x0)
+                : Tr::to_d(n1 * (d0 - w0 * Ssum));
+    e[kSZ] = tail ? xl : Tr::to_d(dprev);
 }
 
 template <typename Tr, bool RECOMPUTE>
@@ -1352,7 +1544,8 @@ __global__ void __launch_bounds__(32) k_seg_backward(const __grid_constant__ Dev
         read_halo<Tr, 1, false>(op, TileView<S>{tile, r0, r0 + m, in + gofs}, xs, K, c, hb, ha, unsafe);
         __syncwarp();
         Pack<A, 1> dprev = zero_a<Tr, 1>(), Ssum = zero_a<Tr, 1>();
-        forward_phase<Tr, 1, false>(op, row, xs, K, cls, c, hb, ha, dprev, Ssum, unsafe);
+        Ends64<1> ex;
+        forward_phase<Tr, 1, false>(op, row, xs, K, cls, c, hb, ha, dprev, Ssum, ex, unsafe);
     }
     Pack<A, 1> F, L;
     F.v[0] = Tr::from_d(F64);
@@ -1528,6 +1721,13 @@ tds_status launch_resident(const tds_plan *p, int which, const void *in, void *o
         return lanes == 2 ? launch_resident_v<TrF64, 2>(p, which, tm, in, out, st)
                           : launch_resident_v<TrF64, 1>(p, which, tm, in, out, st);
     }
+    if (p->op[which].e64) {
+        if (W == 16) return launch_resident_v<TrF32cw<16>, 1>(p, which, tm, in, out, st);
+        if (W == 8) return launch_resident_v<TrF32cw<8>, 1>(p, which, tm, in, out, st);
+        return lanes == 4 ? launch_resident_v<TrF32c, 4>(p, which, tm, in, out, st)
+             : lanes == 2 ? launch_resident_v<TrF32c, 2>(p, which, tm, in, out, st)
+                          : launch_resident_v<TrF32c, 1>(p, which, tm, in, out, st);
+    }
     if (W == 16) return launch_resident_v<TrF32w<16>, 1>(p, which, tm, in, out, st);
     if (W == 8) return launch_resident_v<TrF32w<8>, 1>(p, which, tm, in, out, st);
     return lanes == 4 ? launch_resident_v<TrF32, 4>(p, which, tm, in, out, st)
@@ -1543,6 +1743,10 @@ tds_status launch_pipelined(const tds_plan *p, int which, const void *in, void *
         return W == 16 ? launch_pipe_w<TrF64w<16>>(p, which, tm, in, out, st)
              : W == 8  ? launch_pipe_w<TrF64w<8>>(p, which, tm, in, out, st)
                        : launch_pipe_w<TrF64>(p, which, tm, in, out, st);
+    if (p->op[which].e64)
+        return W == 16 ? launch_pipe_w<TrF32cw<16>>(p, which, tm, in, out, st)
+             : W == 8  ? launch_pipe_w<TrF32cw<8>>(p, which, tm, in, out, st)
+                       : launch_pipe_w<TrF32c>(p, which, tm, in, out, st);
     return W == 16 ? launch_pipe_w<TrF32w<16>>(p, which, tm, in, out, st)
          : W == 8  ? launch_pipe_w<TrF32w<8>>(p, which, tm, in, out, st)
                    : launch_pipe_w<TrF32>(p, which, tm, in, out, st);
@@ -1585,6 +1789,12 @@ tds_status launch_resident_multi(const tds_plan *const *plans, const int *which,
         return W == 16 ? launch_multi_t<TrF64w<16>>(ma, mm, in, smem, st)
              : W == 8  ? launch_multi_t<TrF64w<8>>(ma, mm, in, smem, st)
                        : launch_multi_t<TrF64>(ma, mm, in, smem, st);
+    bool e64 = false;
+    for (int i = 0; i < count; ++i) e64 = e64 || ma.op[i].e64;
+    if (e64)
+        return W == 16 ? launch_multi_t<TrF32cw<16>>(ma, mm, in, smem, st)
+             : W == 8  ? launch_multi_t<TrF32cw<8>>(ma, mm, in, smem, st)
+                       : launch_multi_t<TrF32c>(ma, mm, in, smem, st);
     return W == 16 ? launch_multi_t<TrF32w<16>>(ma, mm, in, smem, st)
          : W == 8  ? launch_multi_t<TrF32w<8>>(ma, mm, in, smem, st)
                    : launch_multi_t<TrF32>(ma, mm, in, smem, st);
@@ -1638,6 +1848,10 @@ tds_status launch_resident_transport(const tds_plan *d1, const tds_plan *d2, con
         return W == 16 ? launch_transport_t<TrF64w<16>>(ta, mm, ui, uj, out, smem, L, st)
              : W == 8  ? launch_transport_t<TrF64w<8>>(ta, mm, ui, uj, out, smem, L, st)
                        : launch_transport_t<TrF64>(ta, mm, ui, uj, out, smem, L, st);
+    if (ta.op1.e64 || ta.op2.e64)
+        return W == 16 ? launch_transport_t<TrF32cw<16>>(ta, mm, ui, uj, out, smem, L, st)
+             : W == 8  ? launch_transport_t<TrF32cw<8>>(ta, mm, ui, uj, out, smem, L, st)
+                       : launch_transport_t<TrF32c>(ta, mm, ui, uj, out, smem, L, st);
     return W == 16 ? launch_transport_t<TrF32w<16>>(ta, mm, ui, uj, out, smem, L, st)
          : W == 8  ? launch_transport_t<TrF32w<8>>(ta, mm, ui, uj, out, smem, L, st)
                    : launch_transport_t<TrF32>(ta, mm, ui, uj, out, smem, L, st);
@@ -1671,6 +1885,7 @@ tds_status launch_segmented(const tds_plan *p, int which, const void *in, void *
     const DevOp &op = which ? p->seg_adj : p->seg;
     if (!op.P || op.adjoint) return TDS_ERR_ARG;
     if (p->dtype == TDS_F64) return launch_segmented_t<TrF64>(op, in, out, ws, st);
+    if (op.e64) return launch_segmented_t<TrF32c>(op, in, out, ws, st);
     return launch_segmented_t<TrF32>(op, in, out, ws, st);
 }
 

@@ -29,6 +29,20 @@ __global__ void __launch_bounds__(kStreamWarps * 32) k_decouple(const __grid_con
     const T *src = in + (size_t)g * n * kSZ + lane;
     T *row = out + (size_t)g * n * kSZ + (size_t)J0 * kSZ + lane;
     T dprev = T(0);
+    // FP32 sweeps of closed lines take the four rows at each end of the line in FP64: the
+    // closure makes the chunk ends ill-conditioned (an error at row 1 reaches row 0 multiplied
+    // by about 100 for the second derivative); h64 keeps the first chunk's forward values of
+    // rows 0..3, xl the last chunk's d_{m-1}
+    const bool e64 = sizeof(T) == 4 && op.e64;
+    const bool head = e64 && k == 0, tail = e64 && k == op.P - 1;
+    double h64[4] = {0.0, 0.0, 0.0, 0.0}, d64 = 0.0;
+    auto step64 = [&](int j, double s) {
+        d64 = rowc<double>(op, kF, cls, j) * (s - rowc<double>(op, kR, cls, j) * d64);
+        if (j < 4) h64[j] = d64;
+        dprev = T(d64);
+        row[(size_t)j * kSZ] = dprev;
+    };
+    const int ja = head ? 4 : 0, jz = tail ? m - 4 : m;
     if (!ADJ) {
         T win[kTaps];
 #pragma unroll
@@ -36,38 +50,76 @@ __global__ void __launch_bounds__(kStreamWarps * 32) k_decouple(const __grid_con
             const int r = line_row(op, J0 - 3 + i);
             win[i] = (r >= 0) ? __ldg(src + (size_t)r * kSZ) : T(0);
         }
-#pragma unroll 4
-        for (int j = 0; j < m; ++j) {
-            const T s = stencil<T>(op, J0 + j, win);
-            const T d = rowc<T>(op, kF, cls, j) * (s - rowc<T>(op, kR, cls, j) * dprev);
-            row[(size_t)j * kSZ] = d;
-            dprev = d;
+        auto slide = [&](int j) {
 #pragma unroll
             for (int i = 0; i < kTaps - 1; ++i) win[i] = win[i + 1];
             const int r = line_row(op, J0 + j + 4);
             win[kTaps - 1] = (r >= 0) ? __ldg(src + (size_t)r * kSZ) : T(0);
+        };
+        auto rows64 = [&](int jb) {
+            for (int j = jb; j < jb + 4; ++j) {
+                const int J = J0 + j, e = (J < kEdgeRows) ? J : kEdgeRows + J - (n - kEdgeRows);
+                double s = 0.0;
+#pragma unroll
+                for (int o = 0; o < kTaps; ++o) s = ::fma(op.edge[e][o], (double)win[o], s);
+                step64(j, s);
+                slide(j);
+            }
+        };
+        if (head) rows64(0);
+#pragma unroll 4
+        for (int j = ja; j < jz; ++j) {
+            const T s = stencil<T>(op, J0 + j, win);
+            const T d = rowc<T>(op, kF, cls, j) * (s - rowc<T>(op, kR, cls, j) * dprev);
+            row[(size_t)j * kSZ] = d;
+            dprev = d;
+            slide(j);
+        }
+        if (tail) {
+            d64 = (double)dprev;
+            rows64(m - 4);
         }
     } else {
         const T *gsrc = src + (size_t)J0 * kSZ;
+        if (head)
+            for (int j = 0; j < 4; ++j) step64(j, (double)__ldg(gsrc + (size_t)j * kSZ));
 #pragma unroll 4
-        for (int j = 0; j < m; ++j) {
+        for (int j = ja; j < jz; ++j) {
             const T d = rowc<T>(op, kF, cls, j) * (__ldg(gsrc + (size_t)j * kSZ) - rowc<T>(op, kR, cls, j) * dprev);
             row[(size_t)j * kSZ] = d;
             dprev = d;
         }
+        if (tail) {
+            d64 = (double)dprev;
+            for (int j = m - 4; j < m; ++j) step64(j, (double)__ldg(gsrc + (size_t)j * kSZ));
+        }
     }
+    const double xl = d64;
+    const int jlo = head ? 4 : 1;
     T dnext = row[(size_t)(m - 2) * kSZ];
 #pragma unroll 4
-    for (int j = m - 3; j >= 1; --j) {
+    for (int j = m - 3; j >= jlo; --j) {
         const T d = row[(size_t)j * kSZ] - rowc<T>(op, kW, cls, j) * dnext;
         row[(size_t)j * kSZ] = d;
         dnext = d;
     }
-    const T d0 = T(__ldg(op.n1 + cls)) * (row[0] - rowc<T>(op, kW, cls, 0) * dnext);
-    row[0] = d0;
     double *e = ends + ((size_t)gw * 2) * kSZ + lane;
-    e[0] = double(d0);
-    e[kSZ] = double(row[(size_t)(m - 1) * kSZ]);
+    if (head) {
+        // rows min(3, m-3)..1 of the backward pass and row 0 in FP64
+        double dn = (m - 2 >= 4) ? (double)dnext : h64[m - 2];
+        for (int j = (m - 3 < 3 ? m - 3 : 3); j >= 1; --j) {
+            dn = h64[j] - rowc<double>(op, kW, cls, j) * dn;
+            row[(size_t)j * kSZ] = T(dn);
+        }
+        const double d0 = __ldg(op.n1 + cls) * (h64[0] - rowc<double>(op, kW, cls, 0) * dn);
+        row[0] = T(d0);
+        e[0] = d0;
+    } else {
+        const T d0 = T(__ldg(op.n1 + cls)) * (row[0] - rowc<T>(op, kW, cls, 0) * dnext);
+        row[0] = d0;
+        e[0] = double(d0);
+    }
+    e[kSZ] = tail ? xl : double(row[(size_t)(m - 1) * kSZ]);
     if (ADJ) {
         T *hl = halo + (size_t)gw * 6 * kSZ + lane;
 #pragma unroll
