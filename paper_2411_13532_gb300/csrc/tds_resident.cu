@@ -997,7 +997,7 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_multi(const __g
         if (ok) read_halo<Tr, 1, false>(op, TileView<S>{tile, 0, n, in + gofs}, xs, k, c, hb, ha, unsafe);
         __syncthreads();
         if (failed) {
-            // let this round's copies land before the CTA's shared memory is released
+            // let this operator's copies land before the CTA's shared memory is released
             for (int q = threadIdx.x; q < P; q += blockDim.x) mbar_wait(&bars[q], par);
             if (threadIdx.x == 0) record_timeout();
             return;
