@@ -233,8 +233,11 @@ TDS_API tds_status tds_solve(const tds_plan *plan, const void *d, void *x, void 
  * runs RESIDENT with the same chunks and CTA width and every operator has the forward form
  * (derivatives, and adjoints on periodic lines), one kernel computes them all from a single
  * read of `in` (the field is read from HBM once and each result written once; Sec. 5 fuses the
- * transport equation's derivative operators the same way); otherwise the operators run one
- * after another on `stream`.  Results are those of the single calls.
+ * transport equation's derivative operators the same way): one CTA per (group of lines,
+ * operator), the operators' CTAs of a group adjacent so that they share the input through L2
+ * (the environment variable TDS_MULTI_FORM=seq selects one CTA per group sweeping the operators
+ * in turn, for tuning); otherwise the operators run one after another on `stream`.  Results are
+ * bitwise those of the single calls.
  *   plans   : count plans over the same field shape, direction and dtype (TDS_ERR_ARG otherwise).
  *   adjoint : count flags, 0 or 1.
  *   in, outs: device arrays as in tds_deriv; no output may overlap `in` or another output
