@@ -252,10 +252,21 @@ def test_solve_split_groups(width):
         assert mx <= TOL["f64"], (bc, mx, rms)
 
 
+@pytest.fixture(params=["ilv", "seq"])
+def multi_form(request, monkeypatch):
+    """Both forms of the fused pass: one CTA per (unit, operator) (the default) and one CTA per
+    unit sweeping the operators in turn (TDS_MULTI_FORM=seq, read at every launch)."""
+    if request.param == "seq":
+        monkeypatch.setenv("TDS_MULTI_FORM", "seq")
+    else:
+        monkeypatch.delenv("TDS_MULTI_FORM", raising=False)
+    return request.param
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("bc", ["periodic", "closed"])
 @pytest.mark.parametrize("width", [None, 16, 8])
-def test_multi_operator_pass_matches_single_calls(dtype, bc, width):
+def test_multi_operator_pass_matches_single_calls(dtype, bc, width, multi_form):
     """tds_deriv_multi (D1, D2 and D1^T of one input; one fused pass when the operators have
     the forward form, one after another otherwise) gives bitwise the single calls' results."""
     shape = (16, 48, 64)
