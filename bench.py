@@ -78,6 +78,9 @@ def parse():
                     help="time the momentum-transport right-hand side (Sec. 5) instead of the "
                          "derivative step: one JSON line")
     ap.add_argument("--nu", type=float, default=1e-3)
+    ap.add_argument("--thomas", action="store_true",
+                    help="the plain Thomas kernel (tds_deriv_thomas) beside the DistD2 kernels at P = 8 "
+                         "and P = 1, 512^3 x lines, FP64 and FP32, periodic and closed, D1 and D2")
     ap.add_argument("--nsweep", action="store_true",
                     help="the single-rank sweep over the line length n = 32..8192 (one JSON line per "
                          "case): first derivative along x, 2^30 points, P = 1 and 8, FP64 and FP32, "
@@ -531,6 +534,72 @@ def run_sweep(args):
         raise RuntimeError("device status after the sweep")
 
 
+# ----------------------------------------------------------- plain Thomas beside DistD2
+
+def run_thomas(args):
+    """The single-rank baseline of the paper's bandwidth table (Table BW): the plain Thomas
+    algorithm on whole lines (one thread per line; cyclic lines: Sherman-Morrison, a third pass)
+    beside the resident DistD2 kernels at P = 8 and P = 1, each the median of the timed launches
+    with a 2x-L2 write between launches.  Algorithmic traffic 2 fields per operator; the Thomas
+    kernel moves 4 (closed) or 6 (cyclic), DistD2 resident 2."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_13532_gb300 as tds
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(2 * 135 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    S = args.size
+    shape = (S, S, S)
+    npts = S ** 3
+    reps = max(args.steps, 5)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        times = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        return statistics.median(times)
+    with ClockSampler(0) as clk:
+        for dname, dt in (("f64", torch.float64), ("f32", torch.float32)):
+            x = (torch.rand(npts, dtype=dt, device=dev) - 0.5) * 2
+            y = torch.empty_like(x)
+            es = x.element_size()
+            for bc in ("periodic", "closed"):
+                for order in (1, 2):
+                    row = {"case": "thomas_vs_distd2", "size": S, "dtype": dname, "op": "D%d" % order, "bc": bc}
+                    p8 = tds.Plan(shape, "x", order, bc, P=args.P, dtype=dt)
+                    p1 = tds.Plan(shape, "x", order, bc, P=1, dtype=dt)
+                    w8, w1 = p8.workspace(), p1.workspace()
+                    for key, fn, moved in (("thomas", lambda: p8.thomas(x, y), 6 if bc == "periodic" else 4),
+                                           ("distd2_P%d" % args.P, lambda: p8.deriv(x, y, w8), 2),
+                                           ("distd2_P1", lambda: p1.deriv(x, y, w1), 2)):
+                        ms = timed(fn)
+                        alg = 2 * es * npts / (ms * 1e-3) / 1e9
+                        row[key] = {"ms": round(ms, 4), "gpoints_s": round(npts / (ms * 1e-3) / 1e9, 2),
+                                    "alg_GB_s": round(alg, 1), "hbm_frac": round(alg / hbm, 4),
+                                    "moved_fields": moved, "moved_hbm_frac": round(alg * moved / 2 / hbm, 4)}
+                    row["variants"] = {"P%d" % args.P: p8.variant, "P1": p1.variant}
+                    row["peak_source"] = peak_kind
+                    print(json.dumps(row), flush=True)
+                    del p8, p1, w8, w1
+            del x, y
+            torch.cuda.empty_cache()
+    print(json.dumps({"case": "thomas_vs_distd2", "clocks": clk.summary()}), flush=True)
+    if tds.device_status() != 0:
+        raise RuntimeError("device status after the Thomas comparison")
+
+
 # ----------------------------------------------------------- line-length sweep (single rank)
 
 def run_nsweep(args):
@@ -906,6 +975,9 @@ def main():
         return
     if args.nsweep:
         run_nsweep(args)
+        return
+    if args.thomas:
+        run_thomas(args)
         return
     if world > 1:
         import torch

@@ -228,6 +228,24 @@ TDS_API tds_status tds_solve(const tds_plan *plan, const void *d, void *x, void 
                      void *stream);
 
 /*
+ * tds_deriv_thomas -- the plan's operator (derivative, filter or interpolation; not its
+ * adjoint) by the plain Thomas algorithm (Algorithm 1) on each whole line, the single-rank
+ * baseline DistD2 is measured against (Table BW): one thread per line, the stencil right-hand
+ * side fused into the forward pass, the forward values kept in `out` and read back by the
+ * backward pass; cyclic lines by Sherman-Morrison (Sec. 2.1): Thomas on the modified matrix A'
+ * then a third pass x = y - (v.y / (1 + v.z)) z with z = A'^{-1} u from the planner.  The
+ * plan's chunking and variant are ignored.  FP32 plans run every step in FP32 (no FP64 chunk-end
+ * system: there is none).
+ *   plan   : a derivative, filter or interpolation plan; a band plan, or one whose whole-line
+ *            elimination meets a zero pivot, gives TDS_ERR_ARG.
+ *   in, out: device arrays in the plan's direction layout, 16-byte aligned, not overlapping
+ *            (TDS_ERR_ALIAS).  No workspace.
+ * HBM traffic: `in` read once, `out` written twice and read once (cyclic lines: once more
+ * each), against one read and one write for the resident DistD2 kernels.
+ */
+TDS_API tds_status tds_deriv_thomas(const tds_plan *plan, const void *in, void *out, void *stream);
+
+/*
  * tds_deriv_multi -- several operators of one input: outs[i] = plans[i]'s derivative
  * (adjoint[i] = 0) or its adjoint (adjoint[i] = 1) of `in`, 1 <= count <= 4.  When every plan
  * runs RESIDENT with the same chunks and CTA width and every operator has the forward form

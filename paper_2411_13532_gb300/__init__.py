@@ -173,6 +173,20 @@ class Plan:
         """x = A^{-1} d: the tridiagonal solve of this plan's compact scheme alone (``tds_solve``)."""
         return self._run(_lib.lib().tds_solve, d, out, ws, stream, "tds_solve")
 
+    def thomas(self, x, out=None, stream=None):
+        """``tds_deriv_thomas``: this plan's operator by the plain Thomas algorithm on whole lines
+        (cyclic lines: Sherman-Morrison), the single-rank baseline of the DistD2 kernels."""
+        _check_tensor(x, self.dtype, self.numel, "input")
+        if out is None:
+            out = torch.empty_like(x)
+        _check_tensor(out, self.dtype, self.numel, "out")
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.lib().tds_deriv_thomas(self._handle, ctypes.c_void_p(x.data_ptr()),
+                                                   ctypes.c_void_p(out.data_ptr()),
+                                                   _stream_ptr(stream, self.device)),
+                       "tds_deriv_thomas")
+        return out
+
     def deriv_host(self, host_in, host_out, d_in, d_out, ws=None, stream=None):
         """``tds_deriv_host``: host_in (a host tensor, or None when d_in already holds the input)
         through d_in / d_out to host_out, copies pipelined with the compute inside the call."""

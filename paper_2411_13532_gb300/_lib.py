@@ -33,6 +33,7 @@ SIGNATURES = [
     ("tds_deriv", _i, [_vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_deriv_adjoint", _i, [_vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_solve", _i, [_vp, _vp, _vp, _vp, _sz, _vp]),
+    ("tds_deriv_thomas", _i, [_vp, _vp, _vp, _vp]),
     ("tds_deriv_multi", _i, [_i, ctypes.POINTER(_vp), _ip, _vp, ctypes.POINTER(_vp), _vp, _sz, _vp]),
     ("tds_transport", _i, [_vp, _vp, _vp, _vp, _d, _vp, _vp]),
     ("tds_deriv_host", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),

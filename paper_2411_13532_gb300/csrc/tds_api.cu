@@ -513,6 +513,14 @@ tds_status tds_solve(const tds_plan *p, const void *d, void *x, void *ws, size_t
     return run(p, 2, d, x, ws, ws_bytes, stream);
 }
 
+tds_status tds_deriv_thomas(const tds_plan *p, const void *in, void *out, void *stream) {
+    if (!p || !in || !out || p->band || !p->thomas_mem) return TDS_ERR_ARG;
+    if (!aligned(in, 16) || !aligned(out, 16)) return TDS_ERR_ARG;
+    const size_t bytes = (size_t)p->n * p->nlines * elem_size(p->dtype);
+    if (overlaps(in, bytes, out, bytes)) return TDS_ERR_ALIAS;
+    return launch_thomas(p, in, out, static_cast<cudaStream_t>(stream));
+}
+
 tds_status tds_deriv_multi(int count, const tds_plan *const *plans, const int *adjoint, const void *in,
                            void *const *outs, void *ws, size_t ws_bytes, void *stream) {
     if (count < 1 || count > kMaxMulti || !plans || !adjoint || !outs) return TDS_ERR_ARG;
@@ -618,6 +626,7 @@ void tds_plan_destroy(tds_plan *p) {
     if (p->copy_in) cudaStreamDestroy(p->copy_in);
     if (p->copy_out) cudaStreamDestroy(p->copy_out);
     if (p->dmem) cudaFree(p->dmem);
+    if (p->thomas_mem) cudaFree(p->thomas_mem);
     std::free(p->hmem);
     delete p;
 }

@@ -132,6 +132,12 @@ struct tds_plan {
     tds_plan *sub;         // AUTO, FP32: the same operator on finer chunks (P x 2^k), run in this
                            // plan's place when this plan's resident CTAs would be too thin; NULL
     bool is_sub;           // this plan is another plan's `sub` (it gets none of its own)
+    // tds_deriv_thomas: the whole-line Thomas records (device, one allocation): [n] folded
+    // forward records {f t0, f t1, f t2, f a} (FP64, then FP32 with f tapsum for t0 on
+    // symmetric taps), [n] {f, c'} (FP64, FP32), and on cyclic lines z = A'^{-1} u (FP64, FP32);
+    // thomas_ratio = A[0][n-1] / gamma, thomas_inv_den = 1 / (1 + v.z) (Sherman-Morrison)
+    void *thomas_mem;
+    double thomas_ratio, thomas_inv_den;
     void *dmem;            // one device allocation holding every array of both operators
     void *hmem;            // host copies (reduced coefficients)
 };
@@ -167,6 +173,9 @@ tds_status launch_streaming(const tds_plan *p, int which, const void *in, void *
                             void *ws, cudaStream_t st);
 tds_status launch_reduced_only(const tds_plan *p, const double *rhs, double *x,
                                cudaStream_t st);
+// The plain Thomas algorithm on whole lines (tds_thomas.cu), stencil fused, cyclic lines by
+// Sherman-Morrison; the plan's Thomas records must exist (p->thomas_mem).
+tds_status launch_thomas(const tds_plan *p, const void *in, void *out, cudaStream_t st);
 tds_status launch_reorder(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
                           tds_layout to, size_t elem, cudaStream_t st);
 // out += the reorder of in (the accumulation of a direction's result into another layout).

@@ -419,6 +419,85 @@ static double end_gain(const LineOperator &L, int n) {
     return g;
 }
 
+// Records of the plain Thomas algorithm on whole lines (Algorithm 1), stencil fused into the
+// forward pass; cyclic lines (Sec. 2.1): Sherman-Morrison with A = A' + u v^T, gamma = -b_0,
+// u = (gamma, 0, ..., 0, A[n-1][0]), v = (1, 0, ..., 0, A[0][n-1] / gamma), so that
+// x = y - (v.y / (1 + v.z)) z with A' y = d and A' z = u.  Device layout in tds_plan::thomas_mem.
+static tds_status build_thomas(tds_plan *p, const LineOperator &L, const DevOp &op) {
+    const int n = p->n;
+    const bool periodic = (p->bc == TDS_BC_PERIODIC);
+    std::vector<double> a(L.a), b(L.b), c(L.c);
+    double ratio = 0.0, gamma = 0.0;
+    const double top = L.a[0], bot = L.c[n - 1];   // A[0][n-1], A[n-1][0] on cyclic lines
+    if (periodic) {
+        gamma = -b[0];
+        if (gamma == 0.0) return TDS_ERR_ARG;
+        b[0] -= gamma;
+        b[n - 1] -= top * bot / gamma;
+        ratio = top / gamma;
+    }
+    a[0] = 0.0;
+    c[n - 1] = 0.0;
+    std::vector<double> f(n), cp(n);
+    for (int j = 0; j < n; ++j) {
+        const double den = b[j] - (j > 0 ? a[j] * cp[j - 1] : 0.0);
+        if (den == 0.0 || !std::isfinite(den)) return TDS_ERR_ARG;
+        f[j] = 1.0 / den;
+        cp[j] = c[j] * f[j];
+    }
+    std::vector<double> z;
+    double inv_den = 0.0;
+    if (periodic) {
+        z.assign(n, 0.0);
+        for (int j = 0; j < n; ++j) {
+            const double u = (j == 0) ? gamma : (j == n - 1 ? bot : 0.0);
+            z[j] = f[j] * (u - (j > 0 ? a[j] * z[j - 1] : 0.0));
+        }
+        for (int j = n - 2; j >= 0; --j) z[j] -= cp[j] * z[j + 1];
+        const double den = 1.0 + z[0] + ratio * z[n - 1];
+        if (den == 0.0 || !std::isfinite(den)) return TDS_ERR_ARG;
+        inv_den = 1.0 / den;
+    }
+    const bool sym = (op.symmetric == 1 || op.symmetric == 4);
+    const size_t nz = periodic ? (size_t)n : 0;
+    // [rec64 n x 4][fc64 n x 2][z64 n][rec32 n x 4][fc32 n x 2][z32 n]
+    const size_t bytes64 = ((size_t)n * 6 + nz) * sizeof(double), bytes32 = ((size_t)n * 6 + nz) * sizeof(float);
+    const size_t off32 = (bytes64 + 255) & ~(size_t)255;
+    std::vector<unsigned char> host(off32 + bytes32, 0);
+    double *r64 = reinterpret_cast<double *>(host.data());
+    float *r32 = reinterpret_cast<float *>(host.data() + off32);
+    for (int j = 0; j < n; ++j) {
+        const double rec[4] = {f[j] * op.tap[3], f[j] * op.tap[4], f[j] * op.tap[5], f[j] * a[j]};
+        for (int q = 0; q < 4; ++q) {
+            r64[4 * (size_t)j + q] = rec[q];
+            r32[4 * (size_t)j + q] = (float)rec[q];
+        }
+        if (sym) r32[4 * (size_t)j] = (float)(f[j] * op.tapsum);
+        r64[4 * (size_t)n + 2 * (size_t)j] = f[j];
+        r64[4 * (size_t)n + 2 * (size_t)j + 1] = cp[j];
+        r32[4 * (size_t)n + 2 * (size_t)j] = (float)f[j];
+        r32[4 * (size_t)n + 2 * (size_t)j + 1] = (float)cp[j];
+        if (periodic) {
+            r64[6 * (size_t)n + j] = z[j];
+            r32[6 * (size_t)n + j] = (float)z[j];
+        }
+    }
+    void *d = nullptr;
+    const cudaError_t e = cudaMalloc(&d, host.size());
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? TDS_ERR_NOMEM : TDS_ERR_CUDA;
+    }
+    if (cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return TDS_ERR_CUDA;
+    }
+    p->thomas_mem = d;
+    p->thomas_ratio = ratio;
+    p->thomas_inv_den = inv_den;
+    return TDS_OK;
+}
+
 tds_status build_plan(tds_plan *p) {
     const bool periodic = (p->bc == TDS_BC_PERIODIC);
     LineOperator L, LT;
@@ -525,6 +604,11 @@ tds_status build_plan(tds_plan *p) {
         p->red_sup_host[w] = hm + (size_t)(2 * w + 1) * R;
         std::memcpy(p->red_sub_host[w], sub[w].data(), sizeof(double) * R);
         std::memcpy(p->red_sup_host[w], sup[w].data(), sizeof(double) * R);
+    }
+    // the whole-line Thomas records (tds_deriv_thomas); a zero pivot there only disables that call
+    if (!p->band) {
+        const tds_status ts = build_thomas(p, L, p->op[0]);
+        if (ts == TDS_ERR_NOMEM || ts == TDS_ERR_CUDA) return ts;
     }
     return TDS_OK;
 }
