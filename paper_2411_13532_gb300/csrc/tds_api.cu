@@ -118,9 +118,11 @@ tds_status launch(const tds_plan *p, int which, const void *in, void *out, void 
     if (p->variant == TDS_VARIANT_PIPELINED) return launch_pipelined(p, which, in, out, st);
     if (p->variant == TDS_VARIANT_SEGMENTED) {
         // the adjoint: on the segment partition when it has the forward form (periodic lines),
-        // else resident when a CTA can hold the lines, else the streaming pipeline
+        // else resident when CTAs holding the lines leave at least 4 warps per SM (measured, FP64
+        // closed lines of 512 at P = 1: one 32-thread CTA per SM took 8.3 ms where the forward
+        // pass takes 1.9), else the streaming pipeline
         if (which == 0 || p->seg_adj.P) return launch_segmented(p, which, in, out, ws, st);
-        if (p->resident_smem) return launch_resident(p, which, in, out, st);
+        if (p->resident_smem && resident_warps_per_sm(p) >= 4) return launch_resident(p, which, in, out, st);
     }
     return launch_streaming(p, which, in, out, ws, st);
 }

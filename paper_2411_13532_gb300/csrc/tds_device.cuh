@@ -126,8 +126,8 @@ template <typename T>
 __device__ __forceinline__ T stencil(const DevOp &op, int J, const T (&w)[kTaps]) {
     if (!op.periodic && (J < kEdgeRows || J >= op.n - kEdgeRows)) {
         const int e = (J < kEdgeRows) ? J : kEdgeRows + J - (op.n - kEdgeRows);
-        // the row's form (DevOp::edge_form), as in the resident sweep
-        const int form = op.edge_form[e];
+        // the row's form (DevOp::edge_form; FP64: the taps as written), as in the resident sweep
+        const int form = (sizeof(T) == 8) ? 0 : op.edge_form[e];
         T s = T(0);
         if (form == 2) {
             T a[kTaps - 1];

@@ -192,7 +192,9 @@ template <typename Tr, int V>
 __device__ __forceinline__ void estencil(const DevOp &op, int e, const Pack<typename Tr::A, V> (&w)[kTaps],
                                          typename Tr::A (&s)[V]) {
     using A = typename Tr::A;
-    const int form = op.edge_form[e];
+    // FP64 sweeps take the taps as written: their cancellation stays far below the FP64 bar, and
+    // the direct form has the fewest FP64 operations (closure rows run on few lanes of a warp)
+    const int form = (sizeof(A) == 8) ? 0 : op.edge_form[e];
 #pragma unroll
     for (int i = 0; i < V; ++i) s[i] = Tr::from_d(0.0);
     if (form == 2) {          // sum_k d_k (a_k - a_{k-1}), a_k = v[J+k-2] - v[J+k-3]
