@@ -282,10 +282,11 @@ __device__ __forceinline__ void fwd_row(const DevOp &op, int cls, int j, typenam
     Tr::template st_mid<V>(row + (size_t)j * Tr::W, dprev);
 }
 
-// FP32 sweeps of closed lines: the closure makes the chunk ends ill-conditioned -- an error in
+// FP32 sweeps of closed lines: a closure can make the chunk ends ill-conditioned -- an error in
 // the right-hand side or the forward value of row 1 (n-2) reaches the solution at row 0 (n-1)
-// multiplied by about 100 for the second derivative (f''_0 + 11 f''_1 = ...).  So the FP32
-// sweeps take the four closure rows at each end of the line in FP64: their right-hand sides from
+// multiplied by about 100 for the second derivative (f''_0 + 11 f''_1 = ...).  Where the planner
+// finds such a gain (DevOp::e64; the kernels are the TrNative<float, W, true> instantiations),
+// the FP32 sweeps take the four closure rows at each end of the line in FP64: their right-hand sides from
 // the (exact) FP32 inputs, their forward steps with the FP64 records, and the quantities the
 // reduced system receives from them -- x0 = d_0 - w_0 sum_{j<4} pi_j d_j of the first chunk,
 // row 0's value before the rest of S joins it, and the last forward value xl when it belongs to
