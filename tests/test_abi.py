@@ -73,6 +73,7 @@ def test_null_pointer_errors_need_no_gpu(L):
     assert L.tds_deriv(None, None, None, None, 0, None) == _lib.ERR_ARG
     assert L.tds_deriv_adjoint(None, None, None, None, 0, None) == _lib.ERR_ARG
     assert L.tds_solve(None, None, None, None, 0, None) == _lib.ERR_ARG
+    assert L.tds_deriv_thomas(None, None, None, None) == _lib.ERR_ARG
     h = ctypes.c_void_p()
     assert L.tds_plan_create_band(ctypes.byref(h), 64, 64, 64, 0, None, None, None, 0, 1, 0, 32, 0) == _lib.ERR_ARG
     assert L.tds_plan_create_band(None, 64, 64, 64, 0, None, None, None, 0, 1, 0, 32, 0) == _lib.ERR_ARG
