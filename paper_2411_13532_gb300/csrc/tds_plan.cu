@@ -392,7 +392,7 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
 
 // How much an FP32 rounding near a closed line's ends can grow in the solve: the largest |entry|
 // of A^{-1} and of A^{-T} in the four columns at each end (Thomas solves of unit vectors in
-// FP64).  Closures such as f''_0 + 11 f''_1 make it about 100, f'_0 + 2 f'_1 about 4.
+// FP64).  Closures such as f''_0 + 11 f''_1 make it about 93, f'_0 + 2 f'_1 about 5, the filter's about 2.
 static double end_gain(const LineOperator &L, int n) {
     std::vector<double> cp(n), x(n);
     double g = 0.0;
