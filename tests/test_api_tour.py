@@ -1,5 +1,5 @@
-"""The calls of the README's API tour, on a small grid (GPU): every public entry point a user
-starts with runs and agrees with the others."""
+"""A tour of the public API on a small grid (GPU): every entry point a user starts with runs
+and agrees with the others."""
 import pytest
 import torch
 
