@@ -9,16 +9,19 @@ FP32 storage:
 i.e. 18 directional operators of 512^3 points and 4 reorders.  The three operators of one
 direction share one read of the field (``tds_deriv_multi``: one fused pass).  ``value`` is
 directional-derivative points per second (Gpoints/s) over all ranks, with the field resident in
-HBM; every field is 0.5-1 GiB, larger than L2, so no flush is needed between steps.  After the
-timed steps each operator is also timed on its own (``breakdown`` entries ``single/...``).
+HBM; every field is 0.5-1 GiB, larger than L2, so no flush is needed between steps.
+``value_f64`` / ``value_f32`` (and ``by_precision``) split it: the nine operators of each
+precision over the time of that precision's launches.  After the timed steps each operator is
+also timed on its own (``breakdown`` entries ``single/...``).
 
 ``e2e`` repeats the step through host buffers: the x-layout field comes from pinned host
 memory each step (``tds_deriv_host`` copies it in for the first operator) and every one of
 the 18 results is copied back to pinned host memory by the host entry points, whose copies
 overlap the compute slab by slab.
 
-``--impl reference`` times the FP64 CPU oracle (plain C, one core) on a bounded sample of the
-same workload (slabs of lines along each direction), with the same metric.
+``--impl reference`` times the FP64 CPU oracle (plain C) on every host core, one spawn-pool
+process per core, on a bounded sample of the same workload (slabs of lines along each
+direction), with the same metric.
 
 Multi-GPU (torchrun): every rank runs the same workload on its own field (independent
 problems: weak scaling, no data exchange); timing is max over ranks.
@@ -343,6 +346,18 @@ def run_ours(args, rank, world, local_rank):
             breakdown[tag + "/".join(str(k) for k in key)] = {
                 "ms": round(avg_ms, 4), "gpoints_s": round(pts / (avg_ms * 1e-3) / 1e9, 2),
                 "alg_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+    # the headline split by precision: each precision's launches of the timed step (three fused
+    # passes, two reorders) and the nine directional derivatives they compute
+    by_precision = {}
+    for name, _ in dtypes:
+        keys = [k for k in per if k[0] == name]
+        ms_p = sum(per[k] * len(timing[k]) for k in keys) / args.steps
+        bytes_p = sum(algorithmic(k)[1] * len(timing[k]) for k in keys) / args.steps
+        by_precision[name] = {
+            "gpoints_s": round(job_throughput(world, ops_per_step // 2, npts, 1, ms_p), 3),
+            "ms_per_step": round(ms_p, 4),
+            "alg_GB_s": round(bytes_p / (ms_p * 1e-3) / 1e9, 1),
+            "hbm_frac": round(bytes_p / (ms_p * 1e-3) / 1e9 / hbm, 4)}
     # dominant kernel of the timed step by total time
     totals = {k: per[k] * len(timing[k]) for k in per}
     dom = max(totals, key=totals.get)
@@ -421,7 +436,7 @@ def run_ours(args, rank, world, local_rank):
     status = tds.device_status()
     if status != 0:
         raise RuntimeError("device status %d after the timed region" % status)
-    return {"value": value, "ms": ms, "roofline": roofline, "breakdown": breakdown,
+    return {"value": value, "ms": ms, "roofline": roofline, "breakdown": breakdown, "by_precision": by_precision,
             "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches}
 
 
@@ -998,6 +1013,9 @@ def main():
         S = args.size
         line = {
             "metric": METRIC, "value": round(res["value"], 3), "unit": UNIT, "n_gpus": world,
+            "value_f64": res["by_precision"]["f64"]["gpoints_s"],
+            "value_f32": res["by_precision"]["f32"]["gpoints_s"],
+            "by_precision": res["by_precision"],
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(res["ms"] / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",

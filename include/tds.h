@@ -385,12 +385,14 @@ TDS_API tds_status tds_reduced_solve(const tds_plan *plan, const double *rhs, do
  * exits) and allocates nothing.
  *   plan    : an existing plan (created beforehand; plan creation itself allocates).
  *   in, out : as in tds_deriv (device, 16-byte aligned, non-overlapping: TDS_ERR_ALIAS).
- * Always runs the three-kernel streaming pipeline.  Its chunk ends need 16*N*P bytes; a plan
- * needing more than TDS_NOALLOC_SCRATCH_BYTES (N*P > 1,048,576 lines x chunks) is rejected
- * with TDS_ERR_WORKSPACE before any launch.
+ * Always runs the three-kernel streaming pipeline on the plan's own P chunks (an AUTO FP32
+ * plan that tds_deriv runs on finer chunks gives the same result to rounding).  Its chunk ends
+ * need 16*N*P bytes; a plan needing more than TDS_NOALLOC_SCRATCH_BYTES (N*P > 1,048,576
+ * lines x chunks) is rejected with TDS_ERR_WORKSPACE before any launch.
  * The first call on each device looks up the array's device address with that device
- * current (cudaGetSymbolAddress) and caches it; make that first call before any stream
- * capture.  All calls share the one array, which keeps the last call's contents (nothing in
+ * current (cudaGetSymbolAddress) and caches it with the driver's identity of the context; a
+ * new context on the device (after cudaDeviceReset) gets a fresh lookup.  Make the first
+ * call on a device, and the first after a reset, before any stream capture.  All calls share the one array, which keeps the last call's contents (nothing in
  * it needs to start at zero): calls that overlap on the GPU -- concurrent streams, or
  * several host threads -- race on it and must be serialised by the caller.
  */

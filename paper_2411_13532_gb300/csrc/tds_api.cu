@@ -7,7 +7,8 @@
 //   variant : AUTO = resident when the lines fit a CTA, unless FP64 CTAs would leave < 6 warps per
 //             SM (then segmented); segmented when they do not fit; else streaming;
 //   sub     : AUTO, FP32, resident CTAs with < 8 warps per SM: a finer-chunk copy of the plan runs in
-//             its place (make_sub); every entry point launches through eff(plan).
+//             its place (make_sub); every entry point launches through eff(plan), except
+//             tds_deriv_noalloc (tds_noalloc.cu), which runs the plan's own chunks.
 #include <cmath>
 #include <cstdlib>
 #include <cstring>

@@ -285,6 +285,36 @@ def test_multi_operator_pass_matches_single_calls(dtype, bc, width, multi_form):
     assert torch.equal(o2[2], refs[0]) and torch.equal(o2[3], refs[1])
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_multi_operator_pass_512_sampled_lines(dtype):
+    """The fused pass the benchmark times, at its size: 512^3, periodic, P = 8, D1, D2 and D1^T
+    of one input in one launch (one CTA per unit and operator), along x, y and z, on the
+    benchmark's field (Fourier modes up to k = 100 plus N(0, 0.1) noise).  Sampled whole lines
+    of every result against the oracle on the same (FP32-rounded for FP32) lines."""
+    shape = (512, 512, 512)
+    t = TORCH[dtype]
+    f, _ = inputs.fourier_field(shape, seed=2, kmax=100, noise=0.1, noise_kind="normal", device="cuda")
+    cart = f.to(t).reshape(-1)
+    del f
+    h = oracle.grid_spacing(512, "periodic")
+    for direction in "xyz":
+        x = tds.reorder(cart, shape, "cart", direction)
+        p1 = tds.Plan(shape, direction, 1, "periodic", P=8, h=h, dtype=t)
+        p2 = tds.Plan(shape, direction, 2, "periodic", P=8, h=h, dtype=t)
+        assert p1.variant == p2.variant == "resident" and p1.width == p2.width   # one fused launch
+        outs = tds.deriv_multi([(p1, False), (p2, False), (p1, True)], x)
+        lines = sample_lines(p1.nlines, 16, seed=40 + ord(direction))
+        src = gather_lines(x, direction, shape, lines).double().cpu().numpy()
+        refs = [oracle.deriv_lines(src, 1, "periodic", h), oracle.deriv_lines(src, 2, "periodic", h),
+                oracle.deriv_adjoint_lines(src, 1, "periodic", h)]
+        for name, o, ref in zip(("D1", "D2", "D1T"), outs, refs):
+            got = gather_lines(o, direction, shape, lines).double().cpu().numpy()
+            mx, rms = rel_errors(got, ref)
+            report("512^3 fused %s %s periodic P=8" % (name, direction), dtype=dtype, max_rel=mx, rms_rel=rms)
+            assert mx <= TOL[dtype], (direction, name, mx, rms)
+        del x, outs
+
+
 def test_multi_operator_pass_fallbacks_and_errors():
     shape = (12, 40, 32)
     x = inputs.uniform_field(shape, seed=22, device="cuda").reshape(-1)

@@ -71,8 +71,9 @@ def test_small_grid_every_point(dtype, direction, op):
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("bc", ["periodic", "closed"])
 def test_long_and_short_lines(dtype, bc):
-    """n = 8 (the smallest line) and n = 2048, both orders."""
-    for shape in ((2, 32, 8), (1, 32, 2048)):
+    """n = 8 (the smallest line: on closed lines the FP64 end rows of FP32 second derivatives
+    meet), 9 and 12 (one and four rows between them) and 2048, both orders."""
+    for shape in ((2, 32, 8), (2, 32, 9), (2, 32, 12), (1, 32, 2048)):
         cart = np.random.default_rng(3).uniform(-1, 1, shape)
         if dtype == "f32":
             cart = cart.astype(np.float32).astype(np.float64)
@@ -115,3 +116,40 @@ def test_full_size_sampled_lines(dtype, bc):
         report("512^3 thomas D%d x %s" % (order, bc), dtype=dtype, max_rel=mx, rms_rel=rms)
         assert mx <= TOL[dtype], (order, mx, rms)
         del y
+
+
+@pytest.mark.parametrize("direction", ["x", "z"])
+@pytest.mark.parametrize("order", [1, 2])
+def test_fp32_closed_smooth_every_point(order, direction):
+    """FP32 on closed lines of a smooth field (Fourier modes, kmax 20).  The second derivative's
+    closure f''_0 + 11 f''_1 = ... magnifies an FP32 rounding at row 1 or n-2 about 100-fold at
+    the end row, so FP32 plans with such a closure run the four rows at each end of the line in
+    FP64; the closure and interior taps of the FP32 rows act on differences of nearby values.
+    Every point of 512-point lines against the oracle on the FP32-rounded field."""
+    shape = (512, 32, 32) if direction == "z" else (4, 32, 512)
+    f, _ = inputs.fourier_field(shape, seed=9, kmax=20, noise=1e-3)
+    cart = f.numpy().astype(np.float32).astype(np.float64)
+    plan = make_plan(shape, direction, order, "closed", "f32")
+    y = plan.thomas(to_device_layout(cart, direction, "f32"))
+    mx, rms = rel_errors(from_device_layout(y, direction, shape), reference(cart, direction, order, "closed"))
+    report("thomas smooth D%d %s closed" % (order, direction), dtype="f32", max_rel=mx, rms_rel=rms)
+    assert mx <= TOL["f32"], (mx, rms)
+
+
+@pytest.mark.parametrize("direction", ["x", "z"])
+@pytest.mark.parametrize("order", [1, 2])
+def test_fp32_closed_smooth_512_sampled_lines(order, direction):
+    """The same at 512^3: sampled whole lines (both ends included) of a smooth field, FP32,
+    closed, against the oracle on the FP32-rounded lines."""
+    shape = (512, 512, 512)
+    f, _ = inputs.fourier_field(shape, seed=6, kmax=20, noise=1e-3, device="cuda")
+    fd = tds.reorder(f.to(torch.float32).reshape(-1), shape, "cart", direction)
+    del f
+    lines = sample_lines(fd.numel() // 512, 32, seed=13)
+    src = gather_lines(fd, direction, shape, lines).double().cpu().numpy()
+    plan = make_plan(shape, direction, order, "closed", "f32")
+    y = plan.thomas(fd)
+    got = gather_lines(y, direction, shape, lines).double().cpu().numpy()
+    mx, rms = rel_errors(got, oracle.deriv_lines(src, order, "closed", oracle.grid_spacing(512, "closed")))
+    report("512^3 thomas smooth D%d %s closed" % (order, direction), dtype="f32", max_rel=mx, rms_rel=rms)
+    assert mx <= TOL["f32"], (mx, rms)
