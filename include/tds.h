@@ -137,11 +137,12 @@ TDS_API tds_status tds_plan_create_interp(tds_plan **out, int nx, int ny, int nz
  * with a[0] coupling to x_{n-1} and c[n-1] to x_0 on periodic lines (ignored on closed lines).
  *   a, b, c : host arrays of n doubles each (n = the extent along dir), copied by the call.
  *   other arguments as in tds_plan_create.
- * The method sweeps without pivoting: the band should be diagonally dominant.  Chunks that share
- * a coefficient class must carry the same band: every chunk on periodic lines, the interior
- * chunks (1 .. P-2) on closed lines -- a uniform interior with its own first and last rows.
- * Errors: TDS_ERR_ARG for a NULL array, a non-finite entry, chunks that differ where they must
- * not, or a zero pivot; the shape rules of tds_plan_create.  Only tds_solve (and the plan
+ * The method sweeps without pivoting: the band should be diagonally dominant.  Any band is
+ * accepted, variable coefficients along the line included (non-uniform grids, variable
+ * diffusivity): the preprocessing of Algorithm 4 runs per chunk, once for every chunk when
+ * the chunks' bands differ, else once per class of equal chunks (first / interior / last).
+ * Errors: TDS_ERR_ARG for a NULL array, a non-finite entry or a zero pivot; the shape rules
+ * of tds_plan_create.  Only tds_solve (and the plan
  * queries and tuning calls) accept a band plan; the derivative calls return TDS_ERR_ARG.
  */
 TDS_API tds_status tds_plan_create_band(tds_plan **out, int nx, int ny, int nz, tds_dir dir,
@@ -392,9 +393,10 @@ TDS_API tds_status tds_reduced_solve(const tds_plan *plan, const double *rhs, do
  * The first call on each device looks up the array's device address with that device
  * current (cudaGetSymbolAddress) and caches it with the driver's identity of the context; a
  * new context on the device (after cudaDeviceReset) gets a fresh lookup.  Make the first
- * call on a device, and the first after a reset, before any stream capture.  All calls share the one array, which keeps the last call's contents (nothing in
- * it needs to start at zero): calls that overlap on the GPU -- concurrent streams, or
- * several host threads -- race on it and must be serialised by the caller.
+ * call on a device, and the first after a reset, before any stream capture.  All calls share
+ * the one array, which keeps the last call's contents (nothing in it needs to start at zero):
+ * calls that overlap on the GPU -- concurrent streams, or several host threads -- race on it
+ * and must be serialised by the caller.
  */
 TDS_API tds_status tds_deriv_noalloc(const tds_plan *plan, const void *in, void *out,
                                      void *stream);

@@ -386,25 +386,9 @@ tds_status tds_plan_create_band(tds_plan **out, int nx, int ny, int nz, tds_dir 
         return TDS_ERR_ARG;
     const tds_status sh = check_shape(nx, ny, nz, dir, P);
     if (sh != TDS_OK) return sh;
-    const int n = extent(nx, ny, nz, dir), m = n / P;
+    const int n = extent(nx, ny, nz, dir);
     for (int j = 0; j < n; ++j)
         if (!std::isfinite(a[j]) || !std::isfinite(b[j]) || !std::isfinite(c[j])) return TDS_ERR_ARG;
-    // chunks that share a class carry the same band: every chunk of a periodic line, the
-    // interior chunks (1 .. P-2) of a closed line
-    auto same = [&](int k, int r) {
-        for (int j = 0; j < m; ++j) {
-            const int x = k * m + j, y = r * m + j;
-            if (a[x] != a[y] || b[x] != b[y] || c[x] != c[y]) return false;
-        }
-        return true;
-    };
-    if (bc == TDS_BC_PERIODIC) {
-        for (int k = 1; k < P; ++k)
-            if (!same(k, 0)) return TDS_ERR_ARG;
-    } else {
-        for (int k = 2; k < P - 1; ++k)
-            if (!same(k, 1)) return TDS_ERR_ARG;
-    }
     tds_plan *p = new_plan(nx, ny, nz, dir, bc, P, dtype, mode);
     if (!p) return TDS_ERR_NOMEM;
     p->band = static_cast<double *>(std::malloc(sizeof(double) * 3 * (size_t)n));

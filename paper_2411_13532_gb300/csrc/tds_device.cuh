@@ -117,8 +117,12 @@ __device__ __forceinline__ T rowc(const DevOp &op, int arr, int cls, int j) {
 }
 
 __device__ __forceinline__ int chunk_class(const DevOp &op, int k) {
+    if (op.cls_each) return k;
     return (k == 0) ? op.cls_first : (k == op.P - 1 ? op.cls_last : op.cls_mid);
 }
+
+// Index of a chunk class's per-class scalars (cut-off rows, constant-record runs).
+__device__ __forceinline__ int scal_cls(const DevOp &op, int cls) { return op.cls_each ? 0 : cls; }
 
 // Stencil of global row J from the window w[i] = v[J - 3 + i] (Eq. cfds and its closures,
 // or the transposed taps for the adjoint).

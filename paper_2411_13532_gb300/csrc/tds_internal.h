@@ -52,6 +52,8 @@ struct DevOp {
                     // magnifies an end row's rounding by more than 16)
     int ncls;       // chunk classes (first / interior / last differ on closed lines)
     int cls_first, cls_mid, cls_last;
+    int cls_each;   // 1: every chunk is its own class (ncls = P; a band whose chunks differ), and
+                    // the per-class scalars below hold one entry (index 0) valid for all chunks
     const double *row64;  // [kNumRowArrays][ncls*m]
     const float *row32;   // the same arrays rounded to float (FP32 sweeps)
     // Row records of the resident sweep, [ncls][m] each, FP64 and FP32 copies:

@@ -8,6 +8,7 @@
 //   * the reduced chunk-end system and its factorisation (cyclic: Sherman-Morrison),
 // for A^{-1} B, its transpose B^T A^{-T} and A^{-1}, on the plan's chunks and (SEGMENTED) on the
 // segment partition.  Everything is uploaded once to the device; the kernels only read it.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -205,11 +206,36 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
     // second derivative's taps (vanishing sum) may be applied to second differences
     op.symmetric = (p->order == 1) ? -1 : (p->order == 4) ? (which == 1 ? 3 : 2) : (p->order == 2 ? 4 : 1);
 
-    // chunk classes: cyclic lines have one; closed lines distinguish first / interior / last
-    int reps[3];
-    if (periodic || P == 1) { op.ncls = 1; reps[0] = 0; op.cls_first = op.cls_mid = op.cls_last = 0; }
-    else if (P == 2) { op.ncls = 2; reps[0] = 0; reps[1] = 1; op.cls_first = 0; op.cls_mid = 0; op.cls_last = 1; }
-    else { op.ncls = 3; reps[0] = 0; reps[1] = 1; reps[2] = P - 1; op.cls_first = 0; op.cls_mid = 1; op.cls_last = 2; }
+    // chunk classes: cyclic lines have one; closed lines distinguish first / interior / last.
+    // A caller's band whose chunks differ beyond that (variable coefficients along the line)
+    // makes every chunk its own class: Algorithm 4 runs per chunk on that chunk's rows.
+    std::vector<int> reps;
+    if (periodic || P == 1) { op.ncls = 1; reps = {0}; op.cls_first = op.cls_mid = op.cls_last = 0; }
+    else if (P == 2) { op.ncls = 2; reps = {0, 1}; op.cls_first = 0; op.cls_mid = 0; op.cls_last = 1; }
+    else { op.ncls = 3; reps = {0, 1, P - 1}; op.cls_first = 0; op.cls_mid = 1; op.cls_last = 2; }
+    {
+        auto same = [&](int k, int r) {   // chunks k and r carry the same band
+            for (int j = 0; j < m; ++j) {
+                const size_t x = (size_t)k * m + j, y = (size_t)r * m + j;
+                if (L.a[x] != L.a[y] || L.b[x] != L.b[y] || L.c[x] != L.c[y]) return false;
+            }
+            return true;
+        };
+        bool uniform = true;
+        for (int k = 0; k < P && uniform; ++k) {
+            const int cl = (k == 0) ? op.cls_first : (k == P - 1 ? op.cls_last : op.cls_mid);
+            uniform = same(k, reps[cl]);
+        }
+        if (!uniform) {
+            op.ncls = P;
+            op.cls_each = 1;
+            reps.resize(P);
+            for (int k = 0; k < P; ++k) reps[k] = k;
+        }
+    }
+    auto class_of = [&](int k) {
+        return op.cls_each ? k : (k == 0) ? op.cls_first : (k == P - 1 ? op.cls_last : op.cls_mid);
+    };
 
     const int nc = op.ncls;
     rows.assign((size_t)kNumRowArrays * nc * m, 0.0);
@@ -286,6 +312,20 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
                 --j0;
             return j0;
         };
+        if (op.cls_each) {
+            // one entry for all chunks: the latest cut-off of any chunk, and no constant runs
+            // (the records of a variable band differ from row to row)
+            if (cl == 0) {
+                op.jpi64[0] = op.jsa64[0] = op.jpi32[0] = op.jsa32[0] = 0;
+                op.kfl64[0] = op.kfh64[0] = op.kbl64[0] = op.kbh64[0] = 0;
+                op.kfl32[0] = op.kfh32[0] = op.kbl32[0] = op.kbh32[0] = 0;
+            }
+            op.jpi64[0] = std::max(op.jpi64[0], cutoff(0, std::ldexp(1.0, -60)));
+            op.jsa64[0] = std::max(op.jsa64[0], cutoff(1, std::ldexp(1.0, -60)));
+            op.jpi32[0] = std::max(op.jpi32[0], cutoff(0, std::ldexp(1.0, -30)));
+            op.jsa32[0] = std::max(op.jsa32[0], cutoff(1, std::ldexp(1.0, -30)));
+            continue;
+        }
         op.jpi64[cl] = cutoff(0, std::ldexp(1.0, -60));
         op.jsa64[cl] = cutoff(1, std::ldexp(1.0, -60));
         op.jpi32[cl] = cutoff(0, std::ldexp(1.0, -30));
@@ -330,7 +370,7 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
     const int R = 2 * P;
     sub.assign(R, 0.0); sup.assign(R, 0.0);
     for (int k = 0; k < P; ++k) {
-        const int cl = (k == 0) ? op.cls_first : (k == P - 1 ? op.cls_last : op.cls_mid);
+        const int cl = class_of(k);
         const double *sa = &rows[((size_t)kSA * nc + cl) * m];
         const double *sc = &rows[((size_t)kSC * nc + cl) * m];
         sub[2 * k] = sa[0];          // row F_k: coupling to L_{k-1}

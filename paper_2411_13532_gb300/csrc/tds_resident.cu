@@ -109,17 +109,21 @@ struct TrNative {
         else return __ldg(op.fwd64 + 4 * i + 2);
     }
     static __device__ __forceinline__ int jpi(const DevOp &op, int cls) {
+        cls = scal_cls(op, cls);
         return sizeof(T) == 4 ? op.jpi32[cls] : op.jpi64[cls];
     }
     static __device__ __forceinline__ int jsa(const DevOp &op, int cls) {
+        cls = scal_cls(op, cls);
         return sizeof(T) == 4 ? op.jsa32[cls] : op.jsa64[cls];
     }
     // the run of rows [lo, hi) with the constant forward record, and that record
     static __device__ __forceinline__ void kf_run(const DevOp &op, int cls, int &lo, int &hi) {
+        cls = scal_cls(op, cls);
         lo = sizeof(T) == 4 ? op.kfl32[cls] : op.kfl64[cls];
         hi = sizeof(T) == 4 ? op.kfh32[cls] : op.kfh64[cls];
     }
     static __device__ __forceinline__ void kf(const DevOp &op, int cls, A &c0, A &c1, A &c2, A &g) {
+        cls = scal_cls(op, cls);
         if constexpr (sizeof(T) == 4) {
             c0 = op.kf32[cls][0]; c1 = op.kf32[cls][1]; c2 = op.kf32[cls][2]; g = op.kf32[cls][3];
         } else {
@@ -128,10 +132,12 @@ struct TrNative {
     }
     // the run of rows [lo, hi) with the constant back-substitution coupling s^c, and that value
     static __device__ __forceinline__ void kb_run(const DevOp &op, int cls, int &lo, int &hi) {
+        cls = scal_cls(op, cls);
         lo = sizeof(T) == 4 ? op.kbl32[cls] : op.kbl64[cls];
         hi = sizeof(T) == 4 ? op.kbh32[cls] : op.kbh64[cls];
     }
     static __device__ __forceinline__ A kb(const DevOp &op, int cls) {
+        cls = scal_cls(op, cls);
         if constexpr (sizeof(T) == 4) return op.kb32[cls];
         else return op.kb64[cls];
     }
@@ -1674,7 +1680,7 @@ tds_status launch_segmented_t(const DevOp &op, const void *in, void *out, void *
     } else {
         // the rows k_seg_ends copies in (seg_ends_rows), the largest over the chunk classes
         int rows = 0;
-        for (int cl = 0; cl < op.ncls; ++cl) {
+        for (int cl = 0; cl < (op.cls_each ? 1 : op.ncls); ++cl) {
             const int jp = op.jpi32[cl], tail = jp + 8;
             const int r = (jp + tail >= op.m || jp + 3 >= op.m - tail - 3) ? op.m : (jp + 3) + (tail + 3);
             rows = r > rows ? r : rows;
