@@ -324,6 +324,23 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
             single[(name, key, var)] = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
 
+    # the fused pass's own ceiling: a copy with its traffic shape (one read, three writes)
+    for name, _ in dtypes:
+        d = data[name]
+        fn = (lambda d=d: tds.fanout_copy(d["ux"], d["o"]))
+        for _ in range(2):
+            fn()
+        evs = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        single[(name, "fanout3", "copy")] = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+
     m_chunk = S // args.P
 
     def algorithmic(key):
@@ -332,6 +349,8 @@ def run_ours(args, rank, world, local_rank):
         es = 8 if name == "f64" else 4
         if kind == "multi":   # one read of the field, three results written
             return 3 * npts, 4 * es * npts, sum(fp64_ops_per_point(o, m_chunk) for o in ("d1", "d2", "d1t")) * npts
+        if kind == "fanout3":
+            return 3 * npts, 4 * es * npts, 0.0
         if kind == "reorder":
             return npts, 2 * es * npts, 0.0
         return npts, 2 * es * npts, fp64_ops_per_point(kind, m_chunk) * npts
@@ -385,6 +404,11 @@ def run_ours(args, rank, world, local_rank):
     # the FP32 derivative kernels on their own against HBM (the 70 % target)
     f32 = [v for k, v in breakdown.items() if k.startswith("single/f32/d")]
     roofline["f32_deriv_hbm_frac_min"] = min(e["hbm_frac"] for e in f32) if f32 else None
+    # the FP32 fused pass against a copy of the same traffic shape (one read, three writes)
+    fan = breakdown.get("single/f32/fanout3/copy")
+    mul = [v for k, v in breakdown.items() if k.startswith("f32/multi/")]
+    if fan and mul:
+        roofline["f32_multi_of_fanout_copy"] = round(fan["ms"] / mul[0]["ms"], 4)
 
     # ------------------------------------------------------------------ end to end
     e2e = None

@@ -72,6 +72,9 @@ typedef enum {
                                    and plans whose resident CTAs would be too thin          */
 } tds_variant;
 
+/* Arithmetic of an FP64 plan's sweeps (tds_plan_set_arith). */
+typedef enum { TDS_ARITH_NATIVE = 0, TDS_ARITH_SPLIT = 1 } tds_arith;
+
 typedef struct tds_plan tds_plan;
 
 /*
@@ -173,6 +176,22 @@ TDS_API tds_status tds_plan_set_variant(tds_plan *plan, tds_variant variant);
  * tds_plan_run_chunks.  Not part of the method (Sec. 4.1 fixes the 32-line group; its split
  * over CTAs is a GPU layout decision). */
 TDS_API tds_status tds_plan_set_width(tds_plan *plan, int lines);
+
+/* How an FP64 plan's resident sweeps do their arithmetic (a GB300 choice; the paper's sweeps
+ * are plain FP64).  TDS_ARITH_NATIVE (the default): FP64 throughout.  TDS_ARITH_SPLIT: the
+ * field stays FP64 in memory and the reduced chunk-end system stays FP64, but the stencil's
+ * differences are taken in FP64 and split into pairs of floats (hi + lo, about 48 significant
+ * bits), and the forward elimination, the accumulation of the chunk ends and the
+ * back-substitution run in float-pair arithmetic on the FP32 pipes, which on GB300 issue 64
+ * times the FP64 rate.  Results agree with FP64 to about 1e-14 of max|result| on the tested
+ * fields.  Values (inputs and results, and the differences of neighbouring inputs) must lie in
+ * float's exponent range with room for the low word, |x| in [2^-70, 2^126]: smaller
+ * differences lose low-word bits, larger ones overflow.  Applies to tds_deriv, the host entry
+ * points and tds_deriv_multi's fused pass when they run the RESIDENT variant on a
+ * forward-form operator with antisymmetric or symmetric interior taps (first and second
+ * derivatives, the adjoint on periodic lines, the filter); every other call and operator runs
+ * native FP64.  TDS_ERR_ARG for an FP32 plan, a band plan or an unknown value. */
+TDS_API tds_status tds_plan_set_arith(tds_plan *plan, tds_arith arith);
 
 /* Describe a plan: line length n, lines N, chunks P, the variant it will run, and the
  * dynamic shared memory per CTA of its resident kernel (0 if streaming).  Any output
@@ -335,6 +354,15 @@ TDS_API tds_status tds_reorder(const void *in, void *out, int nx, int ny, int nz
  */
 TDS_API tds_status tds_reorder_add(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
                                    tds_layout to, tds_dtype dtype, int sz, void *stream);
+
+/*
+ * tds_fanout_copy -- copy `bytes` of `in` to each of `count` outputs (1 <= count <= 4), reading
+ * the input once: a copy with the memory traffic of tds_deriv_multi's fused pass (one read of
+ * the field, one write per result), the ceiling that pass is measured against.  Not part of the
+ * method (a measurement aid).  Device pointers, 16-byte aligned, bytes a multiple of 16, no
+ * two buffers overlapping (TDS_ERR_ALIAS); TDS_ERR_ARG otherwise.  Asynchronous on `stream`.
+ */
+TDS_API tds_status tds_fanout_copy(const void *in, void *const *outs, int count, size_t bytes, void *stream);
 
 /* Free a plan and its device arrays (NULL is a no-op).  Not stream-ordered: the caller makes
  * sure no work that uses the plan is still running. */

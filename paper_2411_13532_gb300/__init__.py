@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import TdsError  # noqa: F401
 
-__all__ = ["Plan", "deriv", "deriv_adjoint", "deriv_multi", "reorder", "reorder_add", "transport_term",
+__all__ = ["Plan", "deriv", "deriv_adjoint", "deriv_multi", "reorder", "reorder_add", "fanout_copy", "transport_term",
            "TransportRHS", "CompactDeriv", "compact_deriv", "device_status", "grid_spacing", "TdsError"]
 
 _TORCH_DTYPES = {torch.float64: "f64", torch.float32: "f32"}
@@ -49,11 +49,14 @@ class Plan:
     are ignored and only ``solve`` is available).  ``order="filter"`` (with ``alpha_f``) makes the
     fourth-order compact filter and ``order="interp"`` the sixth-order interpolation to the
     mid-points of periodic lines (``tds_plan_create_filter`` / ``tds_plan_create_interp``;
-    ``deriv`` applies them, ``adjoint`` their transposes).
+    ``deriv`` applies them, ``adjoint`` their transposes).  ``arith="split"`` (FP64 plans) runs
+    the resident sweeps of forward-form operators in float-pair arithmetic
+    (``tds_plan_set_arith``).
     """
 
     def __init__(self, shape, direction, order, bc, P=1, h=None, dtype=torch.float64,
-                 mode="exact", variant="auto", width=None, device=None, band=None, alpha_f=None):
+                 mode="exact", variant="auto", width=None, device=None, band=None, alpha_f=None,
+                 arith="native"):
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
         kind = {"filter": 3, "interp": 4}.get(order, order)
@@ -100,6 +103,9 @@ class Plan:
             _lib.check(L.tds_plan_set_width(h_, int(width)), "tds_plan_set_width")
         if variant != "auto":
             _lib.check(L.tds_plan_set_variant(h_, _lib.VARIANTS[variant]), "tds_plan_set_variant")
+        if arith != "native":
+            _lib.check(L.tds_plan_set_arith(h_, _lib.ARITHS[arith]), "tds_plan_set_arith")
+        self.arith = arith
         nbytes = ctypes.c_size_t()
         _lib.check(L.tds_workspace_bytes(h_, ctypes.byref(nbytes)), "tds_workspace_bytes")
         self.ws_bytes = nbytes.value
@@ -313,6 +319,23 @@ def reorder_add(x, shape, src, dst, out, stream=None):
             _lib.LAYOUTS[src], _lib.LAYOUTS[dst], _lib.DTYPES[_TORCH_DTYPES[x.dtype]], 32,
             _stream_ptr(stream, x.device)), "tds_reorder_add")
     return out
+
+
+def fanout_copy(x, outs, stream=None):
+    """Copy ``x`` into each tensor of ``outs`` (1 to 4) reading it once (``tds_fanout_copy``):
+    the traffic of the fused multi-operator pass, as a measured ceiling for it."""
+    if not 1 <= len(outs) <= 4:
+        raise ValueError("fanout_copy takes 1 to 4 outputs")
+    for o in outs:
+        if o.dtype != x.dtype or o.numel() != x.numel() or not o.is_contiguous():
+            raise ValueError("outputs must match the input")
+    n = len(outs)
+    op_ = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    with torch.cuda.device(x.device):
+        _lib.check(_lib.lib().tds_fanout_copy(ctypes.c_void_p(x.data_ptr()), op_, n,
+                                              x.numel() * x.element_size(), _stream_ptr(stream, x.device)),
+                   "tds_fanout_copy")
+    return outs
 
 
 def transport_term(d1, d2, ui, uj, nu, out=None, stream=None):

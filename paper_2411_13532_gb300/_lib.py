@@ -15,6 +15,7 @@ BCS = {"periodic": 0, "closed": 1}
 DTYPES = {"f64": 0, "f32": 1}
 MODES = {"exact": 0, "paper_drop": 1}
 VARIANTS = {"auto": 0, "resident": 1, "streaming": 2, "pipelined": 3, "segmented": 4}
+ARITHS = {"native": 0, "split": 1}
 
 # (name, restype, argtypes) of every entry point declared in include/tds.h
 _vp, _i, _sz, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_double
@@ -26,6 +27,7 @@ SIGNATURES = [
     ("tds_plan_create_band", _i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i]),
     ("tds_plan_set_variant", _i, [_vp, _i]),
     ("tds_plan_set_width", _i, [_vp, _i]),
+    ("tds_plan_set_arith", _i, [_vp, _i]),
     ("tds_plan_info", _i, [_vp, _ip, _ip, _ip, _ip, _ip]),
     ("tds_plan_width", _i, [_vp, _ip]),
     ("tds_plan_run_chunks", _i, [_vp, _ip]),
@@ -40,6 +42,7 @@ SIGNATURES = [
     ("tds_deriv_adjoint_host", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     ("tds_reorder", _i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
     ("tds_reorder_add", _i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
+    ("tds_fanout_copy", _i, [_vp, ctypes.POINTER(_vp), _i, _sz, _vp]),
     ("tds_plan_destroy", None, [_vp]),
     ("tds_status_string", ctypes.c_char_p, [_i]),
     ("tds_device_status", _i, []),

@@ -454,6 +454,13 @@ tds_status tds_plan_set_width(tds_plan *p, int lines) {
     return TDS_OK;
 }
 
+tds_status tds_plan_set_arith(tds_plan *p, tds_arith arith) {
+    if (!p || p->dtype != TDS_F64 || p->band || (arith != TDS_ARITH_NATIVE && arith != TDS_ARITH_SPLIT))
+        return TDS_ERR_ARG;
+    p->split = (arith == TDS_ARITH_SPLIT) ? 1 : 0;
+    return TDS_OK;
+}
+
 tds_status tds_plan_info(const tds_plan *q, int *n, int *nlines, int *P, int *variant, int *smem) {
     if (!q) return TDS_ERR_ARG;
     if (n) *n = q->n;
@@ -602,6 +609,24 @@ tds_status tds_reorder_add(const void *in, void *out, int nx, int ny, int nz, td
     if (overlaps(in, bytes, out, bytes)) return TDS_ERR_ALIAS;
     return launch_reorder_add(in, out, nx, ny, nz, from, to, elem_size(dtype),
                               static_cast<cudaStream_t>(stream));
+}
+
+tds_status tds_fanout_copy(const void *in, void *const *outs, int count, size_t bytes, void *stream) {
+    if (!in || !outs || count < 1 || count > kMaxMulti || bytes % 16 || !aligned(in, 16)) return TDS_ERR_ARG;
+    for (int o = 0; o < count; ++o) {
+        if (!outs[o] || !aligned(outs[o], 16)) return TDS_ERR_ARG;
+        if (overlaps(in, bytes, outs[o], bytes)) return TDS_ERR_ALIAS;
+        for (int q = 0; q < o; ++q)
+            if (overlaps(outs[q], bytes, outs[o], bytes)) return TDS_ERR_ALIAS;
+    }
+    if (bytes == 0) return TDS_OK;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return TDS_ERR_CUDA;
+    }
+    return launch_fanout(in, outs, count, bytes, nsm, static_cast<cudaStream_t>(stream));
 }
 
 void tds_plan_destroy(tds_plan *p) {

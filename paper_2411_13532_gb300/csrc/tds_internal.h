@@ -48,8 +48,9 @@ struct DevOp {
                     // +2 pairs about +1/2 (nodes -> mid-points), +3 pairs about -1/2 (mid-points
                     // -> nodes), +4 symmetric with vanishing sum (second derivative); FP32
                     // sweeps apply symmetric taps to second differences (see tapsum)
-    int e64;        // FP32 sweeps of closed lines: the closure rows' steps in FP64 (the solve
-                    // magnifies an end row's rounding by more than 16)
+    int e64;        // FP32 and split-precision FP64 sweeps of closed lines: the closure rows' steps
+                    // in FP64 (the solve magnifies an end row's rounding by more than 16); native
+                    // FP64 sweeps ignore it
     int ncls;       // chunk classes (first / interior / last differ on closed lines)
     int cls_first, cls_mid, cls_last;
     int cls_each;   // 1: every chunk is its own class (ncls = P; a band whose chunks differ), and
@@ -82,6 +83,16 @@ struct DevOp {
     int kfl64[3], kfh64[3], kbl64[3], kbh64[3], kfl32[3], kfh32[3], kbl32[3], kbh32[3];
     double kf64[3][4], kb64[3];
     float kf32[3][4], kb32[3];
+    // The same records as float pairs (hi, lo) for the split-precision FP64 sweeps, [ncls][m]
+    // each: fwdd {f, r, pi, 0} (8 floats), bwdd {s^a, s^c} (4), ifwd {c0, c1, c2, g} (8) with the
+    // interior taps in the form those sweeps apply them (antisymmetric: c0 = 0, c1 = f t1,
+    // c2 = f t2 on v[j+1] - v[j-1] and v[j+2] - v[j-2]; symmetric: c0 = f tapsum on v[j],
+    // c1 = f (t1 + 2 t2) on e_j = v[j+1] - 2 v[j] + v[j-1], c2 = f t2 on e_{j+1} + e_{j-1});
+    // kfd / kbd: the constant-run records (rows [kfl64, kfh64), [kbl64, kbh64)) as pairs
+    const float *fwdd;
+    const float *bwdd;
+    const float *ifwd;
+    float kfd[3][8], kbd[3][2];
     const double *n1;     // [ncls] row-0 normaliser 1/(1 - s^c_1 s^a_2) (Algorithm 4, last lines)
     const double *red;    // [kNumRedArrays][2P]
     int red_cyclic;
@@ -122,6 +133,8 @@ struct tds_plan {
     int pipe_nbuf;         // > 0: run the persistent multi-buffered resident kernel
     int pipe_grid;         // its grid (resident CTAs the device holds at once)
     int lanes;             // lines per thread in the resident kernels (FP32: 1, 2, 4; FP64: 1, 2)
+    int split;             // FP64 plans: 1 = the resident sweeps of forward-form operators carry
+                           // their recurrences as float pairs (tds_plan_set_arith)
     tds::DevOp op[3];      // [0] = A^{-1} B, [1] = B^T A^{-T}, [2] = A^{-1} (the solve alone)
     tds::DevOp seg;        // A^{-1} B on the segment partition of the SEGMENTED variant (P = 0: none)
     tds::DevOp seg_adj;    // periodic lines: the adjoint (forward form) on that partition (P = 0: none)
@@ -183,6 +196,8 @@ tds_status launch_reorder(const void *in, void *out, int nx, int ny, int nz, tds
 // out += the reorder of in (the accumulation of a direction's result into another layout).
 tds_status launch_reorder_add(const void *in, void *out, int nx, int ny, int nz, tds_layout from,
                               tds_layout to, size_t elem, cudaStream_t st);
+// out[o] = in for o < count (<= kMaxMulti), bytes a multiple of 16 (tds_fanout_copy).
+tds_status launch_fanout(const void *in, void *const *outs, int count, size_t bytes, int nsm, cudaStream_t st);
 tds_status read_device_status();
 tds_status launch_selftest_wait(double seconds, cudaStream_t st);
 

@@ -195,7 +195,9 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
                                  std::vector<double> &n1s, std::vector<double> &red,
                                  std::vector<double> &sub, std::vector<double> &sup,
                                  std::vector<double> &fwd, std::vector<double> &bwd,
-                                 std::vector<double> &ifw, std::vector<double> &ifw32) {
+                                 std::vector<double> &ifw, std::vector<double> &ifw32,
+                                 std::vector<float> &fwdd, std::vector<float> &bwdd,
+                                 std::vector<float> &ifwd) {
     const int n = p->n;
     const bool periodic = (p->bc == TDS_BC_PERIODIC);
     std::memset(&op, 0, sizeof(op));
@@ -364,6 +366,47 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
         }
         op.kb64[cl] = rb;
         op.kb32[cl] = (float)rb;
+    }
+
+    // float-pair records of the split-precision FP64 sweeps (value = hi + lo, hi the float
+    // nearest to the FP64 record, lo the float nearest to the rest): fwd {f, r, pi}, bwd
+    // {s^a, s^c}, and the interior records in the form those sweeps evaluate the stencil --
+    // antisymmetric taps {0, f t1, f t2, f r} on v[j+1] - v[j-1] and v[j+2] - v[j-2};
+    // symmetric taps {f tapsum, f (t1 + 2 t2), f t2, f r} on v[j], the second difference
+    // e_j = v[j+1] - 2 v[j] + v[j-1] and e_{j+1} + e_{j-1} (t1 e_j + t2 (v[j+2] - 2 v[j] + v[j-2])
+    // with v[j+2] - 2 v[j] + v[j-2] = e_{j+1} + 2 e_j + e_{j-1})
+    auto pair = [](double x, float *d) {
+        d[0] = (float)x;
+        d[1] = (float)(x - (double)d[0]);
+    };
+    fwdd.assign((size_t)nc * m * 8, 0.0f);
+    bwdd.assign((size_t)nc * m * 4, 0.0f);
+    ifwd.assign((size_t)nc * m * 8, 0.0f);
+    for (int cl = 0; cl < nc; ++cl)
+        for (int j = 0; j < m; ++j) {
+            const size_t i = (size_t)cl * m + j;
+            pair(fwd[i * 4], &fwdd[i * 8]);
+            pair(fwd[i * 4 + 1], &fwdd[i * 8 + 2]);
+            pair(fwd[i * 4 + 2], &fwdd[i * 8 + 4]);
+            pair(bwd[i * 2], &bwdd[i * 4]);
+            pair(bwd[i * 2 + 1], &bwdd[i * 4 + 2]);
+            const double f = fwd[i * 4];
+            double c[4] = {ifw[i * 4], ifw[i * 4 + 1], ifw[i * 4 + 2], ifw[i * 4 + 3]};
+            if (fwd_form && sym) {
+                c[0] = f * op.tapsum;
+                c[1] = f * (op.tap[4] + 2.0 * op.tap[5]);
+                c[2] = f * op.tap[5];
+            } else if (fwd_form && op.symmetric < 0) {
+                c[0] = 0.0;
+            }
+            for (int q = 0; q < 4; ++q) pair(c[q], &ifwd[i * 8 + 2 * q]);
+        }
+    for (int cl = 0; cl < (op.cls_each ? 0 : nc); ++cl) {
+        // the constant runs of the FP64 records carry constant pair records too
+        const size_t i = (size_t)cl * m + (m - 3);
+        for (int q = 0; q < 8; ++q) op.kfd[cl][q] = ifwd[i * 8 + q];
+        op.kbd[cl][0] = bwdd[i * 4 + 2];
+        op.kbd[cl][1] = bwdd[i * 4 + 3];
     }
 
     // reduced chunk-end system, unknowns F_0, L_0, F_1, L_1, ... (2P)
@@ -559,6 +602,7 @@ tds_status build_plan(tds_plan *p) {
     }
     const int nops = sg ? (periodic ? 5 : 4) : 3;
     std::vector<double> rows[5], n1s[5], red[5], sub[5], sup[5], fwd[5], bwd[5], ifw[5], ifw32[5];
+    std::vector<float> fwdd[5], bwdd[5], ifwd[5];
     DevOp *ops[5] = {&p->op[0], &p->op[1], &p->op[2], &p->seg, &p->seg_adj};
     std::memset(&p->seg, 0, sizeof(p->seg));
     std::memset(&p->seg_adj, 0, sizeof(p->seg_adj));
@@ -566,12 +610,15 @@ tds_status build_plan(tds_plan *p) {
         const int P = (w < 3) ? p->P : p->n / sg, m = (w < 3) ? p->m : sg;
         const int kind = (w == 1 || w == 4) ? 1 : (w == 2 ? 2 : 0);
         tds_status s = build_operator(p, P, m, kind == 1 ? LT : L, kind, *ops[w], rows[w], n1s[w],
-                                      red[w], sub[w], sup[w], fwd[w], bwd[w], ifw[w], ifw32[w]);
+                                      red[w], sub[w], sup[w], fwd[w], bwd[w], ifw[w], ifw32[w], fwdd[w],
+                                      bwdd[w], ifwd[w]);
         if (s != TDS_OK) return s;
     }
-    // FP32 sweeps of closed lines take the closure rows in FP64 where the solve magnifies an
-    // end row's rounding by more than 16 (2^-24 x 16 ~ 1e-6)
-    const int e64 = (!periodic && p->dtype == TDS_F32 && end_gain(L, p->n) > 16.0) ? 1 : 0;
+    // FP32 and split-precision FP64 sweeps of closed lines take the closure rows in FP64 where the
+    // solve magnifies an end row's rounding by more than 16 (FP32: 2^-24 x 16 ~ 1e-6; float
+    // pairs: 2^-48 x 16 ~ 6e-14, against about 3e-13 at the gain of 93 of the second derivative's
+    // closure); native FP64 sweeps ignore the flag
+    const int e64 = (!periodic && end_gain(L, p->n) > 16.0) ? 1 : 0;
     for (int w = 0; w < nops; ++w) ops[w]->e64 = e64;
     if (nops >= 4 && (!p->seg.red_decoupled || (nops == 5 && !p->seg_adj.red_decoupled))) {
         std::memset(&p->seg, 0, sizeof(p->seg));
@@ -579,9 +626,10 @@ tds_status build_plan(tds_plan *p) {
     }
 
     // one device allocation per plan, 256-byte aligned parts per operator:
-    // [rows64 | rows32 | n1 | red | fwd64 | fwd32 | bwd64 | bwd32 | ifw64 | ifw32]
+    // [rows64 | rows32 | n1 | red | fwd64 | fwd32 | bwd64 | bwd32 | ifw64 | ifw32 | fwd, bwd and
+    //  ifw float pairs]
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t off[5][10], total = 0;
+    size_t off[5][13], total = 0;
     for (int w = 0; w < nops; ++w) {
         off[w][0] = total; total = align(total + rows[w].size() * sizeof(double));
         off[w][1] = total; total = align(total + rows[w].size() * sizeof(float));
@@ -593,6 +641,9 @@ tds_status build_plan(tds_plan *p) {
         off[w][7] = total; total = align(total + bwd[w].size() * sizeof(float));
         off[w][8] = total; total = align(total + ifw[w].size() * sizeof(double));
         off[w][9] = total; total = align(total + ifw[w].size() * sizeof(float));
+        off[w][10] = total; total = align(total + fwdd[w].size() * sizeof(float));
+        off[w][11] = total; total = align(total + bwdd[w].size() * sizeof(float));
+        off[w][12] = total; total = align(total + ifwd[w].size() * sizeof(float));
     }
     std::vector<unsigned char> host(total, 0);
     auto put64 = [&](size_t o, const std::vector<double> &v) {
@@ -608,6 +659,9 @@ tds_status build_plan(tds_plan *p) {
         put64(off[w][4], fwd[w]); put32(off[w][5], fwd[w]);
         put64(off[w][6], bwd[w]); put32(off[w][7], bwd[w]);
         put64(off[w][8], ifw[w]); put32(off[w][9], ifw32[w]);
+        std::memcpy(&host[off[w][10]], fwdd[w].data(), fwdd[w].size() * sizeof(float));
+        std::memcpy(&host[off[w][11]], bwdd[w].data(), bwdd[w].size() * sizeof(float));
+        std::memcpy(&host[off[w][12]], ifwd[w].data(), ifwd[w].size() * sizeof(float));
     }
     void *d = nullptr;
     const cudaError_t e = cudaMalloc(&d, total);
@@ -638,6 +692,9 @@ tds_status build_plan(tds_plan *p) {
         o.bwd32 = reinterpret_cast<const float *>(base + off[w][7]);
         o.ifw64 = reinterpret_cast<const double *>(base + off[w][8]);
         o.ifw32 = reinterpret_cast<const float *>(base + off[w][9]);
+        o.fwdd = reinterpret_cast<const float *>(base + off[w][10]);
+        o.bwdd = reinterpret_cast<const float *>(base + off[w][11]);
+        o.ifwd = reinterpret_cast<const float *>(base + off[w][12]);
     }
     for (int w = 0; w < 2; ++w) {
         p->red_sub_host[w] = hm + (size_t)(2 * w) * R;

@@ -166,4 +166,48 @@ tds_status launch_reorder_add(const void *in, void *out, int nx, int ny, int nz,
                      : launch_t<float, true>(in, out, nx, ny, nz, from, to, st);
 }
 
+namespace {
+// Fan-out copy: every 16-byte vector of `in` read once and written to each of `count` outputs
+// (the traffic of the fused multi-operator pass: one read, one write per result).  Each thread
+// loads kFanVec vectors before it stores them, so several loads are in flight per thread.
+constexpr int kFanVec = 4;
+
+struct FanArgs {
+    void *out[kMaxMulti];
+    int count;
+};
+
+__global__ void __launch_bounds__(256) k_fanout(const float4 *__restrict__ in, const __grid_constant__ FanArgs fa,
+                                               size_t nvec) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x * kFanVec;
+    for (size_t base = ((size_t)blockIdx.x * blockDim.x * kFanVec) + threadIdx.x; base < nvec; base += stride) {
+        float4 v[kFanVec];
+#pragma unroll
+        for (int u = 0; u < kFanVec; ++u) {
+            const size_t i = base + (size_t)u * blockDim.x;
+            if (i < nvec) v[u] = __ldcs(in + i);
+        }
+        for (int o = 0; o < fa.count; ++o) {
+            float4 *dst = static_cast<float4 *>(fa.out[o]);
+#pragma unroll
+            for (int u = 0; u < kFanVec; ++u) {
+                const size_t i = base + (size_t)u * blockDim.x;
+                if (i < nvec) dst[i] = v[u];
+            }
+        }
+    }
+}
+} // namespace
+
+tds_status launch_fanout(const void *in, void *const *outs, int count, size_t bytes, int nsm, cudaStream_t st) {
+    FanArgs fa;
+    for (int o = 0; o < kMaxMulti; ++o) fa.out[o] = (o < count) ? outs[o] : nullptr;
+    fa.count = count;
+    const size_t nvec = bytes / 16;
+    const size_t need = (nvec + 256 * kFanVec - 1) / (256 * kFanVec);
+    const unsigned grid = (unsigned)(need < (size_t)nsm * 8 ? (need ? need : 1) : (size_t)nsm * 8);
+    k_fanout<<<grid, 256, 0, st>>>(static_cast<const float4 *>(in), fa, nvec);
+    return cudaGetLastError() == cudaSuccess ? TDS_OK : TDS_ERR_CUDA;
+}
+
 } // namespace tds

@@ -32,6 +32,7 @@
 #include <cudaTypedefs.h>
 
 #include "tds_device.cuh"
+#include "tds_df.cuh"
 
 namespace tds {
 
@@ -59,6 +60,7 @@ struct TrNative {
     using A = T;
     static constexpr int W = W_;   // lines per CTA: the row stride of the tile in shared memory
     static constexpr bool kE64 = E64_;   // FP32 closed lines: closure rows in FP64 (Ends64)
+    static constexpr bool kDF = false;   // float-pair recurrences (TrSplit)
     static __device__ __forceinline__ A from_d(double x) { return A(x); }
     static __device__ __forceinline__ double to_d(A x) { return double(x); }
     template <int V>
@@ -140,6 +142,90 @@ struct TrNative {
         cls = scal_cls(op, cls);
         if constexpr (sizeof(T) == 4) return op.kb32[cls];
         else return op.kb64[cls];
+    }
+};
+
+// Split-precision FP64 sweeps: FP64 storage in HBM and in the tile, recurrences as float pairs
+// on the FP32 pipes (tds_df.cuh).  Input rows travel as the FP64 value's bits (ld_in: the stencil
+// takes its differences in FP64 before splitting them, so that on smooth data nothing cancels in
+// the pairs); intermediate values sit in their row's slot as a pair; results leave as FP64.
+// Forward-form operators only (the stencil right-hand side), one line per thread.
+template <int W_ = kSZ>
+struct TrSplit {
+    using S = double;
+    using A = DF;
+    static constexpr int W = W_;
+    static constexpr bool kE64 = true;   // closed lines with a high end gain: closure rows in FP64 (Ends64)
+    static constexpr bool kDF = true;
+    static __device__ __forceinline__ A from_d(double x) { return DF(x); }
+    static __device__ __forceinline__ double to_d(A x) { return static_cast<double>(x); }
+    template <int V>
+    static __device__ __forceinline__ Pack<A, V> ld_in(const DevOp &, const S *p, int &) {
+        Pack<A, V> r;
+#pragma unroll
+        for (int i = 0; i < V; ++i) r.v[i] = df_raw(p[i]);
+        return r;
+    }
+    template <int V>
+    static __device__ __forceinline__ Pack<A, V> ld_mid(const S *p) {
+        Pack<A, V> r;
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const float2 x = *reinterpret_cast<const float2 *>(p + i);
+            r.v[i] = df_make(x.x, x.y);
+        }
+        return r;
+    }
+    template <int V>
+    static __device__ __forceinline__ void st_mid(S *p, const Pack<A, V> &v) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) *reinterpret_cast<float2 *>(p + i) = make_float2(v.v[i].h, v.v[i].l);
+    }
+    template <int V>
+    static __device__ __forceinline__ void st_out(const DevOp &, S *p, const Pack<A, V> &v) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) p[i] = df_join(v.v[i]);
+    }
+    static __device__ __forceinline__ A tap(const DevOp &op, int i) { return DF(op.tap[i]); }
+    static __device__ __forceinline__ A edge(const DevOp &op, int e, int o) { return DF(op.edge[e][o]); }
+    static __device__ __forceinline__ void fwd(const DevOp &op, int cls, int j, A &f, A &r, A &pi) {
+        const float4 *q = reinterpret_cast<const float4 *>(op.fwdd) + 2 * ((size_t)cls * op.m + j);
+        const float4 a = __ldg(q);
+        const float2 b = __ldg(reinterpret_cast<const float2 *>(q + 1));
+        f = df_make(a.x, a.y); r = df_make(a.z, a.w); pi = df_make(b.x, b.y);
+    }
+    static __device__ __forceinline__ void bwd(const DevOp &op, int cls, int j, A &sa, A &sc) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(op.bwdd) + (size_t)cls * op.m + j);
+        sa = df_make(a.x, a.y); sc = df_make(a.z, a.w);
+    }
+    static __device__ __forceinline__ void ifw(const DevOp &op, int cls, int j, A &c0, A &c1, A &c2, A &g) {
+        const float4 *q = reinterpret_cast<const float4 *>(op.ifwd) + 2 * ((size_t)cls * op.m + j);
+        const float4 a = __ldg(q), b = __ldg(q + 1);
+        c0 = df_make(a.x, a.y); c1 = df_make(a.z, a.w); c2 = df_make(b.x, b.y); g = df_make(b.z, b.w);
+    }
+    static __device__ __forceinline__ A pi(const DevOp &op, int cls, int j) {
+        const float2 b = __ldg(reinterpret_cast<const float2 *>(op.fwdd) + 4 * ((size_t)cls * op.m + j) + 2);
+        return df_make(b.x, b.y);
+    }
+    static __device__ __forceinline__ int jpi(const DevOp &op, int cls) { return op.jpi64[scal_cls(op, cls)]; }
+    static __device__ __forceinline__ int jsa(const DevOp &op, int cls) { return op.jsa64[scal_cls(op, cls)]; }
+    static __device__ __forceinline__ void kf_run(const DevOp &op, int cls, int &lo, int &hi) {
+        cls = scal_cls(op, cls);
+        lo = op.kfl64[cls];
+        hi = op.kfh64[cls];
+    }
+    static __device__ __forceinline__ void kf(const DevOp &op, int cls, A &c0, A &c1, A &c2, A &g) {
+        const float *k = op.kfd[scal_cls(op, cls)];
+        c0 = df_make(k[0], k[1]); c1 = df_make(k[2], k[3]); c2 = df_make(k[4], k[5]); g = df_make(k[6], k[7]);
+    }
+    static __device__ __forceinline__ void kb_run(const DevOp &op, int cls, int &lo, int &hi) {
+        cls = scal_cls(op, cls);
+        lo = op.kbl64[cls];
+        hi = op.kbh64[cls];
+    }
+    static __device__ __forceinline__ A kb(const DevOp &op, int cls) {
+        const float *k = op.kbd[scal_cls(op, cls)];
+        return df_make(k[0], k[1]);
     }
 };
 
@@ -383,8 +469,9 @@ __device__ __forceinline__ void fwd_irow(const DevOp &op, int cls, int j, typena
 template <typename Tr, int V, int FORM, bool ACC, bool CONST>
 __device__ __forceinline__ void fwd_irows(const DevOp &op, int cls, typename Tr::S *row, int jb, int je,
                                           Pack<typename Tr::A, V> (&w)[5], Pack<typename Tr::A, V> &dprev,
-                                          Pack<typename Tr::A, V> &S, int &unsafe, typename Tr::A k0 = 0,
-                                          typename Tr::A k1 = 0, typename Tr::A k2 = 0, typename Tr::A kg = 0) {
+                                          Pack<typename Tr::A, V> &S, int &unsafe,
+                                          typename Tr::A k0 = typename Tr::A(0), typename Tr::A k1 = typename Tr::A(0),
+                                          typename Tr::A k2 = typename Tr::A(0), typename Tr::A kg = typename Tr::A(0)) {
 #pragma unroll 4
     for (int j = jb; j < je; ++j) {
         w[4] = Tr::template ld_in<V>(op, row + (size_t)(j + 2) * Tr::W, unsafe);
@@ -412,6 +499,83 @@ __device__ __forceinline__ void fwd_span(const DevOp &op, int cls, typename Tr::
     fwd_irows<Tr, V, FORM, ACC, false>(op, cls, row, b, je, w, dprev, S, unsafe);
 }
 
+// Split-precision forward rows [jb, je) of a chunk (TrSplit, one line per thread): the stencil's
+// differences of the FP64 inputs taken in FP64 and split into float pairs (on smooth data the
+// differences are exact and small, so the pairs lose nothing to cancellation), then the folded
+// taps, the recurrence d_j = (stencil) - g d_{j-1} and S += pi_j d_j in float-pair arithmetic.
+//   antisymmetric taps: c1 (v[j+1] - v[j-1]) + c2 (v[j+2] - v[j-2]), with b_j = v[j+1] - v[j-1]
+//       split once per row and v[j+2] - v[j-2] = b_{j+1} + b_{j-1};
+//   symmetric taps: c0 v[j] + c1 e_j + c2 (e_{j+1} + e_{j-1}), e_j = (v[j+1] - v[j]) - (v[j] -
+//       v[j-1]) split once per row (c0 = f tapsum: zero for a second derivative).
+// w[0..3] carry v[jb-2 .. jb+1] as FP64 bits; v[j+2] comes from the tile ahead of the sweep, then
+// from the halo `ha` (the next chunk's first two rows).
+template <typename Tr, int FORM>
+__device__ __forceinline__ void sweep_interior_df(const DevOp &op, int cls, double *row, int jb, int je,
+                                                  const Pack<DF, 1> (&w)[5], const Pack<DF, 1> (&ha)[2],
+                                                  Pack<DF, 1> &dprev, Pack<DF, 1> &S) {
+    static_assert(FORM == kAnti || FORM == kSym, "split sweeps evaluate the antisymmetric and symmetric forms");
+    const int m = op.m;
+    const int jm = (je < m - 2) ? je : m - 2;
+    const double v0 = df_unraw(w[0].v[0]), v1 = df_unraw(w[1].v[0]);
+    double v2 = df_unraw(w[2].v[0]), v3 = df_unraw(w[3].v[0]);
+    double a2 = 0.0;   // symmetric: v[j+1] - v[j]
+    DF p, c;           // antisymmetric: b_{j-1}, b_j; symmetric: e_{j-1}, e_j
+    if (FORM == kAnti) {
+        p = df_split(v2 - v0);
+        c = df_split(v3 - v1);
+    } else {
+        const double a0 = v1 - v0, a1 = v2 - v1;
+        a2 = v3 - v2;
+        p = df_split(a1 - a0);
+        c = df_split(a2 - a1);
+    }
+    const bool c0 = (FORM == kSym) && op.tapsum != 0.0;
+    DF d = dprev.v[0], Sa = S.v[0];
+    int lo, hi;
+    Tr::kf_run(op, cls, lo, hi);
+    DF k0, k1, k2, kg;
+    Tr::kf(op, cls, k0, k1, k2, kg);
+    const int jp = Tr::jpi(op, cls);
+    auto step = [&](int j, double v4, bool acc, bool cst) {
+        DF q0 = k0, q1 = k1, q2 = k2, qg = kg;
+        if (!cst) Tr::ifw(op, cls, j, q0, q1, q2, qg);
+        DF nx;
+        if (FORM == kAnti) {
+            nx = df_split(v4 - v2);
+        } else {
+            const double a3 = v4 - v3;
+            nx = df_split(a3 - a2);
+            a2 = a3;
+        }
+        DF dn = dot3(q1, c, q2, nx + p, -qg, d);
+        if (c0) dn = mad(q0, df_split(v2), dn);
+        d = dn;
+        if (acc) Sa = mad(Tr::pi(op, cls, j), d, Sa);
+        *reinterpret_cast<float2 *>(row + (size_t)j * Tr::W) = make_float2(d.h, d.l);
+        p = c;
+        c = nx;
+        v2 = v3;
+        v3 = v4;
+    };
+    auto run = [&](int a, int b, bool acc, bool cst) {
+#pragma unroll 4
+        for (int j = a; j < b; ++j) step(j, row[(size_t)(j + 2) * Tr::W], acc, cst);
+    };
+    auto span = [&](int a, int b, bool acc) {
+        const int x = (lo < a) ? a : (lo > b ? b : lo);
+        const int y = (hi < x) ? x : (hi > b ? b : hi);
+        run(a, x, acc, false);
+        run(x, y, acc, true);
+        run(y, b, acc, false);
+    };
+    const int j1 = (jp < jb) ? jb : (jp > jm ? jm : jp);
+    span(jb, j1, true);
+    span(j1, jm, false);
+    for (int j = (jb > m - 2 ? jb : m - 2); j < je; ++j) step(j, df_unraw(ha[j + 2 - m].v[0]), j < jp, false);
+    dprev.v[0] = d;
+    S.v[0] = Sa;
+}
+
 // Interior rows [jb, je) of a stencil sweep over this chunk, in place: w[0..3] holds
 // v[j-2..j+1] on entry; v[j+2] is read from the tile while inside the chunk (rows ahead of the
 // window are not yet overwritten), then from the halo `ha`.  FWD: forward elimination rows
@@ -423,6 +587,10 @@ __device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typenam
                                                Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S,
                                                int &unsafe) {
     using A = typename Tr::A;
+    if constexpr (Tr::kDF && FWD && (FORM == kAnti || FORM == kSym)) {
+        sweep_interior_df<Tr, FORM>(op, cls, row, jb, je, w, ha, dprev, S);
+        return;
+    }
     const int m = op.m;
     const A t0 = (FORM == kSymD) ? Tr::from_d(op.tapsum) : Tr::tap(op, 3), t1 = Tr::tap(op, 4), t2 = Tr::tap(op, 5);
     const int jm = (je < m - 2) ? je : m - 2;
@@ -476,7 +644,50 @@ __device__ __forceinline__ void sweep_edge(const DevOp &op, int cls, typename Tr
                                            Ends64<V> &ex) {
     using A = typename Tr::A;
     bool done = false;
-    if constexpr (FWD && Tr::kE64) {
+    if constexpr (FWD && Tr::kDF) {
+        // split-precision sweeps: the closure rows' right-hand sides in FP64 from the FP64
+        // inputs (the taps as written); where the closure magnifies end errors (DevOp::e64) their
+        // forward steps in FP64 too (Ends64, as for FP32 sweeps), else in float pairs
+        double xw[kTaps + 3][V];
+#pragma unroll
+        for (int o = 0; o < kTaps + 3; ++o) {
+            const int x = o + xlo;
+#pragma unroll
+            for (int q = 0; q < V; ++q) xw[o][q] = (x >= 0 && x < xhi) ? xs[(size_t)x * Tr::W + c + q] : 0.0;
+        }
+        double d[V], Sx[V], d0[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) { d[q] = head ? 0.0 : static_cast<double>(dprev.v[q]); Sx[q] = 0.0; d0[q] = 0.0; }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const double *cf = op.edge[e0 + t];
+            double sd[V];
+            A sv[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                double s0 = cf[0] * xw[t][q], s1 = cf[1] * xw[t + 1][q];
+#pragma unroll
+                for (int o = 2; o < kTaps; o += 2) {
+                    s0 = ::fma(cf[o], xw[t + o][q], s0);
+                    if (o + 1 < kTaps) s1 = ::fma(cf[o + 1], xw[t + o + 1][q], s1);
+                }
+                sd[q] = s0 + s1;
+                sv[q] = df_split(sd[q]);
+            }
+            if (op.e64) {
+                fwd_row64<Tr, V>(op, cls, j0 + t, row, sd, d, Sx);
+                if (t == 0) {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) d0[q] = d[q];
+                }
+            } else {
+                fwd_row<Tr, V>(op, cls, j0 + t, row, sv, dprev, S);
+            }
+        }
+        if (op.e64) close_rows64<Tr, V>(op, cls, j0, head, d, Sx, d0, dprev, S, ex);
+        done = true;
+    }
+    if constexpr (FWD && Tr::kE64 && !Tr::kDF) {
         if (op.e64) {
             // the ten input rows the four windows cover, converted once; two partial sums per
             // row halve the dependent chain
@@ -1742,6 +1953,14 @@ tds_status launch_resident_v(const tds_plan *p, int which, const TileMaps &tm, c
                       : launch_resident_t<Tr, V, 0>(op, tm, in, out, p->resident_smem, st);
 }
 
+// Whether an FP64 plan's operator runs the split-precision sweep (TrSplit): the plan asks for it
+// (tds_plan_set_arith) and the operator has the forward form with antisymmetric or symmetric
+// interior taps (derivatives, their adjoints on periodic lines, the filter).
+bool split_sweep(const tds_plan *p, const DevOp &op) {
+    return p->dtype == TDS_F64 && p->split && op.adjoint == 0 &&
+           (op.symmetric < 0 || op.symmetric == 1 || op.symmetric == 4);
+}
+
 // cuTensorMapEncodeTiled, looked up once through the runtime (no link against the driver API).
 using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
 EncodeTiledFn encode_tiled() {
@@ -1813,6 +2032,12 @@ tds_status launch_resident(const tds_plan *p, int which, const void *in, void *o
     if (!tile_maps(p, in, out, &tm)) return TDS_ERR_CUDA;
     const int W = p->width;
     const int lanes = (p->op[which].adjoint == 2) ? 1 : p->lanes;
+    if (split_sweep(p, p->op[which])) {
+        const DevOp &op = p->op[which];
+        return W == 16 ? launch_resident_t<TrSplit<16>, 1, 0>(op, tm, in, out, p->resident_smem, st)
+             : W == 8  ? launch_resident_t<TrSplit<8>, 1, 0>(op, tm, in, out, p->resident_smem, st)
+                       : launch_resident_t<TrSplit<>, 1, 0>(op, tm, in, out, p->resident_smem, st);
+    }
     if (p->dtype == TDS_F64) {
         if (W == 16) return launch_resident_v<TrF64w<16>, 1>(p, which, tm, in, out, st);
         if (W == 8) return launch_resident_v<TrF64w<8>, 1>(p, which, tm, in, out, st);
@@ -1898,6 +2123,12 @@ tds_status launch_resident_multi(const tds_plan *const *plans, const int *which,
     if (p->width < kSZ && !encode_rows(&mm.in, in, p->dtype, rows, p->width, p->box_rows)) return TDS_ERR_CUDA;
     const int W = p->width, smem = p->resident_smem;
     const bool ilv = multi_ilv(p->dtype);
+    bool split = true;
+    for (int i = 0; i < count; ++i) split = split && split_sweep(plans[i], ma.op[i]);
+    if (split)
+        return W == 16 ? launch_multi_t<TrSplit<16>>(ma, mm, in, smem, ilv, st)
+             : W == 8  ? launch_multi_t<TrSplit<8>>(ma, mm, in, smem, ilv, st)
+                       : launch_multi_t<TrSplit<>>(ma, mm, in, smem, ilv, st);
     if (p->dtype == TDS_F64)
         return W == 16 ? launch_multi_t<TrF64w<16>>(ma, mm, in, smem, ilv, st)
              : W == 8  ? launch_multi_t<TrF64w<8>>(ma, mm, in, smem, ilv, st)

@@ -97,6 +97,8 @@ def test_null_pointer_errors_need_no_gpu(L):
     assert L.tds_plan_create_interp(ctypes.byref(h), 64, 64, 64, 0, 32, 0, 32, 0) == _lib.ERR_SHAPE
     assert not h.value
     assert L.tds_plan_set_width(None, 32) == _lib.ERR_ARG
+    assert L.tds_plan_set_arith(None, 1) == _lib.ERR_ARG
+    assert L.tds_fanout_copy(None, None, 1, 16, None) == _lib.ERR_ARG
     w = ctypes.c_int()
     assert L.tds_plan_width(None, ctypes.byref(w)) == _lib.ERR_ARG
     assert L.tds_plan_run_chunks(None, ctypes.byref(w)) == _lib.ERR_ARG
