@@ -12,7 +12,11 @@ directional-derivative points per second (Gpoints/s) over all ranks, with the fi
 HBM; every field is 0.5-1 GiB, larger than L2, so no flush is needed between steps.
 ``value_f64`` / ``value_f32`` (and ``by_precision``) split it: the nine operators of each
 precision over the time of that precision's launches.  After the timed steps each operator is
-also timed on its own (``breakdown`` entries ``single/...``).
+also timed on its own (``breakdown`` entries ``single/...``), and the FP64 half of the step runs
+again, K steps, with split-precision plans (FP64 fields and results, the sweeps' recurrences in
+float pairs on the FP32 pipes): ``value_f64_split`` and the ``f64s/...`` breakdown entries; a
+copy with the fused pass's traffic shape (one read, three writes: ``fanout3``) gives that pass's
+own ceiling.
 
 ``e2e`` repeats the step through host buffers: the x-layout field comes from pinned host
 memory each step (``tds_deriv_host`` copies it in for the first operator) and every one of
@@ -247,9 +251,9 @@ def run_ours(args, rank, world, local_rank):
         # the adjoint has the forward form (periodic lines)
         return (p1.variant == p2.variant == "resident" and p1.width == p2.width and bc == "periodic")
 
-    def step(record):
+    def step(record, names=("f64", "f32")):
         # per direction: D1, D2 and D1^T of one input through tds_deriv_multi (one fused pass)
-        for name, _ in dtypes:
+        for name in names:
             d = data[name]
             src = d["ux"]
             for direc, nxt in (("x", "uy"), ("y", "uz"), ("z", None)):
@@ -324,6 +328,44 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
             single[(name, key, var)] = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
 
+    # the FP64 step again with split-precision plans (FP64 fields and results, the sweeps'
+    # recurrences in float pairs on the FP32 pipes): K steps after W warm-up steps, not part of
+    # `value`; reported as value_f64_split with its own per-launch breakdown
+    d64 = data["f64"]
+    data["f64s"] = dict(d64)
+    data["f64s"]["plans"] = {k: tds.Plan(shape, k[0], k[1], bc, P=P, dtype=torch.float64, arith="split")
+                             for k in d64["plans"]}
+    for _ in range(args.warmup):
+        step(False, ("f64s",))
+    torch.cuda.synchronize()
+    ts0 = torch.cuda.Event(enable_timing=True)
+    ts1 = torch.cuda.Event(enable_timing=True)
+    ts0.record(stream)
+    for _ in range(args.steps):
+        step(True, ("f64s",))
+    ts1.record(stream)
+    torch.cuda.synchronize()
+    ms_split = max_over_ranks(ts0.elapsed_time(ts1), world, dev)
+    for key in [k for k in timing if k[0] == "f64s"]:
+        per[key] = sum(a.elapsed_time(b) for a, b in timing[key]) / len(timing[key])
+    ds = data["f64s"]
+    p1s, p2s = ds["plans"][("x", 1)], ds["plans"][("x", 2)]
+    for key, fn, var in (("d1", lambda: p1s.deriv(ds["ux"], ds["o"][0]), p1s.variant),
+                         ("d2", lambda: p2s.deriv(ds["ux"], ds["o"][1]), p2s.variant),
+                         ("d1t", lambda: p1s.adjoint(ds["ux"], ds["o"][2]), p1s.variant)):
+        for _ in range(2):
+            fn()
+        evs = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        single[("f64s", key, var)] = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+
     # the fused pass's own ceiling: a copy with its traffic shape (one read, three writes)
     for name, _ in dtypes:
         d = data[name]
@@ -346,7 +388,7 @@ def run_ours(args, rank, world, local_rank):
     def algorithmic(key):
         """(directional-derivative points, algorithmic HBM bytes, FP64 operations) of one launch."""
         name, kind = key[0], key[1]
-        es = 8 if name == "f64" else 4
+        es = 8 if name in ("f64", "f64s") else 4
         if kind == "multi":   # one read of the field, three results written
             return 3 * npts, 4 * es * npts, sum(fp64_ops_per_point(o, m_chunk) for o in ("d1", "d2", "d1t")) * npts
         if kind == "fanout3":
@@ -377,8 +419,18 @@ def run_ours(args, rank, world, local_rank):
             "ms_per_step": round(ms_p, 4),
             "alg_GB_s": round(bytes_p / (ms_p * 1e-3) / 1e9, 1),
             "hbm_frac": round(bytes_p / (ms_p * 1e-3) / 1e9 / hbm, 4)}
+    # the FP64 step with split-precision plans (timed on its own after the timed region)
+    keys = [k for k in per if k[0] == "f64s"]
+    bytes_s = sum(algorithmic(k)[1] * len(timing[k]) for k in keys) / args.steps
+    ms_s = sum(per[k] * len(timing[k]) for k in keys) / args.steps
+    by_precision["f64_split"] = {
+        "gpoints_s": round(job_throughput(world, ops_per_step // 2, npts, args.steps, ms_split), 3),
+        "ms_per_step": round(ms_split / args.steps, 4),
+        "alg_GB_s": round(bytes_s / (ms_s * 1e-3) / 1e9, 1),
+        "hbm_frac": round(bytes_s / (ms_s * 1e-3) / 1e9 / hbm, 4),
+        "arith": "FP64 fields and results; sweeps in float pairs on the FP32 pipes (tds_plan_set_arith)"}
     # dominant kernel of the timed step by total time
-    totals = {k: per[k] * len(timing[k]) for k in per}
+    totals = {k: per[k] * len(timing[k]) for k in per if k[0] != "f64s"}
     dom = max(totals, key=totals.get)
     dom_ms = per[dom]
     pts, nbytes, ops = algorithmic(dom)
@@ -409,6 +461,10 @@ def run_ours(args, rank, world, local_rank):
     mul = [v for k, v in breakdown.items() if k.startswith("f32/multi/")]
     if fan and mul:
         roofline["f32_multi_of_fanout_copy"] = round(fan["ms"] / mul[0]["ms"], 4)
+    # the split-precision FP64 fused pass against HBM
+    sm = [(k, v) for k, v in breakdown.items() if k.startswith("f64s/multi/")]
+    if sm:
+        roofline["f64_split_multi_hbm_frac"] = sm[0][1]["hbm_frac"]
 
     # ------------------------------------------------------------------ end to end
     e2e = None
@@ -1039,6 +1095,7 @@ def main():
             "metric": METRIC, "value": round(res["value"], 3), "unit": UNIT, "n_gpus": world,
             "value_f64": res["by_precision"]["f64"]["gpoints_s"],
             "value_f32": res["by_precision"]["f32"]["gpoints_s"],
+            "value_f64_split": res["by_precision"]["f64_split"]["gpoints_s"],
             "by_precision": res["by_precision"],
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(res["ms"] / args.steps, 4), "higher_is_better": True,

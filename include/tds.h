@@ -185,12 +185,16 @@ TDS_API tds_status tds_plan_set_width(tds_plan *plan, int lines);
  * back-substitution run in float-pair arithmetic on the FP32 pipes, which on GB300 issue 64
  * times the FP64 rate.  Results agree with FP64 to about 1e-14 of max|result| on the tested
  * fields.  Values (inputs and results, and the differences of neighbouring inputs) must lie in
- * float's exponent range with room for the low word, |x| in [2^-70, 2^126]: smaller
+ * float's exponent range with room for the low word, |x| in [2^-74, 2^126]: smaller
  * differences lose low-word bits, larger ones overflow.  Applies to tds_deriv, the host entry
- * points and tds_deriv_multi's fused pass when they run the RESIDENT variant on a
- * forward-form operator with antisymmetric or symmetric interior taps (first and second
- * derivatives, the adjoint on periodic lines, the filter); every other call and operator runs
- * native FP64.  TDS_ERR_ARG for an FP32 plan, a band plan or an unknown value. */
+ * points, tds_deriv_multi (one launch per operator: these sweeps are bound by their own issue
+ * rate, not by HBM reads, so the fused pass gains nothing) and tds_transport when they run the
+ * RESIDENT variant on a forward-form operator with antisymmetric or symmetric interior taps
+ * (first and second derivatives, the adjoint on periodic lines, the filter); every other call
+ * and operator runs native FP64.  The plan's CTA width follows the arithmetic (split sweeps, bound by the FP32
+ * issue rate, take the widest CTA that lets two share an SM, as FP32 plans do) and the variant
+ * is chosen again (AUTO): call this before tds_plan_set_width and tds_plan_set_variant.
+ * TDS_ERR_ARG for an FP32 plan, a band plan or an unknown value. */
 TDS_API tds_status tds_plan_set_arith(tds_plan *plan, tds_arith arith);
 
 /* Describe a plan: line length n, lines N, chunks P, the variant it will run, and the
@@ -269,7 +273,8 @@ TDS_API tds_status tds_deriv_thomas(const tds_plan *plan, const void *in, void *
  * tds_deriv_multi -- several operators of one input: outs[i] = plans[i]'s derivative
  * (adjoint[i] = 0) or its adjoint (adjoint[i] = 1) of `in`, 1 <= count <= 4.  When every plan
  * runs RESIDENT with the same chunks and CTA width and every operator has the forward form
- * (derivatives, and adjoints on periodic lines), one kernel computes them all from a single
+ * (derivatives, and adjoints on periodic lines) and no plan has split-precision FP64 sweeps
+ * (tds_plan_set_arith), one kernel computes them all from a single
  * read of `in` (the field is read from HBM once and each result written once; Sec. 5 fuses the
  * transport equation's derivative operators the same way): one CTA per (group of lines,
  * operator), the operators' CTAs of a group adjacent so that they share the input through L2

@@ -99,13 +99,13 @@ class Plan:
                                                   _lib.BCS[bc], self.P, _lib.DTYPES[_TORCH_DTYPES[dtype]],
                                                   32, _lib.MODES[mode]), "tds_plan_create_band")
         self._handle = h_
+        if arith != "native":   # first: it re-picks the width and the AUTO variant
+            _lib.check(L.tds_plan_set_arith(h_, _lib.ARITHS[arith]), "tds_plan_set_arith")
+        self.arith = arith
         if width is not None:
             _lib.check(L.tds_plan_set_width(h_, int(width)), "tds_plan_set_width")
         if variant != "auto":
             _lib.check(L.tds_plan_set_variant(h_, _lib.VARIANTS[variant]), "tds_plan_set_variant")
-        if arith != "native":
-            _lib.check(L.tds_plan_set_arith(h_, _lib.ARITHS[arith]), "tds_plan_set_arith")
-        self.arith = arith
         nbytes = ctypes.c_size_t()
         _lib.check(L.tds_workspace_bytes(h_, ctypes.byref(nbytes)), "tds_workspace_bytes")
         self.ws_bytes = nbytes.value
@@ -366,18 +366,20 @@ class TransportRHS:
     into the x-layout output with ``reorder_add`` (six accumulations): 21 launches.  ``P`` is
     the chunk count per line (an int, or one per direction x, y, z); ``width`` optionally fixes
     the lines per resident CTA.  The plans must be able to hold their lines in a CTA.
-    Six temporary fields are allocated with the object.
+    ``arith="split"`` (FP64) runs the term groups' sweeps in float-pair arithmetic
+    (``tds_plan_set_arith``).  Six temporary fields are allocated with the object.
     """
 
     DIRS = ("x", "y", "z")
 
-    def __init__(self, shape, P=1, bc="periodic", dtype=torch.float64, width=None, device=None):
+    def __init__(self, shape, P=1, bc="periodic", dtype=torch.float64, width=None, device=None,
+                 arith="native"):
         self.shape = tuple(int(v) for v in shape)
         Ps = (P, P, P) if isinstance(P, int) else tuple(int(p) for p in P)
         self.d1, self.d2 = {}, {}
         for d, p in zip(self.DIRS, Ps):
-            self.d1[d] = Plan(self.shape, d, 1, bc, P=p, dtype=dtype, width=width, device=device)
-            self.d2[d] = Plan(self.shape, d, 2, bc, P=p, dtype=dtype, width=width, device=device)
+            self.d1[d] = Plan(self.shape, d, 1, bc, P=p, dtype=dtype, width=width, device=device, arith=arith)
+            self.d2[d] = Plan(self.shape, d, 2, bc, P=p, dtype=dtype, width=width, device=device, arith=arith)
             for pl in (self.d1[d], self.d2[d]):
                 if not pl.width:
                     raise ValueError("the %s lines do not fit a resident CTA" % d)

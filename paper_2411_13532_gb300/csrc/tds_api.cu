@@ -70,6 +70,29 @@ bool resident_width_ok(const tds_plan *p, int w, bool two) {
     return true;
 }
 
+void configure_pipe(tds_plan *p);
+
+// Resident kernel width (lines per CTA: 32, 16 or 8), among those that let two CTAs share an
+// SM.  FP32 sweeps (bound by HBM) and split-precision FP64 sweeps (bound by the issue rate of the
+// FP32 pipes): the largest such width (fewest per-CTA overheads, the longest contiguous copies;
+// measured for the split FP64 fused pass at 512^3: 16 lines 3.28 ms, 8 lines 4.21 ms).  Native
+// FP64 sweeps are bound by the FP64 pipe: the smallest (most CTAs per SM keep the pipe busy
+// through each CTA's copy and reduced-system phases).  Else 32 if a whole group fits at all.
+void pick_width(tds_plan *p) {
+    p->width = 0;
+    if (p->dtype == TDS_F64 && !p->split) {
+        for (int w = 8; w <= kSZ; w *= 2)
+            if (resident_width_ok(p, w, true)) { p->width = w; break; }
+    } else {
+        for (int w = kSZ; w >= 8; w /= 2)
+            if (resident_width_ok(p, w, true)) { p->width = w; break; }
+    }
+    if (!p->width && resident_width_ok(p, kSZ, false)) p->width = kSZ;
+    p->resident_smem = p->width ? (int)resident_smem_bytes(p->n, p->P, p->dtype, p->width) : 0;
+    p->box_rows = p->width ? resident_box_rows(p->n, p->m, p->dtype, p->width) : 0;
+    configure_pipe(p);
+}
+
 // Persistent pipelined kernel at the plan's width: two tile buffers per CTA (one in use, one
 // loading) when they fit, else one; as many such CTAs as fit on every SM.  TDS_PIPE_NBUF (1..4)
 // overrides the buffer count (tuning).
@@ -218,7 +241,6 @@ tds_plan *new_plan(int nx, int ny, int nz, tds_dir dir, tds_bc bc, int P, tds_dt
 // The operators (host preprocessing and upload), the kernel configuration for this device, the
 // host entry points' streams and events, and the AUTO variant; destroys p on failure.
 tds_status finish_plan(tds_plan *p, tds_plan **out) {
-    const int n = p->n, P = p->P;
     const tds_dtype dtype = p->dtype;
     tds_status s = build_plan(p);
     if (s != TDS_OK) { tds_plan_destroy(p); return s; }
@@ -237,24 +259,8 @@ tds_status finish_plan(tds_plan *p, tds_plan **out) {
     }
     p->smem_optin = optin;
     p->smem_sm = smem_sm;
-    // Resident kernel width (lines per CTA: 32, 16 or 8), among those that let two CTAs share
-    // an SM.  FP32 sweeps are bound by HBM: the largest such width (fewest per-CTA overheads,
-    // the longest contiguous copies).  FP64 sweeps are bound by the FP64 pipe: the smallest
-    // (most CTAs per SM keep the pipe busy through each CTA's copy and reduced-system phases).
-    // Else 32 if a whole group fits at all.
-    p->width = 0;
-    if (dtype == TDS_F64) {
-        for (int w = 8; w <= kSZ; w *= 2)
-            if (resident_width_ok(p, w, true)) { p->width = w; break; }
-    } else {
-        for (int w = kSZ; w >= 8; w /= 2)
-            if (resident_width_ok(p, w, true)) { p->width = w; break; }
-    }
-    if (!p->width && resident_width_ok(p, kSZ, false)) p->width = kSZ;
-    p->resident_smem = p->width ? (int)resident_smem_bytes(n, P, dtype, p->width) : 0;
-    p->box_rows = p->width ? resident_box_rows(n, n / P, dtype, p->width) : 0;
     p->nsm = nsm;
-    configure_pipe(p);
+    pick_width(p);
     // lines per thread in the resident kernels; TDS_RESIDENT_LANES overrides (tuning)
     p->lanes = 1;
     if (const char *e = std::getenv("TDS_RESIDENT_LANES")) {
@@ -457,8 +463,12 @@ tds_status tds_plan_set_width(tds_plan *p, int lines) {
 tds_status tds_plan_set_arith(tds_plan *p, tds_arith arith) {
     if (!p || p->dtype != TDS_F64 || p->band || (arith != TDS_ARITH_NATIVE && arith != TDS_ARITH_SPLIT))
         return TDS_ERR_ARG;
-    p->split = (arith == TDS_ARITH_SPLIT) ? 1 : 0;
-    return TDS_OK;
+    const int split = (arith == TDS_ARITH_SPLIT) ? 1 : 0;
+    if (split == p->split) return TDS_OK;
+    // the width rule follows the arithmetic; AUTO chooses the variant again for that width
+    p->split = split;
+    pick_width(p);
+    return tds_plan_set_variant(p, TDS_VARIANT_AUTO);
 }
 
 tds_status tds_plan_info(const tds_plan *q, int *n, int *nlines, int *P, int *variant, int *smem) {
@@ -540,9 +550,11 @@ tds_status tds_deriv_multi(int count, const tds_plan *const *plans, const int *a
         if (s != TDS_OK) return s;
         for (int j = 0; j < i; ++j)
             if (overlaps(outs[i], bytes, outs[j], bytes)) return TDS_ERR_ALIAS;
-        // one pass needs resident plans of one geometry and width, forward-form operators
+        // one pass needs resident plans of one geometry and width, forward-form operators; split-
+        // precision FP64 plans run one launch per operator (their sweeps, not HBM reads, bound
+        // them: measured at 512^3, D1 + D2 + D1^T 2.93 ms as three launches, 3.30 ms fused)
         fused = fused && p->variant == TDS_VARIANT_RESIDENT && p->lanes == 1 && p->P == p0->P &&
-                p->width == p0->width && p->op[which[i]].adjoint == 0;
+                p->width == p0->width && p->op[which[i]].adjoint == 0 && !p->split;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (fused) return launch_resident_multi(run_plans, which, count, in, outs, st);

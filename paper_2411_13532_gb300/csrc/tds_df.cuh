@@ -13,12 +13,12 @@
 // Every float operation here goes through the _rn intrinsics, so that the compiler never
 // contracts a product and a sum into an FMA (that would break the error terms).
 //
-// Conversions between FP64 and float pairs use integer bit operations (the f64 <-> f32
-// conversion instructions issue on the FP64 pipe on this part): the split keeps the top 24 bits
-// of the significand in h and the next 24 (of the remaining 29, rounded) in l; the join adds the
-// exact FP64 images of h and l with one FP64 addition.  Values must lie in float's normal range
-// with room for the low word: |x| in [2^-70, 2^126]; smaller magnitudes lose low-word bits (an
-// absolute error below 2^-94), zero and subnormal floats map to zero.
+// Conversions between FP64 and float pairs use integer bit operations rather than the f64 <->
+// f32 conversion instructions, which issue on the FP64 pipe on this part: the split keeps the
+// top 24 bits of the significand in h and the next 24 in l; the join adds l to h's FP64
+// encoding as an integer.  Values must lie in float's normal range with room for the low word:
+// |x| in [2^-74, 2^126]; smaller magnitudes lose low-word bits (an absolute error below
+// 2^-98), zero and subnormal floats map to zero.
 #pragma once
 
 #include <cstdint>
@@ -120,23 +120,24 @@ __device__ __forceinline__ DF dot2(DF a1, DF b1, DF a2, DF b2) {
     return df_fast2(s.h, __fadd_rn(s.l, __fadd_rn(e1, e2)));
 }
 
-// FP64 -> float pair by bit operations (see the header): h is x with its significand cut to 24
-// bits (toward zero), l the remaining 29 bits rounded to 24.
+// FP64 -> float pair by bit operations: h is x with its significand cut to 24 bits (toward
+// zero), l the remaining 29 bits rounded to 24 (one integer-to-float conversion, scaled by an
+// exponent built from x's), so |x - (h + l)| <= 2^-48 |x|.  Exponents outside float's range give
+// an infinite h (too large), a zero l (|x| below 2^-74) and a zero h (|x| below 2^-126).
 __device__ __forceinline__ DF df_split(double x) {
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
     const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
     const unsigned sign = hi & 0x80000000u;
-    const int e = static_cast<int>((hi >> 20) & 0x7ffu);               // biased FP64 exponent
-    const unsigned mant = __funnelshift_l(lo, hi, 3) & 0x007fffffu;   // significand bits 51..29
-    const int fe = e - 896;                                            // biased float exponent
-    // the low 29 bits, as a float scaled by 2^(e - 1075) (the weight of the last FP64 bit)
+    const int e = static_cast<int>((hi >> 20) & 0x7ffu);
+    const unsigned mant = __funnelshift_l(lo, hi, 3) & 0x007fffffu;
+    const int fe = e - 896;
     const float r = __uint2float_rn(lo & 0x1fffffffu);
-    const int se = e - 948;                                            // biased exponent of 2^(e - 1075)
+    const int se = e - 948;
     const float scale = __uint_as_float(sign | (static_cast<unsigned>(se > 0 ? se : 0) << 23));
     DF o;
     o.h = (fe > 0) ? __uint_as_float(sign | (static_cast<unsigned>(fe) << 23) | mant) : __uint_as_float(sign);
     o.l = (fe > 0) ? __fmul_rn(r, scale) : 0.0f;
-    if (fe > 254) o.h = __uint_as_float(sign | 0x7f800000u);   // beyond float's range: infinity
+    if (fe > 254) o.h = __uint_as_float(sign | 0x7f800000u);
     return o;
 }
 
@@ -151,8 +152,27 @@ __device__ __forceinline__ double df_f2d(float x) {
     return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
 }
 
-// float pair -> FP64: h + l rounded once
-__device__ __forceinline__ double df_join(DF a) { return __dadd_rn(df_f2d(a.h), df_f2d(a.l)); }
+// float pair -> FP64 by integer arithmetic on the FP64 encoding, without branches and without
+// an FP64 instruction: the FP64 image of |h|, plus or minus l counted in units of the last
+// place of that image (l's significand shifted left by 29 - (e_h - e_l); e_h - e_l >= 23, bits
+// shifted out to the right are dropped, an error below 2^-52 of |h|).  When l has the opposite
+// sign and h is a power of two the result lies in the binade below, whose last place is half as
+// large, so l counts twice as many units there.  A zero h gives zero (in a normalised pair l is
+// then zero too); subnormal words count as zero.
+__device__ __forceinline__ double df_join(DF a) {
+    const unsigned hb = __float_as_uint(a.h), lb = __float_as_uint(a.l);
+    const unsigned hm = hb & 0x7fffffffu, lm = lb & 0x7fffffffu;
+    const unsigned long long base = (static_cast<unsigned long long>((hm >> 3) + (896u << 20)) << 32) | (hm << 29);
+    const int k = static_cast<int>(hm >> 23) - static_cast<int>(lm >> 23);
+    const unsigned subm = static_cast<unsigned>(static_cast<int>(hb ^ lb) >> 31);
+    const int sh = 29 - k + static_cast<int>(subm & ((hm & 0x007fffffu) == 0u ? 1u : 0u));
+    const unsigned ml = (lm >= 0x00800000u) ? ((lm & 0x007fffffu) | 0x00800000u) : 0u;
+    const unsigned u = (sh >= 0) ? (ml << sh) : __funnelshift_rc(ml, 0u, static_cast<unsigned>(-sh));
+    const unsigned long long su = static_cast<unsigned long long>(static_cast<long long>(static_cast<int>(subm)));
+    const unsigned long long r = base + ((static_cast<unsigned long long>(u) ^ su) - su);
+    const unsigned long long bits = (hm < 0x00800000u) ? 0ull : r;
+    return __longlong_as_double(static_cast<long long>(bits | (static_cast<unsigned long long>(hb & 0x80000000u) << 32)));
+}
 
 // The FP64 value's bits carried in a pair (input rows of the split sweeps, which take their
 // differences in FP64 before splitting), and back.

@@ -76,6 +76,8 @@ struct DevOp {
     // per chunk class: rows j >= jpi carry |pi_j| below the cut-off and rows j >= jsa carry
     // |s^a_j| below it (2^-60 for FP64 sweeps, 2^-30 for FP32): those terms are not issued
     int jpi64[3], jsa64[3], jpi32[3], jsa32[3];
+    int jpid[3], jsad[3];   // the same at 2^-56 for the split-precision FP64 sweeps (float pairs
+                            // carry about 47 bits; the margin covers closed lines' end gain of ~100)
     // per chunk class: rows [kfl, kfh) carry the same folded forward record (bitwise, in the
     // sweep's precision) kf = {c0, c1, c2, g}, and rows [kbl, kbh) the same back-substitution
     // coupling kb = s^c_j: the forward factor converges geometrically away from the chunk's

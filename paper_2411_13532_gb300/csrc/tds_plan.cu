@@ -318,7 +318,7 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
             // one entry for all chunks: the latest cut-off of any chunk, and no constant runs
             // (the records of a variable band differ from row to row)
             if (cl == 0) {
-                op.jpi64[0] = op.jsa64[0] = op.jpi32[0] = op.jsa32[0] = 0;
+                op.jpi64[0] = op.jsa64[0] = op.jpi32[0] = op.jsa32[0] = op.jpid[0] = op.jsad[0] = 0;
                 op.kfl64[0] = op.kfh64[0] = op.kbl64[0] = op.kbh64[0] = 0;
                 op.kfl32[0] = op.kfh32[0] = op.kbl32[0] = op.kbh32[0] = 0;
             }
@@ -326,12 +326,16 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
             op.jsa64[0] = std::max(op.jsa64[0], cutoff(1, std::ldexp(1.0, -60)));
             op.jpi32[0] = std::max(op.jpi32[0], cutoff(0, std::ldexp(1.0, -30)));
             op.jsa32[0] = std::max(op.jsa32[0], cutoff(1, std::ldexp(1.0, -30)));
+            op.jpid[0] = std::max(op.jpid[0], cutoff(0, std::ldexp(1.0, -56)));
+            op.jsad[0] = std::max(op.jsad[0], cutoff(1, std::ldexp(1.0, -56)));
             continue;
         }
         op.jpi64[cl] = cutoff(0, std::ldexp(1.0, -60));
         op.jsa64[cl] = cutoff(1, std::ldexp(1.0, -60));
         op.jpi32[cl] = cutoff(0, std::ldexp(1.0, -30));
         op.jsa32[cl] = cutoff(1, std::ldexp(1.0, -30));
+        op.jpid[cl] = cutoff(0, std::ldexp(1.0, -56));
+        op.jsad[cl] = cutoff(1, std::ldexp(1.0, -56));
         // the run of rows around row m-3 (interior in every class) whose records equal that
         // row's, bitwise in each precision
         const int ref = m - 3;

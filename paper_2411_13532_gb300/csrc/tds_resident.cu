@@ -28,6 +28,7 @@
 // The sweep is written once over storage/arithmetic traits (FP32, FP64).
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include <cudaTypedefs.h>
 
@@ -207,8 +208,8 @@ struct TrSplit {
         const float2 b = __ldg(reinterpret_cast<const float2 *>(op.fwdd) + 4 * ((size_t)cls * op.m + j) + 2);
         return df_make(b.x, b.y);
     }
-    static __device__ __forceinline__ int jpi(const DevOp &op, int cls) { return op.jpi64[scal_cls(op, cls)]; }
-    static __device__ __forceinline__ int jsa(const DevOp &op, int cls) { return op.jsa64[scal_cls(op, cls)]; }
+    static __device__ __forceinline__ int jpi(const DevOp &op, int cls) { return op.jpid[scal_cls(op, cls)]; }
+    static __device__ __forceinline__ int jsa(const DevOp &op, int cls) { return op.jsad[scal_cls(op, cls)]; }
     static __device__ __forceinline__ void kf_run(const DevOp &op, int cls, int &lo, int &hi) {
         cls = scal_cls(op, cls);
         lo = op.kfl64[cls];
@@ -1453,9 +1454,11 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_transport(const
         }
         group_sweep<Tr, V, 0>(op, tile, xs, ends, k, c, hb, ha, unsafe);
         // epilogue on this thread's rows (the sweep leaves them in the tile): o = 0 writes
-        // -1/2 u_j r, the others add their weight times r to what is there
+        // -1/2 u_j r, the others add their weight times r to what is there (split-precision
+        // sweeps leave FP64 results: their epilogue runs in FP64)
         if constexpr (sizeof(S) == 8) {
-            const A wgt = (o == 2) ? A(ta.nu) : A(-0.5);
+            using E = std::conditional_t<Tr::kDF, double, A>;
+            const E wgt = (o == 2) ? E(ta.nu) : E(-0.5);
             const S *srcb = (o == 0) ? uj : out;
             for (int j0 = 0; j0 < m; j0 += kB) {
                 const int nb = (m - j0 < kB) ? m - j0 : kB;
@@ -1470,8 +1473,8 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_transport(const
                         Pack<S, V> x;
 #pragma unroll
                         for (int i = 0; i < V; ++i)
-                            x.v[i] = (o == 0) ? S(wgt * A(q[b].v[i]) * A(r.v[i]))
-                                              : S(mad(wgt, A(r.v[i]), A(q[b].v[i])));
+                            x.v[i] = (o == 0) ? S(wgt * E(q[b].v[i]) * E(r.v[i]))
+                                              : S(mad(wgt, E(r.v[i]), E(q[b].v[i])));
                         stv<S, V>(out + ob + (size_t)(j0 + b) * kSZ, x);
                     }
                 }
@@ -2188,6 +2191,10 @@ tds_status launch_resident_transport(const tds_plan *d1, const tds_plan *d2, con
         !encode_rows(&mm.in, ui, d1->dtype, (long long)d1->n * (d1->nlines / kSZ), d1->width, d1->box_rows))
         return TDS_ERR_CUDA;
     const int W = d1->width, smem = d1->resident_smem, L = d1->lanes;
+    if (split_sweep(d1, ta.op1) && split_sweep(d2, ta.op2))
+        return W == 16 ? launch_transport_v<TrSplit<16>, 1>(ta, mm, ui, uj, out, smem, st)
+             : W == 8  ? launch_transport_v<TrSplit<8>, 1>(ta, mm, ui, uj, out, smem, st)
+                       : launch_transport_v<TrSplit<>, 1>(ta, mm, ui, uj, out, smem, st);
     if (d1->dtype == TDS_F64)
         return W == 16 ? launch_transport_t<TrF64w<16>>(ta, mm, ui, uj, out, smem, L, st)
              : W == 8  ? launch_transport_t<TrF64w<8>>(ta, mm, ui, uj, out, smem, L, st)

@@ -74,7 +74,8 @@ def test_split_filter_every_point(bc):
 
 @pytest.mark.parametrize("bc", ["periodic", "closed"])
 def test_split_fused_pass(bc):
-    """tds_deriv_multi with split plans: bitwise the single split calls, and against the oracle."""
+    """tds_deriv_multi with split plans (one launch per operator): bitwise the single split
+    calls, and against the oracle."""
     shape = (16, 48, 64)
     cart = np.random.default_rng(23).uniform(-1, 1, shape)
     h = oracle.grid_spacing(64, bc)
@@ -180,3 +181,35 @@ def test_fanout_copy_bitwise_and_rules():
     o = torch.empty((1 << 12) + 4, dtype=torch.float32, device="cuda")
     with pytest.raises(tds.TdsError):
         tds.fanout_copy(x[1:-3], [o[4:4 + x.numel() - 4]])  # misaligned input
+
+
+@pytest.mark.parametrize("direction", ["x", "y", "z"])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+@pytest.mark.parametrize("same", [False, True])
+def test_split_transport_term_every_point(direction, bc, same):
+    """One transport term group (Eq. mom-comps) with split plans: three split sweeps, the product
+    and the combination in FP64; every point against the oracle."""
+    shape, Ps = (20, 64, 96), {"x": 4, "y": 2, "z": 5}
+    rng = np.random.default_rng(3 + "xyz".index(direction) + 7 * same)
+    ui = rng.uniform(-1, 1, shape)
+    uj = ui if same else rng.uniform(-1, 1, shape)
+    d1 = tds.Plan(shape, direction, 1, bc, P=Ps[direction], arith="split")
+    d2 = tds.Plan(shape, direction, 2, bc, P=Ps[direction], arith="split")
+    a = to_device_layout(ui, direction, "f64")
+    b = a if same else to_device_layout(uj, direction, "f64")
+    out = tds.transport_term(d1, d2, a, b, 0.02)
+    mx, rms = rel_errors(from_device_layout(out, direction, shape), oracle.transport_term(ui, uj, direction, 0.02, bc))
+    assert mx <= TOL["f64"], (mx, rms)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+def test_split_transport_rhs_every_point(bc):
+    shape = (20, 64, 96)
+    rng = np.random.default_rng(17)
+    u = [rng.uniform(-1, 1, shape) for _ in range(3)]
+    rhs = tds.TransportRHS(shape, P=(4, 2, 5), bc=bc, arith="split")
+    out = rhs([to_device_layout(f, "x", "f64") for f in u], 0.02)
+    ref = oracle.transport_rhs(u, 0.02, bc)
+    for i in range(3):
+        mx, rms = rel_errors(from_device_layout(out[i], "x", shape), ref[i])
+        assert mx <= TOL["f64"], (i, mx, rms)
