@@ -537,7 +537,9 @@ SWEEP_CASES = [
     ("512^3 solve A x = d, x periodic/closed P=8 FP64/FP32", (512, 512, 512), "x", (1, 2),
      ("periodic", "closed"), (8,), ("f64", "f32"), "solve"),
     ("512^3 compact filter (alpha_f 0.45) and mid-point interpolation, x, P=8 FP64/FP32", (512, 512, 512),
-     "x", ("filter", "interp"), ("periodic",), (8,), ("f64", "f32"), "deriv"),
+     "x", ("filter", "interp"), ("periodic", "closed"), (8,), ("f64", "f32"), "deriv"),
+    ("512^3 batched tridiagonal solve, variable-coefficient band (implicit diffusion on a stretched grid), "
+     "x, P=8 FP64/FP32", (512, 512, 512), "x", ("band",), ("periodic", "closed"), (8,), ("f64", "f32"), "band"),
 ]
 
 
@@ -557,6 +559,7 @@ def run_sweep(args):
     reps = max(args.steps, 5)
     import numpy as np
     import oracle
+    from paper_2411_13532_gb300 import inputs
     oracle.build()
 
     def oracle_rate(n, order, bc, kind):
@@ -569,11 +572,15 @@ def run_sweep(args):
         if order == "filter":
             oracle.filter_lines(lines, 0.45, bc)
         elif order == "interp":
-            oracle.interp_lines(lines)
+            oracle.interp_lines(lines, bc)
         elif kind == "adjoint":
             oracle.deriv_adjoint_lines(lines, order, bc, h)
         elif kind == "solve":
             a, b, c, _ = oracle.bands(n, order, bc, h)
+            for d in lines:
+                oracle.tridiag_solve(a, b, c, d, bc == "periodic")
+        elif kind == "band":
+            a, b, c = inputs.diffusion_band(n, seed=1)
             for d in lines:
                 oracle.tridiag_solve(a, b, c, d, bc == "periodic")
         else:
@@ -591,11 +598,16 @@ def run_sweep(args):
                 for order in orders:
                     for bc in bcs:
                         for P in Ps:
-                            plan = tds.Plan(shape, direc, order, bc, P=P, dtype=dt,
-                                            alpha_f=0.45 if order == "filter" else None)
+                            n = shape[{"x": 2, "y": 1, "z": 0}[direc]]
+                            if kind == "band":
+                                plan = tds.Plan(shape, direc, 0, bc, P=P, dtype=dt,
+                                                band=inputs.diffusion_band(n, seed=1))
+                            else:
+                                plan = tds.Plan(shape, direc, order, bc, P=P, dtype=dt,
+                                                alpha_f=0.45 if order == "filter" else None)
                             ws = plan.workspace()
                             fn = {"adjoint": lambda: plan.adjoint(x, y, ws), "solve": lambda: plan.solve(x, y, ws),
-                                  "deriv": lambda: plan.deriv(x, y, ws)}[kind]
+                                  "band": lambda: plan.solve(x, y, ws), "deriv": lambda: plan.deriv(x, y, ws)}[kind]
                             for _ in range(max(args.warmup, 3)):
                                 fn()
                             times = []

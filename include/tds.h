@@ -122,15 +122,18 @@ TDS_API tds_status tds_plan_create_filter(tds_plan **out, int nx, int ny, int nz
 
 /*
  * tds_plan_create_interp -- a plan whose operator is the sixth-order compact interpolation from
- * the nodes to the mid-points of a periodic line (Lele 1992's family, as for the filter):
+ * the nodes to the mid-points (Lele 1992's family, as for the filter):
  *     3/10 g[i-1] + g[i] + 3/10 g[i+1] = 3/4 (f[i] + f[i+1]) + 1/20 (f[i-1] + f[i+2]),
- * g[i] approximating f at x_i + h/2.  Lines are cyclic (a closed line has one mid-point fewer
- * than nodes, which this layout does not represent).  tds_deriv interpolates to the mid-points;
- * tds_deriv_adjoint applies the transpose, which is the interpolation from mid-points (g[i] at
- * x_i + h/2) back to the nodes.  Arguments, rules and errors as tds_plan_create.
+ * g[i] approximating f at x_i + h/2.  Periodic lines have n mid-points.  A closed line has n-1
+ * (g[0..n-2]): the first and the last use the compact closure exact through degree 4 (the paper
+ * prints none), g[0] + 5/3 g[1] = 5/24 f[0] + 15/8 f[1] + 5/8 f[2] - 1/24 f[3] and its mirror
+ * image, and the result's last slot g[n-1] is set to zero so that the layout maps n points to
+ * n.  tds_deriv interpolates to the mid-points; tds_deriv_adjoint applies the transpose, which is
+ * the interpolation from mid-points (g[i] at x_i + h/2) back to the nodes (on closed lines the
+ * input's last slot is not read).  Arguments, rules and errors as tds_plan_create.
  */
-TDS_API tds_status tds_plan_create_interp(tds_plan **out, int nx, int ny, int nz, tds_dir dir, int P,
-                                          tds_dtype dtype, int sz, tds_reduced mode);
+TDS_API tds_status tds_plan_create_interp(tds_plan **out, int nx, int ny, int nz, tds_dir dir, tds_bc bc,
+                                          int P, tds_dtype dtype, int sz, tds_reduced mode);
 
 /*
  * tds_plan_create_band -- a plan for the batched tridiagonal solve A x = d with a caller-given

@@ -222,21 +222,22 @@ def filter_adjoint_lines(lines, alpha_f, bc):
     return _lines_call(_load().tdso_deriv_adjoint_lines, lines, FILTER, bc, alpha_f)
 
 
-def interp_lines(lines):
+def interp_lines(lines, bc="periodic"):
     """Sixth-order compact interpolation from the nodes to the mid-points x_i + h/2 (Lele 1992,
-    App. C.1), cyclic lines."""
-    return _lines_call(_load().tdso_deriv_lines, lines, INTERP, "periodic", 1.0)
+    App. C.1); closed lines give n - 1 mid-points and a zero in the last slot."""
+    return _lines_call(_load().tdso_deriv_lines, lines, INTERP, bc, 1.0)
 
 
-def interp_adjoint_lines(lines):
-    """Transpose of ``interp_lines``: the interpolation from the mid-points back to the nodes."""
-    return _lines_call(_load().tdso_deriv_adjoint_lines, lines, INTERP, "periodic", 1.0)
+def interp_adjoint_lines(lines, bc="periodic"):
+    """Transpose of ``interp_lines``: the interpolation from the mid-points back to the nodes
+    (closed lines: the last slot of the input is not used)."""
+    return _lines_call(_load().tdso_deriv_adjoint_lines, lines, INTERP, bc, 1.0)
 
 
 def apply_op(cart, direction, op, bc, param=None, adjoint=False):
     """One of the line operators along a direction of a Cartesian field: op 1 / 2 (derivatives,
     param = h or None for the default spacing), 3 (filter, param = alpha_f) or 4 (mid-point
-    interpolation, cyclic lines)."""
+    interpolation)."""
     cart = np.ascontiguousarray(cart, dtype=np.float64)
     n = {"x": cart.shape[2], "y": cart.shape[1], "z": cart.shape[0]}[direction]
     if op in (1, 2) and param is None:

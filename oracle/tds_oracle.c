@@ -39,11 +39,18 @@
  *     (transfer function 1 at k = 0, 0 at the grid's odd-even mode); closed lines keep the
  *     end values (g[0] = f[0], g[n-1] = f[n-1]) and use the second-order member at rows 1
  *     and n-2 (a0 = a1 = 1/2 + alpha_f, a2 = 0);
- *   order 4, mid-point interpolation (Lele 1992, App. C.1, sixth-order member), cyclic
- *     lines only, h unused: g[i] approximates f at x[i] + h/2,
+ *   order 4, mid-point interpolation (Lele 1992, App. C.1, sixth-order member), h unused:
+ *     g[i] approximates f at x[i] + h/2,
  *       alpha g[i-1] + g[i] + alpha g[i+1] = (a/2)(f[i] + f[i+1]) + (b/2)(f[i-1] + f[i+2]),
  *       alpha = 3/10, a = 3/2, b = 1/10;
  *     its transpose (the adjoint) is the interpolation from mid-points back to the nodes.
+ *     Closed lines have n - 1 mid-points g[0..n-2]; row n-1 is a zero row (g[n-1] = 0, no
+ *     coupling), so that n points map to n.  The first mid-point uses the compact closure with
+ *     four nodes that is exact for polynomials through degree 4 (the unique such row with one
+ *     coupling g[1]: five conditions, five coefficients),
+ *       g[0] + (5/3) g[1] = (5/24) f[0] + (15/8) f[1] + (5/8) f[2] - (1/24) f[3],
+ *     and row n-2 its mirror image, (5/3) g[n-3] + g[n-2] = (5/24) f[n-1] + (15/8) f[n-2]
+ *     + (5/8) f[n-3] - (1/24) f[n-4]; rows 1 .. n-3 are interior rows.
  *
  * Band convention: row i of A is a[i]*u[i-1] + b[i]*u[i] + c[i]*u[i+1]; for cyclic
  * lines a[0] multiplies u[n-1] and c[n-1] multiplies u[0].  Row i of B is stored as 7
@@ -81,13 +88,21 @@ static int other_bands(int n, int order, int periodic, double param,
         return 0;
     }
     /* order 4 */
-    if (!periodic) return -1;
     const double alpha = 3.0 / 10.0, ha = 0.5 * 1.5, hb = 0.5 * (1.0 / 10.0);
     for (int i = 0; i < n; ++i) {
         a[i] = alpha; b[i] = 1.0; c[i] = alpha;
         double *r = B7 + (size_t)TAPS * i + MID;
         r[-1] = hb; r[0] = ha; r[1] = ha; r[2] = hb;
     }
+    if (periodic) return 0;
+    /* closed: mid-points 0 .. n-2, the closure rows 0 and n-2, the zero row n-1 */
+    double *r0 = B7 + MID, *rm = B7 + (size_t)TAPS * (n - 2) + MID, *rl = B7 + (size_t)TAPS * (n - 1) + MID;
+    for (int o = -MID; o <= MID; ++o) { r0[o] = 0.0; rm[o] = 0.0; rl[o] = 0.0; }
+    a[0] = 0.0; b[0] = 1.0; c[0] = 5.0 / 3.0;
+    r0[0] = 5.0 / 24.0; r0[1] = 15.0 / 8.0; r0[2] = 5.0 / 8.0; r0[3] = -1.0 / 24.0;
+    a[n - 2] = 5.0 / 3.0; b[n - 2] = 1.0; c[n - 2] = 0.0;
+    rm[1] = 5.0 / 24.0; rm[0] = 15.0 / 8.0; rm[-1] = 5.0 / 8.0; rm[-2] = -1.0 / 24.0;
+    a[n - 1] = 0.0; b[n - 1] = 1.0; c[n - 1] = 0.0;
     return 0;
 }
 

@@ -48,7 +48,8 @@ class Plan:
     batched tridiagonal solve of that band instead (``tds_plan_create_band``; ``order`` and ``h``
     are ignored and only ``solve`` is available).  ``order="filter"`` (with ``alpha_f``) makes the
     fourth-order compact filter and ``order="interp"`` the sixth-order interpolation to the
-    mid-points of periodic lines (``tds_plan_create_filter`` / ``tds_plan_create_interp``;
+    mid-points (closed lines: n - 1 of them, the last slot zero) (``tds_plan_create_filter`` /
+    ``tds_plan_create_interp``;
     ``deriv`` applies them, ``adjoint`` their transposes).  ``arith="split"`` (FP64 plans) runs
     the resident sweeps of forward-form operators in float-pair arithmetic
     (``tds_plan_set_arith``).
@@ -79,11 +80,9 @@ class Plan:
                                                     _lib.DTYPES[_TORCH_DTYPES[dtype]], 32,
                                                     _lib.MODES[mode]), "tds_plan_create_filter")
             elif self.order == 4:
-                if bc != "periodic":
-                    raise ValueError("the mid-point interpolation needs periodic lines")
                 _lib.check(L.tds_plan_create_interp(ctypes.byref(h_), nx, ny, nz, _lib.DIRS[direction],
-                                                    self.P, _lib.DTYPES[_TORCH_DTYPES[dtype]], 32,
-                                                    _lib.MODES[mode]), "tds_plan_create_interp")
+                                                    _lib.BCS[bc], self.P, _lib.DTYPES[_TORCH_DTYPES[dtype]],
+                                                    32, _lib.MODES[mode]), "tds_plan_create_interp")
             elif band is None:
                 _lib.check(L.tds_plan_create(ctypes.byref(h_), nx, ny, nz, _lib.DIRS[direction],
                                              self.order, _lib.BCS[bc], self.P, self.h,

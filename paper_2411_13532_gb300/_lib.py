@@ -23,7 +23,7 @@ _ip = ctypes.POINTER(ctypes.c_int)
 SIGNATURES = [
     ("tds_plan_create", _i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i, _i, _i, _d, _i, _i, _i]),
     ("tds_plan_create_filter", _i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _d, _i, _i, _i, _i, _i]),
-    ("tds_plan_create_interp", _i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i, _i, _i, _i]),
+    ("tds_plan_create_interp", _i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i, _i, _i, _i, _i]),
     ("tds_plan_create_band", _i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i]),
     ("tds_plan_set_variant", _i, [_vp, _i]),
     ("tds_plan_set_width", _i, [_vp, _i]),

@@ -365,16 +365,17 @@ tds_status tds_plan_create_filter(tds_plan **out, int nx, int ny, int nz, tds_di
     return finish_plan(p, out);
 }
 
-tds_status tds_plan_create_interp(tds_plan **out, int nx, int ny, int nz, tds_dir dir, int P,
+tds_status tds_plan_create_interp(tds_plan **out, int nx, int ny, int nz, tds_dir dir, tds_bc bc, int P,
                                   tds_dtype dtype, int sz, tds_reduced mode) {
     if (!out) return TDS_ERR_ARG;
     *out = nullptr;
-    if (dir < TDS_DIR_X || dir > TDS_DIR_Z || (dtype != TDS_F64 && dtype != TDS_F32) ||
+    if (dir < TDS_DIR_X || dir > TDS_DIR_Z || (bc != TDS_BC_PERIODIC && bc != TDS_BC_CLOSED) ||
+        (dtype != TDS_F64 && dtype != TDS_F32) ||
         (mode != TDS_REDUCED_EXACT && mode != TDS_REDUCED_PAPER_DROP) || sz != kSZ || P < 1)
         return TDS_ERR_ARG;
     const tds_status sh = check_shape(nx, ny, nz, dir, P);
     if (sh != TDS_OK) return sh;
-    tds_plan *p = new_plan(nx, ny, nz, dir, TDS_BC_PERIODIC, P, dtype, mode);
+    tds_plan *p = new_plan(nx, ny, nz, dir, bc, P, dtype, mode);
     if (!p) return TDS_ERR_NOMEM;
     p->order = 4;
     p->h = 1.0;

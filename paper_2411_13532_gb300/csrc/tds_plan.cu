@@ -88,8 +88,11 @@ void scheme_line(int n, int order, bool periodic, double h, LineOperator &L) {
 //     + (a2/2)(f[i+2] + f[i-2]), a0 = 5/8 + 3 alpha_f/4, a1 = 1/2 + alpha_f,
 //     a2 = -1/8 + alpha_f/4; closed lines keep the end values and use the second-order member
 //     (a0 = a1 = 1/2 + alpha_f) at rows 1 and n-2;
-//   order 4, interpolation from the nodes to the mid-points x_i + h/2, the sixth-order member,
-//     cyclic lines: 3/10 g[i-1] + g[i] + 3/10 g[i+1] = 3/4 (f[i] + f[i+1]) + 1/20 (f[i-1] + f[i+2]).
+//   order 4, interpolation from the nodes to the mid-points x_i + h/2, the sixth-order member:
+//     3/10 g[i-1] + g[i] + 3/10 g[i+1] = 3/4 (f[i] + f[i+1]) + 1/20 (f[i-1] + f[i+2]); a closed
+//     line has n-1 mid-points: the first and last use the compact closure exact through degree 4,
+//     g[0] + 5/3 g[1] = 5/24 f[0] + 15/8 f[1] + 5/8 f[2] - 1/24 f[3] and its mirror image, and
+//     row n-1 is a zero row (g[n-1] = 0) so that the layout maps n points to n.
 void other_line(int n, int order, bool periodic, double alpha_f, LineOperator &L) {
     L.a.assign(n, 0.0); L.b.assign(n, 1.0); L.c.assign(n, 0.0);
     L.taps.assign((size_t)n * kTaps, 0.0);
@@ -104,7 +107,17 @@ void other_line(int n, int order, bool periodic, double alpha_f, LineOperator &L
             t[-1] = 0.05; t[0] = 0.75; t[1] = 0.75; t[2] = 0.05;
         }
     }
-    if (periodic) return;   // order 4 plans are cyclic (checked at creation)
+    if (periodic) return;
+    if (order == 4) {
+        double *t0 = &L.taps[3], *tm = &L.taps[(size_t)(n - 2) * kTaps + 3], *tl = &L.taps[(size_t)(n - 1) * kTaps + 3];
+        for (int o = -3; o <= 3; ++o) { t0[o] = 0.0; tm[o] = 0.0; tl[o] = 0.0; }
+        L.a[0] = 0.0; L.c[0] = 5.0 / 3.0;
+        t0[0] = 5.0 / 24.0; t0[1] = 15.0 / 8.0; t0[2] = 5.0 / 8.0; t0[3] = -1.0 / 24.0;
+        L.a[n - 2] = 5.0 / 3.0; L.c[n - 2] = 0.0;
+        tm[1] = 5.0 / 24.0; tm[0] = 15.0 / 8.0; tm[-1] = 5.0 / 8.0; tm[-2] = -1.0 / 24.0;
+        L.a[n - 1] = 0.0; L.c[n - 1] = 0.0;
+        return;
+    }
     for (int e = 0; e < 2; ++e) {
         const int J0 = e ? n - 1 : 0, J1 = e ? n - 2 : 1;
         double *t0 = &L.taps[(size_t)J0 * kTaps + 3], *t1 = &L.taps[(size_t)J1 * kTaps + 3];

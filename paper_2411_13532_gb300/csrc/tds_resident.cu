@@ -790,9 +790,10 @@ __device__ __forceinline__ void stencil_sweep(const DevOp &op, int k, int cls, t
             sweep_interior<Tr, V, kSymD, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
     } else if (op.symmetric < 0) {
         sweep_interior<Tr, V, kAnti, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
-    } else if constexpr (FWD && V == 1) {
-        // the half-point forms belong to the mid-point interpolation and its transpose: cyclic
-        // lines only (forward form) and one line per thread (the planner fixes both)
+    } else if constexpr (V == 1) {
+        // the half-point forms belong to the mid-point interpolation and its transpose, one line
+        // per thread (the planner fixes it): the forward sweep, and on closed lines the B^T pass
+        // of the transpose
         if (op.symmetric == 2) sweep_interior<Tr, V, kHalfFwd, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
         else sweep_interior<Tr, V, kHalfBwd, FWD>(op, cls, row, jb, je, w, ha, dprev, S, unsafe);
     }

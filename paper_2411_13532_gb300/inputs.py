@@ -12,6 +12,8 @@ paper prints no field, so these stand in for it):
     or N(0, ``noise``).
   * ``uniform_field``: i.i.d. U(-1,1).
   * ``normal_field``: i.i.d. N(0,1).
+  * ``diffusion_band``: a variable-coefficient tridiagonal band (implicit diffusion on a
+    stretched grid), the input of the batched solve.
 Mode parameters come from ``numpy.random.default_rng(seed)``; bulk random numbers come
 from a ``torch.Generator`` seeded with ``seed`` on the target device (CPU and CUDA
 generators give different streams, so a field is generated once and then copied).
@@ -60,6 +62,27 @@ def fourier_field(shape, seed, n_modes=4, kmax=20, noise=1e-3, noise_kind="unifo
         else:
             raise ValueError(noise_kind)
     return f.to(dtype), (k, amp, phase)
+
+
+def diffusion_band(n, seed, dmax=100.0):
+    """A variable-coefficient tridiagonal band (a, b, c), numpy arrays of n entries: one
+    backward-Euler step of d/dx (kappa d/dx) on a tanh-stretched grid of n cells (faces clustered
+    at both ends), kappa(x) = 1 + 0.8 sin(3 x + phase) with a seeded phase, the step chosen so
+    that the largest dt kappa / dx^2 is ``dmax``: the implicit system of an ADI sweep, a[i] x[i-1]
+    + b[i] x[i] + c[i] x[i+1] = d[i] (b = 1 + the two couplings: diagonally dominant by 1)."""
+    rng = np.random.default_rng(seed)
+    s = np.linspace(0.0, 1.0, n + 1)
+    x = np.tanh(2.0 * (s - 0.5)) / np.tanh(1.0)
+    dxf = np.diff(x)
+    xc = 0.5 * (x[1:] + x[:-1])
+    kappa = 1.0 + 0.8 * np.sin(3.0 * xc + rng.uniform(0.0, 2.0 * math.pi))
+    kf = 0.5 * (kappa + np.roll(kappa, -1))
+    dxc = 0.5 * (dxf + np.roll(dxf, -1))
+    gp = kf / (dxc * dxf)
+    gm = np.roll(kf, 1) / (np.roll(dxc, 1) * dxf)
+    dt = dmax / max(gp.max(), gm.max())
+    gp, gm = dt * gp, dt * gm
+    return -gm, 1.0 + gm + gp, -gp
 
 
 def uniform_field(shape, seed, device="cpu", dtype=torch.float64):

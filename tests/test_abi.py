@@ -87,14 +87,15 @@ def test_null_pointer_errors_need_no_gpu(L):
     assert L.tds_reorder_add(None, None, 32, 32, 1, 0, 1, 0, 32, None) == _lib.ERR_ARG
     assert L.tds_transport(None, None, None, None, 0.1, None, None) == _lib.ERR_ARG
     assert L.tds_plan_create_filter(None, 64, 64, 64, 0, 0.4, 0, 1, 0, 32, 0) == _lib.ERR_ARG
-    assert L.tds_plan_create_interp(None, 64, 64, 64, 0, 1, 0, 32, 0) == _lib.ERR_ARG
+    assert L.tds_plan_create_interp(None, 64, 64, 64, 0, 0, 1, 0, 32, 0) == _lib.ERR_ARG
     # argument and shape rules of the filter and interpolation plans, checked before the device
     for af, want in ((0.5, _lib.ERR_ARG), (-0.5, _lib.ERR_ARG), (float("nan"), _lib.ERR_ARG)):
         assert L.tds_plan_create_filter(ctypes.byref(h), 64, 64, 64, 0, af, 0, 1, 0, 32, 0) == want
         assert not h.value
     assert L.tds_plan_create_filter(ctypes.byref(h), 64, 64, 64, 0, 0.4, 0, 3, 0, 32, 0) == _lib.ERR_SHAPE
-    assert L.tds_plan_create_interp(ctypes.byref(h), 64, 64, 64, 3, 1, 0, 32, 0) == _lib.ERR_ARG
-    assert L.tds_plan_create_interp(ctypes.byref(h), 64, 64, 64, 0, 32, 0, 32, 0) == _lib.ERR_SHAPE
+    assert L.tds_plan_create_interp(ctypes.byref(h), 64, 64, 64, 3, 0, 1, 0, 32, 0) == _lib.ERR_ARG
+    assert L.tds_plan_create_interp(ctypes.byref(h), 64, 64, 64, 0, 2, 1, 0, 32, 0) == _lib.ERR_ARG
+    assert L.tds_plan_create_interp(ctypes.byref(h), 64, 64, 64, 0, 1, 32, 0, 32, 0) == _lib.ERR_SHAPE
     assert not h.value
     assert L.tds_plan_set_width(None, 32) == _lib.ERR_ARG
     assert L.tds_plan_set_arith(None, 1) == _lib.ERR_ARG

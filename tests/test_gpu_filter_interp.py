@@ -1,4 +1,5 @@
-"""GPU parity of the compact filter and mid-point interpolation plans against the FP64 oracle.
+"""GPU parity of the compact filter and mid-point interpolation plans (periodic and closed lines)
+against the FP64 oracle.
 
 Every point on small grids over dtype x variant x direction x boundary x P x (operator,
 transpose) x CTA width; the segmented variant on long lines; sampled whole lines at 512^3, P = 8;
@@ -33,7 +34,7 @@ def built():
 AF = 0.45
 SMALL = (12, 40, 32)
 PS = {"x": [1, 2, 8], "y": [1, 2, 5], "z": [1, 3]}
-OPS = [("filter", "periodic"), ("filter", "closed"), ("interp", "periodic")]
+OPS = [("filter", "periodic"), ("filter", "closed"), ("interp", "periodic"), ("interp", "closed")]
 
 
 def make_plan(shape, direction, kind, bc, P, dtype, **kw):
@@ -45,7 +46,7 @@ def make_plan(shape, direction, kind, bc, P, dtype, **kw):
 def reference(cart, direction, kind, bc, adjoint):
     if kind == "filter":
         return oracle.apply_op(cart, direction, oracle.FILTER, bc, AF, adjoint=adjoint)
-    return oracle.apply_op(cart, direction, oracle.INTERP, "periodic", adjoint=adjoint)
+    return oracle.apply_op(cart, direction, oracle.INTERP, bc, adjoint=adjoint)
 
 
 def rand_cart(shape, dtype, seed):
@@ -113,8 +114,6 @@ def test_segmented_long_lines(dtype, op):
 
 def test_plan_rules():
     with pytest.raises(ValueError):
-        tds.Plan(SMALL, "x", "interp", "closed")           # cyclic lines only
-    with pytest.raises(ValueError):
         tds.Plan(SMALL, "x", "filter", "periodic")         # alpha_f missing
     with pytest.raises(tds.TdsError):
         tds.Plan(SMALL, "x", "filter", "periodic", alpha_f=0.5)
@@ -143,6 +142,24 @@ def test_filter_and_interp_identities_on_device():
     assert torch.max(torch.abs(y)).item() <= 1e-14
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_closed_interp_last_slot(dtype):
+    """Closed lines have n - 1 mid-points: the interpolation writes exactly zero to the last slot
+    of every line, and its transpose does not read that slot of its input."""
+    shape = (8, 32, 64)
+    cart = rand_cart(shape, dtype, seed=19)
+    for P in (1, 4):
+        plan = make_plan(shape, "x", "interp", "closed", P, dtype)
+        x = to_device_layout(cart, "x", dtype)
+        y = from_device_layout(plan.deriv(x), "x", shape)
+        assert not np.any(y[:, :, -1])
+        cart2 = cart.copy()
+        cart2[:, :, -1] = 3.0
+        a = plan.adjoint(x)
+        b = plan.adjoint(to_device_layout(cart2, "x", dtype))
+        assert torch.equal(a, b)
+
+
 FULL = (512, 512, 512)
 
 
@@ -156,7 +173,7 @@ def test_full_size_sampled_lines(dtype, direction):
     n = 512
     lines = sample_lines(fx.numel() // n, 32, seed=11)
     src = gather_lines(fx, direction, shape, lines).double().cpu().numpy()
-    for kind, bc in (("filter", "periodic"), ("filter", "closed"), ("interp", "periodic")):
+    for kind, bc in OPS:
         plan = make_plan(shape, direction, kind, bc, 8, dtype)
         for adjoint in (False, True):
             y = plan.adjoint(fx) if adjoint else plan.deriv(fx)
@@ -164,7 +181,7 @@ def test_full_size_sampled_lines(dtype, direction):
             if kind == "filter":
                 ref = (oracle.filter_adjoint_lines if adjoint else oracle.filter_lines)(src, AF, bc)
             else:
-                ref = (oracle.interp_adjoint_lines if adjoint else oracle.interp_lines)(src)
+                ref = (oracle.interp_adjoint_lines if adjoint else oracle.interp_lines)(src, bc)
             mx, rms = rel_errors(got, ref)
             report("512^3 %s%s %s P=8" % (kind, "T" if adjoint else "", direction), dtype=dtype,
                    variant=plan.variant, width=plan.width, max_rel=mx, rms_rel=rms)

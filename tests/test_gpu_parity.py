@@ -204,18 +204,7 @@ def variable_band(n, seed, kind):
         b = (np.abs(a) + np.abs(c)) * rng.uniform(1.2, 2.0, n) + rng.uniform(0.1, 0.3, n)
         b *= np.where(rng.uniform(size=n) < 0.3, -1.0, 1.0)   # dominant diagonal of either sign
         return a, b, c
-    s = np.linspace(0.0, 1.0, n + 1)
-    x = np.tanh(2.0 * (s - 0.5)) / np.tanh(1.0)              # cell faces clustered at both ends
-    dxf = np.diff(x)                                          # cell widths (n)
-    xc = 0.5 * (x[1:] + x[:-1])
-    kappa = 1.0 + 0.8 * np.sin(3.0 * xc + rng.uniform(0, 6.28))
-    kf = 0.5 * (kappa + np.roll(kappa, -1))                   # face diffusivity between i and i+1
-    dxc = 0.5 * (dxf + np.roll(dxf, -1))
-    gp = kf / (dxc * dxf)                                     # coupling to i+1, per unit dt
-    gm = np.roll(kf, 1) / (np.roll(dxc, 1) * dxf)             # coupling to i-1, per unit dt
-    dt = 100.0 / max(gp.max(), gm.max())
-    gp, gm = dt * gp, dt * gm
-    return -gm, 1.0 + gm + gp, -gp
+    return inputs.diffusion_band(n, seed, dmax=100.0)
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])

@@ -31,7 +31,7 @@ def built():
 SMALL = (12, 40, 32)
 AF = 0.45
 OPS = [(1, "periodic"), (1, "closed"), (2, "periodic"), (2, "closed"),
-       ("filter", "periodic"), ("filter", "closed"), ("interp", "periodic")]
+       ("filter", "periodic"), ("filter", "closed"), ("interp", "periodic"), ("interp", "closed")]
 
 
 def make_plan(shape, direction, op, bc, dtype, P=1):
@@ -47,7 +47,7 @@ def reference(cart, direction, op, bc):
     if op == "filter":
         return oracle.apply_op(cart, direction, oracle.FILTER, bc, AF)
     if op == "interp":
-        return oracle.apply_op(cart, direction, oracle.INTERP, "periodic")
+        return oracle.apply_op(cart, direction, oracle.INTERP, bc)
     return oracle.deriv(cart, direction, op, bc)
 
 

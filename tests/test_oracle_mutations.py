@@ -38,6 +38,10 @@ MUTATIONS = [
      "a0 = 5.0 / 8.0 + 0.75 * af", "a0 = 5.0 / 8.0 + 0.5 * af"),
     ("filter closure row 1 centre 1/2 - alpha_f", C, "r1[0] = 0.5 + af;", "r1[0] = 0.5 - af;"),
     ("interpolation inner pair 1.4/2 for 3/2 / 2", C, "ha = 0.5 * 1.5", "ha = 0.5 * 1.4"),
+    ("closed interpolation closure: coupling 4/3 for 5/3", C,
+     "a[0] = 0.0; b[0] = 1.0; c[0] = 5.0 / 3.0;", "a[0] = 0.0; b[0] = 1.0; c[0] = 4.0 / 3.0;"),
+    ("closed interpolation mirror row: taps not mirrored", C,
+     "rm[1] = 5.0 / 24.0; rm[0] = 15.0 / 8.0;", "rm[1] = 15.0 / 8.0; rm[0] = 5.0 / 24.0;"),
     ("transport: conservative term subtracted", PY, "-0.5 * (conv + cons)", "-0.5 * (conv - cons)"),
     ("transport: viscous term of u_j", PY, "visc = deriv_lines(ui, 2, bc, h)", "visc = deriv_lines(uj, 2, bc, h)"),
     ("y lines taken in z-major order", PY,

@@ -507,7 +507,7 @@ def test_interp_transfer_function_and_dense_lu(oracle_mod, n):
                                rtol=0, atol=1e-14)
 
 
-def test_interp_sixth_order_and_closed_lines_refused(oracle_mod):
+def test_interp_sixth_order_and_filter_parameter_refused(oracle_mod):
     errs = []
     for n in (32, 64, 128):
         h = 2 * np.pi / n
@@ -518,6 +518,59 @@ def test_interp_sixth_order_and_closed_lines_refused(oracle_mod):
     for e0, e1 in zip(errs, errs[1:]):
         assert 5.7 < math.log2(e0 / e1) < 6.3, errs
     with pytest.raises(ValueError):
-        oracle_mod.bands(16, oracle_mod.INTERP, "closed", 1.0)
-    with pytest.raises(ValueError):
         oracle_mod.bands(16, oracle_mod.FILTER, "periodic", 0.5)
+
+
+# Closed lines: n nodes give n - 1 mid-points.  The closure rows (the first mid-point and its
+# mirror) are pinned by their defining conditions -- exact at their mid-point for polynomials
+# through degree 4 and not degree 5 -- on the oracle's own band rows in rational arithmetic;
+# the last row is a zero row; the solved operator is pinned by dense LU and by its order of
+# convergence on a smooth non-periodic function.
+@pytest.mark.parametrize("row", [0, -2, 1, -3])
+def test_interp_closed_rows_exact_to_their_degree(oracle_mod, row):
+    n = 16
+    a, b, c, B7 = oracle_mod.bands(n, oracle_mod.INTERP, "closed", 1.0)
+    i = row % n
+    half = Fraction(1, 2)
+
+    def residual(p):
+        def f(x): return x ** p if p > 0 else Fraction(1)
+        x0 = Fraction(i)   # g[j] sits at x_j + 1/2, f[j] at x_j (units of h)
+        lhs = Fraction(b[i]) * f(x0 + half)
+        if i > 0: lhs += Fraction(a[i]) * f(x0 - 1 + half)
+        if i < n - 1: lhs += Fraction(c[i]) * f(x0 + 1 + half)
+        rhs = sum(Fraction(B7[i, t]) * f(x0 + t - 3) for t in range(7) if B7[i, t] != 0.0)
+        return lhs - rhs
+    deg = 4 if row in (0, -2) else 5    # closures through degree 4, interior rows through 5
+    for p in range(deg + 1):
+        assert abs(float(residual(p))) <= 1e-15 * 16.0 ** p, (row, p)
+    assert abs(float(residual(deg + 1))) > 1e-3, row
+
+
+def test_interp_closed_zero_row_dense_lu_and_fifth_order(oracle_mod):
+    for n in (16, 33):
+        a, b, c, B7 = oracle_mod.bands(n, oracle_mod.INTERP, "closed", 1.0)
+        assert a[n - 1] == 0 and c[n - 1] == 0 and c[n - 2] == 0 and b[n - 1] == 1
+        assert not np.any(B7[n - 1])
+        rng = np.random.default_rng(n)
+        A, B = dense(oracle_mod, n, oracle_mod.INTERP, "closed", 1.0)
+        f = rng.uniform(-1, 1, (3, n))
+        got = oracle_mod.interp_lines(f, "closed")
+        np.testing.assert_allclose(got, np.linalg.solve(A, B @ f.T).T, rtol=0, atol=1e-14)
+        assert not np.any(got[:, -1])
+        back = oracle_mod.interp_adjoint_lines(f, "closed")
+        np.testing.assert_allclose(back, (B.T @ np.linalg.solve(A.T, f.T)).T, rtol=0, atol=1e-14)
+        f2 = f.copy()
+        f2[:, -1] = 7.0   # the last slot is no mid-point: the transpose does not read it
+        np.testing.assert_array_equal(oracle_mod.interp_adjoint_lines(f2, "closed"), back)
+    # order of convergence: the closures (exact through degree 4) make it five near the ends
+    errs = []
+    for n in (33, 65, 129, 257):
+        x = np.linspace(0.0, 2 * np.pi, n)
+        h = x[1] - x[0]
+        f = np.sin(x) + 0.5 * np.cos(2 * x + 0.3)
+        xm = x[:-1] + h / 2
+        ex = np.sin(xm) + 0.5 * np.cos(2 * xm + 0.3)
+        errs.append(np.max(np.abs(oracle_mod.interp_lines(f[None, :], "closed")[0, :-1] - ex)))
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 4.8 < math.log2(e0 / e1) < 5.8, errs
