@@ -76,11 +76,14 @@ void configure_pipe(tds_plan *p);
 // SM.  FP32 sweeps (bound by HBM) and split-precision FP64 sweeps (bound by the issue rate of the
 // FP32 pipes): the largest such width (fewest per-CTA overheads, the longest contiguous copies;
 // measured for the split FP64 fused pass at 512^3: 16 lines 3.28 ms, 8 lines 4.21 ms).  Native
-// FP64 sweeps are bound by the FP64 pipe: the smallest (most CTAs per SM keep the pipe busy
-// through each CTA's copy and reduced-system phases).  Else 32 if a whole group fits at all.
+// FP64 sweeps are bound by the FP64 pipe: on periodic lines the smallest (most CTAs per SM keep
+// the pipe busy through each CTA's copy and reduced-system phases); on closed lines the largest
+// too, so that the first and last chunks' closure rows do not run on a few lanes of a warp
+// whose other lanes wait (measured at 512^3, P = 8, D1 / D2: 8 lines 2.197 / 2.179 ms, 16 lines
+// 2.099 / 2.158, 32 lines 2.082 / 2.168).  Else 32 if a whole group fits at all.
 void pick_width(tds_plan *p) {
     p->width = 0;
-    if (p->dtype == TDS_F64 && !p->split) {
+    if (p->dtype == TDS_F64 && !p->split && p->bc == TDS_BC_PERIODIC) {
         for (int w = 8; w <= kSZ; w *= 2)
             if (resident_width_ok(p, w, true)) { p->width = w; break; }
     } else {

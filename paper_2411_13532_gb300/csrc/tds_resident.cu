@@ -1126,9 +1126,9 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident(const __grid_co
     if (MODE == 0) {
         if (k > 0 || op.periodic) ok = mbar_wait(&bars[(k - 1 + P) % P], 0) && ok;
         if (k < P - 1 || op.periodic) ok = mbar_wait(&bars[(k + 1) % P], 0) && ok;
-        // the closure rows of a closed line may reach into the second / second-to-last chunk
-        if (!op.periodic && (k == 0 || k == P - 1))
-            for (int q = 0; q < P; ++q) ok = mbar_wait(&bars[q], 0) && ok;
+        // the closure rows of a closed line reach 3 rows in (rows 0..6 and n-7..n-1, copied to
+        // the scratch rows by the first and last chunks' threads): with m >= 4 they lie in the
+        // chunk and its neighbour, so the first and last chunks start as soon as those two land
     }
     if (!ok) atomicExch(&failed, 1);
     int unsafe = 0;
@@ -1212,8 +1212,6 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_multi(const __g
         bool ok = mbar_wait(&bars[k], par);
         if (k > 0 || op.periodic) ok = mbar_wait(&bars[(k - 1 + P) % P], par) && ok;
         if (k < P - 1 || op.periodic) ok = mbar_wait(&bars[(k + 1) % P], par) && ok;
-        if (!op.periodic && (k == 0 || k == P - 1))
-            for (int q = 0; q < P; ++q) ok = mbar_wait(&bars[q], par) && ok;
         if (!ok) atomicExch(&failed, 1);
         int unsafe = 0;
         Pack<typename Tr::A, 1> hb[2], ha[2];
@@ -1306,8 +1304,6 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_ilv(const __gri
     bool ok = mbar_wait(&bars[k], 0);
     if (k > 0 || op.periodic) ok = mbar_wait(&bars[(k - 1 + P) % P], 0) && ok;
     if (k < P - 1 || op.periodic) ok = mbar_wait(&bars[(k + 1) % P], 0) && ok;
-    if (!op.periodic && (k == 0 || k == P - 1))
-        for (int q = 0; q < P; ++q) ok = mbar_wait(&bars[q], 0) && ok;
     if (!ok) atomicExch(&failed, 1);
     int unsafe = 0;
     Pack<typename Tr::A, 1> hb[2], ha[2];
