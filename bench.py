@@ -92,7 +92,49 @@ def parse():
                     help="the single-rank sweep over the line length n = 32..8192 (one JSON line per "
                          "case): first derivative along x, 2^30 points, P = 1 and 8, FP64 and FP32, "
                          "against a device copy of the same bytes")
+    ap.add_argument("--one", action="store_true",
+                    help="a small fixed launch sequence for profiler captures: on a --size^3 Fourier field "
+                         "along x (periodic, --P chunks), --reps launches of the first derivative, then "
+                         "--reps of the second, in --dtype with --arith; prints one JSON line of timings")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--width", type=int, default=0, help="with --one: lines per resident CTA (0: the plan's)")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--arith", default="native", choices=["native", "split"])
     return ap.parse_args()
+
+
+def run_one(args):
+    """--one: the launch sequence a profiler capture selects from (-s / -c)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_13532_gb300 as tds
+    from paper_2411_13532_gb300 import inputs
+    S = args.size
+    shape = (S, S, S)
+    dt = torch.float64 if args.dtype == "f64" else torch.float32
+    f, _ = inputs.fourier_field(shape, seed=2, kmax=100, noise=0.1, noise_kind="normal", device="cuda")
+    x = tds.reorder(f.to(dt).reshape(-1), shape, "cart", "x")
+    del f
+    y = torch.empty_like(x)
+    out = {"mode": "one", "size": S, "P": args.P, "dtype": args.dtype, "arith": args.arith}
+    for order in (1, 2):
+        p = tds.Plan(shape, "x", order, "periodic", P=args.P, dtype=dt, width=args.width or None,
+                     arith=args.arith if args.dtype == "f64" else "native")
+        ms = []
+        for _ in range(args.reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            p.deriv(x, y)
+            b.record()
+            b.synchronize()
+            ms.append(round(a.elapsed_time(b), 4))
+        out["D%d_ms" % order] = ms
+        out["D%d_width" % order] = p.width
+    if tds.device_status() != 0:
+        raise RuntimeError("device status after --one")
+    print(json.dumps(out))
 
 
 def load_peaks():
@@ -1085,6 +1127,9 @@ def main():
         return
     if args.thomas:
         run_thomas(args)
+        return
+    if args.one:
+        run_one(args)
         return
     if world > 1:
         import torch

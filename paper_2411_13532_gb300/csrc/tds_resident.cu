@@ -507,7 +507,8 @@ __device__ __forceinline__ void fwd_span(const DevOp &op, int cls, typename Tr::
 //   antisymmetric taps: c1 (v[j+1] - v[j-1]) + c2 (v[j+2] - v[j-2]), with b_j = v[j+1] - v[j-1]
 //       split once per row and v[j+2] - v[j-2] = b_{j+1} + b_{j-1};
 //   symmetric taps: c0 v[j] + c1 e_j + c2 (e_{j+1} + e_{j-1}), e_j = (v[j+1] - v[j]) - (v[j] -
-//       v[j-1]) split once per row (c0 = f tapsum: zero for a second derivative).
+//       v[j-1]): the first difference v[j+2] - v[j+1] taken in FP64 and split once per row, e
+//       formed in pairs (c0 = f tapsum: zero for a second derivative).
 // w[0..3] carry v[jb-2 .. jb+1] as FP64 bits; v[j+2] comes from the tile ahead of the sweep, then
 // from the halo `ha` (the next chunk's first two rows).
 template <typename Tr, int FORM>
@@ -519,16 +520,16 @@ __device__ __forceinline__ void sweep_interior_df(const DevOp &op, int cls, doub
     const int jm = (je < m - 2) ? je : m - 2;
     const double v0 = df_unraw(w[0].v[0]), v1 = df_unraw(w[1].v[0]);
     double v2 = df_unraw(w[2].v[0]), v3 = df_unraw(w[3].v[0]);
-    double a2 = 0.0;   // symmetric: v[j+1] - v[j]
-    DF p, c;           // antisymmetric: b_{j-1}, b_j; symmetric: e_{j-1}, e_j
+    DF p, c;   // antisymmetric: b_{j-1}, b_j; symmetric: e_{j-1}, e_j
+    DF A2;     // symmetric: v[j+1] - v[j], split
     if (FORM == kAnti) {
         p = df_split(v2 - v0);
         c = df_split(v3 - v1);
     } else {
-        const double a0 = v1 - v0, a1 = v2 - v1;
-        a2 = v3 - v2;
+        const double a0 = v1 - v0, a1 = v2 - v1, a2 = v3 - v2;
         p = df_split(a1 - a0);
         c = df_split(a2 - a1);
+        A2 = df_split(a2);
     }
     const bool c0 = (FORM == kSym) && op.tapsum != 0.0;
     DF d = dprev.v[0], Sa = S.v[0];
@@ -544,9 +545,11 @@ __device__ __forceinline__ void sweep_interior_df(const DevOp &op, int cls, doub
         if (FORM == kAnti) {
             nx = df_split(v4 - v2);
         } else {
-            const double a3 = v4 - v3;
-            nx = df_split(a3 - a2);
-            a2 = a3;
+            // e_{j+1} = a_{j+1} - a_j with the first differences split (one FP64 operation per row;
+            // measured 10 % faster for the second derivative than taking e in FP64 too)
+            const DF A3 = df_split(v4 - v3);
+            nx = A3 - A2;
+            A2 = A3;
         }
         DF dn = dot3(q1, c, q2, nx + p, -qg, d);
         if (c0) dn = mad(q0, df_split(v2), dn);
