@@ -94,12 +94,16 @@ def parse():
                          "against a device copy of the same bytes")
     ap.add_argument("--one", action="store_true",
                     help="a small fixed launch sequence for profiler captures: on a --size^3 Fourier field "
-                         "along x (periodic, --P chunks), --reps launches of the first derivative, then "
-                         "--reps of the second, in --dtype with --arith; prints one JSON line of timings")
+                         "along x (--bc lines, --P chunks), --reps launches of the first derivative (or its "
+                         "transpose, --adjoint), then --reps of the second, in --dtype with --arith; prints "
+                         "one JSON line of timings")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--bc", default="periodic", choices=["periodic", "closed"], help="with --one: the lines' ends")
+    ap.add_argument("--adjoint", action="store_true", help="with --one: the transposed operators")
     ap.add_argument("--width", type=int, default=0, help="with --one: lines per resident CTA (0: the plan's)")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
-    ap.add_argument("--arith", default="native", choices=["native", "split"])
+    ap.add_argument("--arith", default="native", choices=["native", "split"],
+                    help="with --one or --sweep: the arithmetic of FP64 plans (tds_plan_set_arith)")
     return ap.parse_args()
 
 
@@ -117,16 +121,18 @@ def run_one(args):
     x = tds.reorder(f.to(dt).reshape(-1), shape, "cart", "x")
     del f
     y = torch.empty_like(x)
-    out = {"mode": "one", "size": S, "P": args.P, "dtype": args.dtype, "arith": args.arith}
+    out = {"mode": "one", "size": S, "P": args.P, "dtype": args.dtype, "arith": args.arith, "bc": args.bc,
+           "adjoint": args.adjoint}
     for order in (1, 2):
-        p = tds.Plan(shape, "x", order, "periodic", P=args.P, dtype=dt, width=args.width or None,
+        p = tds.Plan(shape, "x", order, args.bc, P=args.P, dtype=dt, width=args.width or None,
                      arith=args.arith if args.dtype == "f64" else "native")
+        call = p.adjoint if args.adjoint else p.deriv
         ms = []
         for _ in range(args.reps):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record()
-            p.deriv(x, y)
+            call(x, y)
             b.record()
             b.synchronize()
             ms.append(round(a.elapsed_time(b), 4))
@@ -646,7 +652,8 @@ def run_sweep(args):
                                                 band=inputs.diffusion_band(n, seed=1))
                             else:
                                 plan = tds.Plan(shape, direc, order, bc, P=P, dtype=dt,
-                                                alpha_f=0.45 if order == "filter" else None)
+                                                alpha_f=0.45 if order == "filter" else None,
+                                                arith=args.arith if dname == "f64" else "native")
                             ws = plan.workspace()
                             fn = {"adjoint": lambda: plan.adjoint(x, y, ws), "solve": lambda: plan.solve(x, y, ws),
                                   "band": lambda: plan.solve(x, y, ws), "deriv": lambda: plan.deriv(x, y, ws)}[kind]
@@ -670,6 +677,7 @@ def run_sweep(args):
                                 "op": (order if isinstance(order, str) else
                                        {"adjoint": "D%dT", "solve": "A%d^-1", "deriv": "D%d"}[kind] % order),
                                 "dir": direc, "bc": bc, "P": P, "variant": plan.variant, "width": plan.width,
+                                "arith": plan.arith,
                                 "ms": round(ms, 4), "gpoints_s": round(npts / (ms * 1e-3) / 1e9, 2),
                                 "alg_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
                                 "hbm_frac_nominal_7900": round(gbs / 7900.0, 4), "peak_source": peak_kind,

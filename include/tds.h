@@ -192,11 +192,13 @@ TDS_API tds_status tds_plan_set_width(tds_plan *plan, int lines);
  * differences lose low-word bits, larger ones overflow.  Applies to tds_deriv, the host entry
  * points, tds_deriv_multi (one launch per operator: these sweeps are bound by their own issue
  * rate, not by HBM reads, so the fused pass gains nothing) and tds_transport when they run the
- * RESIDENT variant on a forward-form operator with antisymmetric or symmetric interior taps
- * (first and second derivatives, the adjoint on periodic lines, the filter); every other call
- * and operator runs native FP64.  The plan's CTA width follows the arithmetic (split sweeps, bound by the FP32
- * issue rate, take the widest CTA that lets two share an SM, as FP32 plans do) and the variant
- * is chosen again (AUTO): call this before tds_plan_set_width and tds_plan_set_variant.
+ * RESIDENT variant on a forward-form operator (the stencil right-hand side: first and second
+ * derivatives and their adjoints on periodic lines, the filter, the mid-point interpolation and
+ * its transpose on periodic lines); the closed-line adjoints, tds_solve and every other variant
+ * run native FP64.  The plan's CTA width follows the arithmetic its forward operator runs
+ * (split sweeps, bound by the FP32 issue rate, take the widest CTA that lets two share an SM, as
+ * FP32 plans do) and the variant is chosen again (AUTO): call this before tds_plan_set_width
+ * and tds_plan_set_variant.
  * TDS_ERR_ARG for an FP32 plan, a band plan or an unknown value. */
 TDS_API tds_status tds_plan_set_arith(tds_plan *plan, tds_arith arith);
 

@@ -14,8 +14,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libtds.so")
-SOURCES = ["tds_plan.cu", "tds_resident.cu", "tds_streaming.cu", "tds_thomas.cu", "tds_reorder.cu",
-           "tds_api.cu", "tds_noalloc.cu"]
+SOURCES = ["tds_fam_f32c.cu", "tds_fam_f32.cu", "tds_fam_f64.cu", "tds_fam_split.cu", "tds_resident.cu",
+           "tds_plan.cu", "tds_streaming.cu", "tds_thomas.cu", "tds_reorder.cu", "tds_api.cu", "tds_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

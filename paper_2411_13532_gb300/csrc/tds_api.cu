@@ -80,10 +80,12 @@ void configure_pipe(tds_plan *p);
 // the pipe busy through each CTA's copy and reduced-system phases); on closed lines the largest
 // too, so that the first and last chunks' closure rows do not run on a few lanes of a warp
 // whose other lanes wait (measured at 512^3, P = 8, D1 / D2: 8 lines 2.197 / 2.179 ms, 16 lines
-// 2.099 / 2.158, 32 lines 2.082 / 2.168).  Else 32 if a whole group fits at all.
+// 2.099 / 2.158, 32 lines 2.082 / 2.168).  Else 32 if a whole group fits at all.  The rule follows
+// the sweep the plan's operator actually runs: a split-precision plan whose operator has no split
+// sweep runs native and takes the native rule.
 void pick_width(tds_plan *p) {
     p->width = 0;
-    if (p->dtype == TDS_F64 && !p->split && p->bc == TDS_BC_PERIODIC) {
+    if (p->dtype == TDS_F64 && !runs_split(p, 0) && p->bc == TDS_BC_PERIODIC) {
         for (int w = 8; w <= kSZ; w *= 2)
             if (resident_width_ok(p, w, true)) { p->width = w; break; }
     } else {

@@ -53,6 +53,8 @@ struct DevOp {
                     // FP64 sweeps ignore it
     int ncls;       // chunk classes (first / interior / last differ on closed lines)
     int cls_first, cls_mid, cls_last;
+    int bt_fold;    // closed-line adjoint (adjoint 1) with m >= 16: x = B^T y formed inside the
+                    // back-substitution (FP32 plans; TDS_ADJOINT_FOLD = 0 / 1 forces either form)
     int cls_each;   // 1: every chunk is its own class (ncls = P; a band whose chunks differ), and
                     // the per-class scalars below hold one entry (index 0) valid for all chunks
     const double *row64;  // [kNumRowArrays][ncls*m]
@@ -201,6 +203,9 @@ tds_status launch_reorder_add(const void *in, void *out, int nx, int ny, int nz,
 // out[o] = in for o < count (<= kMaxMulti), bytes a multiple of 16 (tds_fanout_copy).
 tds_status launch_fanout(const void *in, void *const *outs, int count, size_t bytes, int nsm, cudaStream_t st);
 tds_status read_device_status();
+// Whether operator `which` of an FP64 plan runs the split-precision sweep (the plan asks for it
+// and the operator has a split form).
+bool runs_split(const tds_plan *p, int which);
 tds_status launch_selftest_wait(double seconds, cudaStream_t st);
 
 } // namespace tds

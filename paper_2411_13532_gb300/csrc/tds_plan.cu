@@ -217,6 +217,14 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
     op.n = n; op.m = m; op.P = P; op.nlines = p->nlines; op.ngroups = p->nlines / kSZ;
     const bool fwd_form = (which == 0) || (which == 1 && periodic);
     op.periodic = periodic; op.adjoint = fwd_form ? 0 : which;
+    if (op.adjoint == 1 && m >= 16) {
+        // FP32 sweeps fold x = B^T y into the back-substitution (measured at 512^3, P = 8, D1^T /
+        // D2^T: 0.249 / 0.265 -> 0.235 / 0.262 ms); FP64 sweeps, bound by the FP64 pipe, keep the
+        // separate pass (folded 2.38 / 2.53 -> 2.47 / 2.70 ms).  TDS_ADJOINT_FOLD = 0 / 1 forces
+        // either form (tuning).
+        const char *e = std::getenv("TDS_ADJOINT_FOLD");
+        op.bt_fold = (e && (e[0] == '0' || e[0] == '1')) ? (e[0] == '1') : (p->dtype == TDS_F32);
+    }
     // interior stencil form: the interpolation's transpose pairs its taps about -1/2; the
     // second derivative's taps (vanishing sum) may be applied to second differences
     op.symmetric = (p->order == 1) ? -1 : (p->order == 4) ? (which == 1 ? 3 : 2) : (p->order == 2 ? 4 : 1);

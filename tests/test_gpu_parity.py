@@ -766,3 +766,32 @@ def test_fp32_closed_smooth_every_variant(variant, order, adjoint):
     report("closed smooth D%d%s f32" % (order, "T" if adjoint else ""), variant=plan.variant, max_rel=mx,
            rms_rel=rms)
     assert mx <= TOL["f32"], (mx, rms)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("kind", [1, 2, "interp"])
+@pytest.mark.parametrize("fold", ["0", "1"])
+def test_closed_adjoint_fold_forms(dtype, kind, fold, monkeypatch):
+    """The closed-line adjoint with x = B^T y folded into the back-substitution (chunks of at least
+    16 rows; FP32 plans by default) and as a separate pass, both forced through TDS_ADJOINT_FOLD
+    (read at plan creation): every point against the oracle, for chunks of 16 to 128 rows in the
+    first, interior and last positions (P = 1 has the line's closures at both ends of one chunk)."""
+    monkeypatch.setenv("TDS_ADJOINT_FOLD", fold)
+    shape = (4, 32, 128)
+    cart = np.random.default_rng(41).uniform(-1, 1, shape)
+    if dtype == "f32":
+        cart = cart.astype(np.float32).astype(np.float64)
+    if kind == "interp":
+        ref = oracle.apply_op(cart, "x", oracle.INTERP, "closed", adjoint=True)
+    else:
+        h = oracle.grid_spacing(128, "closed")
+        ref = oracle.deriv_adjoint(cart, "x", kind, "closed", h)
+    x = to_device_layout(cart, "x", dtype)
+    for P in (1, 2, 4, 8):
+        for variant in ("resident", "pipelined"):
+            if kind == "interp":
+                plan = tds.Plan(shape, "x", "interp", "closed", P=P, dtype=TORCH[dtype], variant=variant)
+            else:
+                plan = tds.Plan(shape, "x", kind, "closed", P=P, h=h, dtype=TORCH[dtype], variant=variant)
+            mx, rms = rel_errors(from_device_layout(plan.adjoint(x), "x", shape), ref)
+            assert mx <= TOL[dtype], (P, variant, mx, rms)

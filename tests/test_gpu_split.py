@@ -72,6 +72,38 @@ def test_split_filter_every_point(bc):
         assert mx <= TOL["f64"], (P, mx, rms)
 
 
+@pytest.mark.parametrize("direction", ["x", "y", "z"])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_split_interp_every_point(direction, bc, adjoint):
+    """The mid-point interpolation (half-point taps) and its transpose; the split sweep runs the
+    forward operator and, on periodic lines, the transpose (closed lines: native FP64)."""
+    shape = (12, 40, 32)
+    cart = np.random.default_rng(31).uniform(-1, 1, shape)
+    ref = oracle.apply_op(cart, direction, oracle.INTERP, bc, adjoint=adjoint)
+    x = to_device_layout(cart, direction, "f64")
+    for P in {"x": (1, 2, 8), "y": (1, 2, 5), "z": (1, 3)}[direction]:
+        plan = tds.Plan(shape, direction, "interp", bc, P=P, variant="resident", arith="split")
+        native = tds.Plan(shape, direction, "interp", bc, P=P, variant="resident")
+        y = plan.adjoint(x) if adjoint else plan.deriv(x)
+        mx, rms = rel_errors(from_device_layout(y, direction, shape), ref)
+        assert mx <= TOL["f64"], (P, mx, rms)
+        yn = native.adjoint(x) if adjoint else native.deriv(x)
+        if not adjoint or bc == "periodic":
+            assert not torch.equal(y, yn)    # a different arithmetic ran
+        else:
+            assert torch.equal(y, yn)
+
+
+def test_split_interp_width_rule():
+    """A split interpolation plan takes the split width rule now that its operator runs split."""
+    shape = (32, 48, 512)
+    for bc in ("periodic", "closed"):
+        sp = tds.Plan(shape, "x", "interp", bc, P=8, arith="split")
+        d1 = tds.Plan(shape, "x", 1, bc, P=8, arith="split")
+        assert sp.width == d1.width
+
+
 @pytest.mark.parametrize("bc", ["periodic", "closed"])
 def test_split_fused_pass(bc):
     """tds_deriv_multi with split plans (one launch per operator): bitwise the single split
