@@ -106,6 +106,8 @@ struct DevOp {
     double tap[kTaps];                 // interior stencil taps, offsets -3..3
     double tapsum;                     // symmetric taps: t0 + 2 t1 + 2 t2 (0 for a second derivative)
     double edge[2 * kEdgeRows][kTaps]; // closed lines: rows 0..3 then n-4..n-1
+    float edge_pf[2 * kEdgeRows][kTaps][2]; // the same taps as float pairs (hi, lo): FP32 sweeps
+                                            // evaluate closure rows with e64 in pair arithmetic
     // How each edge row is evaluated: 0 as the taps; 1 from first differences v[J+o] - v[J] (taps
     // summing to 0: rows of a first derivative); 2 from second differences with the weights
     // edge_dd (taps with vanishing sum and first moment: rows of a second derivative).  On

@@ -289,6 +289,12 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
                 op.edge[e][o] = L.taps[(size_t)e * kTaps + o];
                 op.edge[kEdgeRows + e][o] = L.taps[(size_t)(n - kEdgeRows + e) * kTaps + o];
             }
+        for (int e = 0; e < 2 * kEdgeRows; ++e)
+            for (int o = 0; o < kTaps; ++o) {
+                const float hi = (float)op.edge[e][o];
+                op.edge_pf[e][o][0] = hi;
+                op.edge_pf[e][o][1] = (float)(op.edge[e][o] - (double)hi);
+            }
     }
     // the form each edge row is evaluated in (DevOp::edge_form): moments of its taps
     for (int e = 0; e < 2 * kEdgeRows; ++e) {

@@ -439,6 +439,72 @@ __device__ __forceinline__ void close_rows64(const DevOp &op, int cls, int j0, b
     for (int q = 0; q < V; ++q) dprev.v[q] = static_cast<typename Tr::A>(d[q]);
 }
 
+// FP32 sweeps of closed lines with e64 take the closure rows in float-pair arithmetic (about 48
+// bits) on the FP32 pipes: the FP64 pipe issues at 1/64 of the FP32 rate on GB300, and in FP64
+// these rows put some 70 dependent FP64 warp instructions on the first and last chunks' critical
+// path; pairs leave their rounding, magnified about 100 times by the closure, far below the FP32
+// bar.  The FP32 inputs are exact in a pair; the quantities handed to the FP64 reduced system
+// are joined to FP64 by integer operations (df_join).
+
+// sum_o c_o x_o over the taps of closure row e, c_o as float pairs (DevOp::edge_pf)
+__device__ __forceinline__ DF edge_dot_pf(const DevOp &op, int e, const float (&x)[kTaps]) {
+    float sh = 0.0f, se = 0.0f;
+#pragma unroll
+    for (int o = 0; o < kTaps; ++o) {
+        const float ch = op.edge_pf[e][o][0], cl = op.edge_pf[e][o][1];
+        const float p = __fmul_rn(ch, x[o]);
+        float err = __fmaf_rn(ch, x[o], -p);
+        err = __fmaf_rn(cl, x[o], err);
+        const DF t = df_two(sh, p);
+        sh = t.h;
+        se = __fadd_rn(se, __fadd_rn(t.l, err));
+    }
+    return df_two(sh, se);
+}
+
+// One closure row in pairs: d = f (s - r d), Sx += pi d (the pair records), d -> tile as FP32.
+template <typename Tr, int V>
+__device__ __forceinline__ void fwd_row_pf(const DevOp &op, int cls, int j, typename Tr::S *row,
+                                           const DF (&sv)[V], DF (&d)[V], DF (&Sx)[V]) {
+    const float4 *q = reinterpret_cast<const float4 *>(op.fwdd) + 2 * ((size_t)cls * op.m + j);
+    const float4 a = __ldg(q);
+    const float2 b = __ldg(reinterpret_cast<const float2 *>(q + 1));
+    const DF f = df_make(a.x, a.y), r = df_make(a.z, a.w), pi = df_make(b.x, b.y);
+    Pack<typename Tr::A, V> x;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        d[i] = f * (sv[i] - r * d[i]);
+        Sx[i] = mad(pi, d[i], Sx[i]);
+        x.v[i] = __fadd_rn(d[i].h, d[i].l);
+    }
+    Tr::template st_mid<V>(row + (size_t)j * Tr::W, x);
+}
+
+// After pair rows [j0, j0 + 4) of a chunk: as close_rows64.
+template <typename Tr, int V>
+__device__ __forceinline__ void close_rows_pf(const DevOp &op, int cls, int j0, bool head, const DF (&d)[V],
+                                              const DF (&Sx)[V], const DF (&d0)[V],
+                                              Pack<typename Tr::A, V> &dprev, Pack<typename Tr::A, V> &S,
+                                              Ends64<V> &ex) {
+    if (head) {
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(op.bwdd) + (size_t)cls * op.m);
+        const DF w0 = df_make(b.z, b.w);   // c_0 / b_0
+#pragma unroll
+        for (int i = 0; i < V; ++i) ex.x0[i] = df_join(d0[i] - w0 * Sx[i]);
+        ex.first = true;
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) S.v[i] += __fadd_rn(Sx[i].h, Sx[i].l);
+    }
+    if (j0 + 4 == op.m) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) ex.xl[i] = df_join(d[i]);
+        ex.last = true;
+    }
+#pragma unroll
+    for (int i = 0; i < V; ++i) dprev.v[i] = __fadd_rn(d[i].h, d[i].l);
+}
+
 // Interior row of the forward pass with f folded into the coefficients:
 // d_j = (the FORM's stencil with taps c0, c1, c2) - g d_{j-1}, one FMA on the recurrence;
 // ACC: S += pi_j d_j (rows past the plan's cut-off skip it).
@@ -717,9 +783,8 @@ __device__ __forceinline__ void sweep_edge(const DevOp &op, int cls, typename Tr
     }
     if constexpr (FWD && Tr::kE64 && !Tr::kDF) {
         if (op.e64) {
-            // the ten input rows the four windows cover, converted once; two partial sums per
-            // row halve the dependent chain
-            double xw[kTaps + 3][V];
+            // the ten input rows the four windows cover, then the four rows in pairs
+            float xw[kTaps + 3][V];
 #pragma unroll
             for (int o = 0; o < kTaps + 3; ++o) {
                 const int x = o + xlo;
@@ -727,32 +792,32 @@ __device__ __forceinline__ void sweep_edge(const DevOp &op, int cls, typename Tr
                 const Pack<A, V> v = (x >= 0 && x < xhi) ? Tr::template ld_in<V>(op, xs + (size_t)x * Tr::W + c, dummy)
                                                          : zero_a<Tr, V>();
 #pragma unroll
-                for (int q = 0; q < V; ++q) xw[o][q] = (double)v.v[q];
+                for (int q = 0; q < V; ++q) xw[o][q] = (float)v.v[q];
             }
-            double d[V], Sx[V], d0[V];
+            DF d[V], Sx[V], d0[V];
 #pragma unroll
-            for (int q = 0; q < V; ++q) { d[q] = head ? 0.0 : (double)dprev.v[q]; Sx[q] = 0.0; d0[q] = 0.0; }
+            for (int q = 0; q < V; ++q) {
+                d[q] = df_make(head ? 0.0f : (float)dprev.v[q], 0.0f);
+                Sx[q] = df_make(0.0f, 0.0f);
+                d0[q] = Sx[q];
+            }
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                const double *cf = op.edge[e0 + t];
-                double sv[V];
+                DF sv[V];
 #pragma unroll
                 for (int q = 0; q < V; ++q) {
-                    double s0 = cf[0] * xw[t][q], s1 = cf[1] * xw[t + 1][q];
+                    float xv[kTaps];
 #pragma unroll
-                    for (int o = 2; o < kTaps; o += 2) {
-                        s0 = ::fma(cf[o], xw[t + o][q], s0);
-                        if (o + 1 < kTaps) s1 = ::fma(cf[o + 1], xw[t + o + 1][q], s1);
-                    }
-                    sv[q] = s0 + s1;
+                    for (int o = 0; o < kTaps; ++o) xv[o] = xw[t + o][q];
+                    sv[q] = edge_dot_pf(op, e0 + t, xv);
                 }
-                fwd_row64<Tr, V>(op, cls, j0 + t, row, sv, d, Sx);
+                fwd_row_pf<Tr, V>(op, cls, j0 + t, row, sv, d, Sx);
                 if (t == 0) {
 #pragma unroll
                     for (int q = 0; q < V; ++q) d0[q] = d[q];
                 }
             }
-            close_rows64<Tr, V>(op, cls, j0, head, d, Sx, d0, dprev, S, ex);
+            close_rows_pf<Tr, V>(op, cls, j0, head, d, Sx, d0, dprev, S, ex);
             done = true;
         }
     }
@@ -841,7 +906,7 @@ __device__ __forceinline__ void forward_phase(const DevOp &op, typename Tr::S *r
     using A = typename Tr::A;
     const int m = op.m;
     ex.first = ex.last = false;
-    if (!ADJ) {
+    if constexpr (!ADJ) {
         stencil_sweep<Tr, V, true>(op, K, cls, row, xs, c, hb, ha, dprev, Ssum, ex, unsafe);
     } else {
         // identity right-hand side: d_j = f_j g_j - (f_j r_j) d_{j-1}
@@ -872,24 +937,29 @@ __device__ __forceinline__ void forward_phase(const DevOp &op, typename Tr::S *r
 #pragma unroll 4
             for (int j = y; j < b; ++j) arow(j, acc, false);
         };
-        // FP32 sweeps of closed lines: the four rows at each end of the line in FP64 (Ends64)
+        // FP32 sweeps of closed lines: the four rows at each end of the line in float pairs
+        // (Ends64; the FP32 right-hand side is exact in a pair)
         auto rows64 = [&](int j0, bool head) {
-            double d[V], Sx[V], d0[V];
+            DF d[V], Sx[V], d0[V];
 #pragma unroll
-            for (int i = 0; i < V; ++i) { d[i] = head ? 0.0 : (double)dprev.v[i]; Sx[i] = 0.0; d0[i] = 0.0; }
+            for (int i = 0; i < V; ++i) {
+                d[i] = df_make(head ? 0.0f : (float)dprev.v[i], 0.0f);
+                Sx[i] = df_make(0.0f, 0.0f);
+                d0[i] = Sx[i];
+            }
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const Pack<A, V> g = Tr::template ld_in<V>(op, row + (size_t)(j0 + t) * Tr::W, unsafe);
-                double sv[V];
+                DF sv[V];
 #pragma unroll
-                for (int i = 0; i < V; ++i) sv[i] = (double)g.v[i];
-                fwd_row64<Tr, V>(op, cls, j0 + t, row, sv, d, Sx);
+                for (int i = 0; i < V; ++i) sv[i] = df_make((float)g.v[i], 0.0f);
+                fwd_row_pf<Tr, V>(op, cls, j0 + t, row, sv, d, Sx);
                 if (t == 0) {
 #pragma unroll
                     for (int i = 0; i < V; ++i) d0[i] = d[i];
                 }
             }
-            close_rows64<Tr, V>(op, cls, j0, head, d, Sx, d0, dprev, Ssum, ex);
+            close_rows_pf<Tr, V>(op, cls, j0, head, d, Sx, d0, dprev, Ssum, ex);
         };
         const bool e64 = Tr::kE64 && op.e64;
         const bool head = e64 && K == 0, tail = e64 && K == op.P - 1;
