@@ -255,6 +255,36 @@ __device__ __forceinline__ Pack<typename Tr::A, V> zero_a() {
     return r;
 }
 
+// Row bounds that cut a sweep into loops (the pi and s^a cut-offs, the constant-record runs)
+// belong to the chunk's class.  A warp that holds chunks of several classes (CTAs of 8 or 16
+// lines on closed lines: the first and last chunks share warps with interior ones) would run
+// every loop to the latest lane's bound, one class's segment after another; the warp takes
+// common bounds instead: the latest cut-off (rows past a lane's own cut-off add terms below its
+// threshold) and the common part of the constant runs (a lane's per-row records equal its
+// class constant there).  Any subset of lanes gives valid bounds, so the mask is the converged
+// lanes'.
+__device__ __forceinline__ int warp_max_i(int x) { return __reduce_max_sync(__activemask(), x); }
+__device__ __forceinline__ int warp_min_i(int x) { return __reduce_min_sync(__activemask(), x); }
+
+template <typename Tr>
+__device__ __forceinline__ int warp_jpi(const DevOp &op, int cls) { return warp_max_i(Tr::jpi(op, cls)); }
+template <typename Tr>
+__device__ __forceinline__ int warp_jsa(const DevOp &op, int cls) { return warp_max_i(Tr::jsa(op, cls)); }
+template <typename Tr>
+__device__ __forceinline__ void warp_kf_run(const DevOp &op, int cls, int &lo, int &hi) {
+    Tr::kf_run(op, cls, lo, hi);
+    lo = warp_max_i(lo);
+    hi = warp_min_i(hi);
+    if (hi < lo) hi = lo;
+}
+template <typename Tr>
+__device__ __forceinline__ void warp_kb_run(const DevOp &op, int cls, int &lo, int &hi) {
+    Tr::kb_run(op, cls, lo, hi);
+    lo = warp_max_i(lo);
+    hi = warp_min_i(hi);
+    if (hi < lo) hi = lo;
+}
+
 // Forms of the uniform interior stencil (taps t0, t1, t2 at offsets 0, +1, +2 of the row):
 //   kAnti: t1 (v[j+1] - v[j-1]) + t2 (v[j+2] - v[j-2])              (first derivative)
 //   kSym : t0 v[j] + t1 (v[j+1] + v[j-1]) + t2 (v[j+2] + v[j-2])     (second derivative, filter: FP64)
@@ -561,7 +591,7 @@ __device__ __forceinline__ void fwd_span(const DevOp &op, int cls, typename Tr::
                                          Pack<typename Tr::A, V> (&w)[5], Pack<typename Tr::A, V> &dprev,
                                          Pack<typename Tr::A, V> &S, int &unsafe) {
     int lo, hi;
-    Tr::kf_run(op, cls, lo, hi);
+    warp_kf_run<Tr>(op, cls, lo, hi);
     const int a = (lo < jb) ? jb : (lo > je ? je : lo);
     const int b = (hi < a) ? a : (hi > je ? je : hi);
     typename Tr::A k0, k1, k2, kg;
@@ -617,10 +647,10 @@ __device__ __forceinline__ void sweep_interior_df(const DevOp &op, int cls, doub
     const bool c0 = (FORM == kSym) && op.tapsum != 0.0;
     DF d = dprev.v[0], Sa = S.v[0];
     int lo, hi;
-    Tr::kf_run(op, cls, lo, hi);
+    warp_kf_run<Tr>(op, cls, lo, hi);
     DF k0, k1, k2, kg;
     Tr::kf(op, cls, k0, k1, k2, kg);
-    const int jp = Tr::jpi(op, cls);
+    const int jp = warp_jpi<Tr>(op, cls);
     auto step = [&](int j, double v4, bool acc, bool cst) {
         DF q0 = k0, q1 = k1, q2 = k2, qg = kg;
         if (!cst) Tr::ifw(op, cls, j, q0, q1, q2, qg);
@@ -688,9 +718,9 @@ __device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typenam
     const int m = op.m;
     const A t0 = (FORM == kSymD) ? Tr::from_d(op.tapsum) : Tr::tap(op, 3), t1 = Tr::tap(op, 4), t2 = Tr::tap(op, 5);
     const int jm = (je < m - 2) ? je : m - 2;
+    const int jp = FWD ? warp_jpi<Tr>(op, cls) : 0;
     if (FWD) {
         // rows before the pi cut-off accumulate S, the rest do not
-        const int jp = Tr::jpi(op, cls);
         const int j1 = (jp < jb) ? jb : (jp > jm ? jm : jp);
         fwd_span<Tr, V, FORM, true>(op, cls, row, jb, j1, w, dprev, S, unsafe);
         fwd_span<Tr, V, FORM, false>(op, cls, row, j1, jm, w, dprev, S, unsafe);
@@ -713,7 +743,7 @@ __device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typenam
         if (FWD) {
             // FP64 sweeps skip S on these rows past the pi cut-off too (measured: the FP32
             // sweeps run faster with the uniform row)
-            if (sizeof(A) == 4 || j < Tr::jpi(op, cls)) fwd_irow<Tr, V, FORM, true>(op, cls, j, row, w, dprev, S);
+            if (sizeof(A) == 4 || j < jp) fwd_irow<Tr, V, FORM, true>(op, cls, j, row, w, dprev, S);
             else fwd_irow<Tr, V, FORM, false>(op, cls, j, row, w, dprev, S);
         } else {
             A sv[V];
@@ -911,7 +941,8 @@ __device__ __forceinline__ void forward_phase(const DevOp &op, typename Tr::S *r
     } else {
         // identity right-hand side: d_j = f_j g_j - (f_j r_j) d_{j-1}
         int lo, hi;
-        Tr::kf_run(op, cls, lo, hi);
+        warp_kf_run<Tr>(op, cls, lo, hi);
+        const int jp0 = warp_jpi<Tr>(op, cls);
         A k0, k1, k2, kg;
         Tr::kf(op, cls, k0, k1, k2, kg);
         auto arow = [&](int j, bool acc, bool cst) {
@@ -965,7 +996,6 @@ __device__ __forceinline__ void forward_phase(const DevOp &op, typename Tr::S *r
         const bool head = e64 && K == 0, tail = e64 && K == op.P - 1;
         const int ja = head ? 4 : 0, jz = tail ? m - 4 : m;
         if (head) rows64(0, true);
-        const int jp0 = Tr::jpi(op, cls);
         const int jp = (jp0 < ja) ? ja : (jp0 > jz ? jz : jp0);
         span(ja, jp, true);
         span(jp, jz, false);
@@ -1018,9 +1048,9 @@ __device__ __forceinline__ void backsub_range(const DevOp &op, typename Tr::S *r
     using A = typename Tr::A;
     if (lo >= hi) return;
     const int m = op.m;
-    const int js = Tr::jsa(op, cls) > 1 ? Tr::jsa(op, cls) : 1;
+    const int js0 = warp_jsa<Tr>(op, cls), js = js0 > 1 ? js0 : 1;
     int rl, rh;
-    Tr::kb_run(op, cls, rl, rh);
+    warp_kb_run<Tr>(op, cls, rl, rh);
     const int kh = (rh < js) ? js : (rh > m - 1 ? m - 1 : rh);
     const int kl = (rl < js) ? js : (rl > kh ? kh : rl);
     auto clip = [&](int x) { return x < lo ? lo : (x > hi ? hi : x); };
@@ -1107,7 +1137,7 @@ __device__ __forceinline__ void adjoint_fold(const DevOp &op, typename Tr::S *ro
     for (int i = 0; i < 4; ++i) yt[i] = zero_a<Tr, V>();
     // generic back-substitution row (any j in 1..m-2; the row's own s^c record, s^a F before the
     // cut-off): the straight-line blocks at both ends of the chunk
-    const int js = Tr::jsa(op, cls) > 1 ? Tr::jsa(op, cls) : 1;
+    const int js0 = warp_jsa<Tr>(op, cls), js = js0 > 1 ? js0 : 1;
     Pack<A, V> u = L;
     auto gstep = [&](int j) {
         const Pack<A, V> d = Tr::template ld_mid<V>(row + (size_t)j * Tr::W);
