@@ -46,7 +46,8 @@ if ROOT not in sys.path:
 
 METRIC = "Gpoints/s and % of HBM roofline per directional derivative, FP64 vs FP32"
 UNIT = "Gpoints/s"
-KERNEL_SRC = os.path.join(ROOT, "paper_2411_13532_gb300", "csrc", "tds_resident.cu")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2411_13532_gb300", "csrc", f)
+              for f in ("tds_resident.cuh", "tds_device.cuh", "tds_df.cuh")]
 
 def fp64_ops_per_point(op, m, periodic=True):
     """FP64-pipe operations per interior point as the resident kernel issues them.
@@ -151,12 +152,14 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def code_fingerprint(path):
-    """sha256[:12] of a C/C++/CUDA source with its comments and whitespace removed: the counters
-    of a capture stay valid across edits that do not touch the code."""
+def code_fingerprint(paths):
+    """sha256[:12] of C/C++/CUDA sources (concatenated in order) with their comments and whitespace
+    removed: the counters of a capture stay valid across edits that do not touch the code."""
     import re
-    with open(path) as fh:
-        text = fh.read()
+    text = ""
+    for path in paths:
+        with open(path) as fh:
+            text += fh.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     text = re.sub(r"//[^\n]*", "", text)
     text = re.sub(r"\s+", "", text)
@@ -571,7 +574,8 @@ def run_ours(args, rank, world, local_rank):
 # ------------------------------------------------------------------ per-configuration sweep
 
 SWEEP_CASES = [
-    # (label, shape (nz, ny, nx), directions, orders, bcs, Ps, dtypes, kind: "deriv" | "adjoint" | "solve")
+    # (label, shape (nz, ny, nx), directions, orders, bcs, Ps, dtypes,
+    #  kind: "deriv" | "adjoint" | "solve" | "band", or "deriv+adjoint" for both on one plan)
     ("64^3 D1 x periodic P=1", (64, 64, 64), "x", (1,), ("periodic",), (1,), ("f64",), "deriv"),
     ("256^3 D1/D2 x,y,z periodic/closed P=1,4", (256, 256, 256), "xyz", (1, 2), ("periodic", "closed"),
      (1, 4), ("f64",), "deriv"),
@@ -580,6 +584,8 @@ SWEEP_CASES = [
     ("512^3 D1^T x periodic P=8 FP64/FP32", (512, 512, 512), "x", (1,), ("periodic",), (8,), ("f64", "f32"),
      "adjoint"),
     ("256^3 D1^T z closed P=4 FP64/FP32", (256, 256, 256), "z", (1,), ("closed",), (4,), ("f64", "f32"), "adjoint"),
+    ("512^3 D1/D2 and D1^T/D2^T x closed P=8 FP64/FP32", (512, 512, 512), "x", (1, 2), ("closed",), (8,),
+     ("f64", "f32"), "deriv+adjoint"),
     ("1024^3 D1 x,y,z periodic P=8,2", (1024, 1024, 1024), "xyz", (1,), ("periodic",), (8, 2), ("f64",), "deriv"),
     ("256 x 262144 D1 x periodic P=64", (1, 256, 262144), "x", (1,), ("periodic",), (64,), ("f64", "f32"), "deriv"),
     ("512^3 solve A x = d, x periodic/closed P=8 FP64/FP32", (512, 512, 512), "x", (1, 2),
@@ -655,35 +661,36 @@ def run_sweep(args):
                                                 alpha_f=0.45 if order == "filter" else None,
                                                 arith=args.arith if dname == "f64" else "native")
                             ws = plan.workspace()
-                            fn = {"adjoint": lambda: plan.adjoint(x, y, ws), "solve": lambda: plan.solve(x, y, ws),
-                                  "band": lambda: plan.solve(x, y, ws), "deriv": lambda: plan.deriv(x, y, ws)}[kind]
-                            for _ in range(max(args.warmup, 3)):
-                                fn()
-                            times = []
-                            for _ in range(reps):
-                                flush.fill_(1.0)
-                                a = torch.cuda.Event(enable_timing=True)
-                                b = torch.cuda.Event(enable_timing=True)
-                                a.record()
-                                fn()
-                                b.record()
-                                b.synchronize()
-                                times.append(a.elapsed_time(b))
-                            ms = statistics.median(times)
-                            es = x.element_size()
-                            gbs = 2 * es * npts / (ms * 1e-3) / 1e9
-                            print(json.dumps({
-                                "case": label, "dtype": dname,
-                                "op": (order if isinstance(order, str) else
-                                       {"adjoint": "D%dT", "solve": "A%d^-1", "deriv": "D%d"}[kind] % order),
-                                "dir": direc, "bc": bc, "P": P, "variant": plan.variant, "width": plan.width,
-                                "arith": plan.arith,
-                                "ms": round(ms, 4), "gpoints_s": round(npts / (ms * 1e-3) / 1e9, 2),
-                                "alg_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
-                                "hbm_frac_nominal_7900": round(gbs / 7900.0, 4), "peak_source": peak_kind,
-                                "oracle_gpoints_s_1core": round(oracle_rate(shape[{"x": 2, "y": 1, "z": 0}[direc]],
-                                                                            order, bc, kind), 5)}),
-                                  flush=True)
+                            for sub in kind.split("+"):
+                                fn = {"adjoint": lambda: plan.adjoint(x, y, ws), "solve": lambda: plan.solve(x, y, ws),
+                                      "band": lambda: plan.solve(x, y, ws), "deriv": lambda: plan.deriv(x, y, ws)}[sub]
+                                for _ in range(max(args.warmup, 3)):
+                                    fn()
+                                times = []
+                                for _ in range(reps):
+                                    flush.fill_(1.0)
+                                    a = torch.cuda.Event(enable_timing=True)
+                                    b = torch.cuda.Event(enable_timing=True)
+                                    a.record()
+                                    fn()
+                                    b.record()
+                                    b.synchronize()
+                                    times.append(a.elapsed_time(b))
+                                ms = statistics.median(times)
+                                es = x.element_size()
+                                gbs = 2 * es * npts / (ms * 1e-3) / 1e9
+                                print(json.dumps({
+                                    "case": label, "dtype": dname,
+                                    "op": (order if isinstance(order, str) else
+                                           {"adjoint": "D%dT", "solve": "A%d^-1", "deriv": "D%d"}[sub] % order),
+                                    "dir": direc, "bc": bc, "P": P, "variant": plan.variant, "width": plan.width,
+                                    "arith": plan.arith,
+                                    "ms": round(ms, 4), "gpoints_s": round(npts / (ms * 1e-3) / 1e9, 2),
+                                    "alg_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                                    "hbm_frac_nominal_7900": round(gbs / 7900.0, 4), "peak_source": peak_kind,
+                                    "oracle_gpoints_s_1core": round(oracle_rate(shape[{"x": 2, "y": 1, "z": 0}[direc]],
+                                                                                order, bc, sub), 5)}),
+                                      flush=True)
                             del plan, ws
             del x, y
             torch.cuda.empty_cache()

@@ -17,8 +17,9 @@ def test_fingerprint_ignores_comments_and_whitespace(tmp_path):
     a.write_text("// header\nint f(int x) { return x + 1; }  /* note */\n")
     b.write_text("int  f(int x)\n{\n    return x + 1;   // another note\n}\n")
     c.write_text("int f(int x) { return x + 2; }\n")
-    assert bench.code_fingerprint(str(a)) == bench.code_fingerprint(str(b))
-    assert bench.code_fingerprint(str(a)) != bench.code_fingerprint(str(c))
+    assert bench.code_fingerprint([str(a)]) == bench.code_fingerprint([str(b)])
+    assert bench.code_fingerprint([str(a)]) != bench.code_fingerprint([str(c)])
+    assert bench.code_fingerprint([str(a), str(c)]) != bench.code_fingerprint([str(c), str(a)])
 
 
 def test_traffic_lookup_is_keyed_by_the_current_code():
