@@ -1305,22 +1305,38 @@ struct TileMaps {
     int box_rows;
 };
 
+// FP32 whole-group CTAs: each chunk's rows leave as soon as its own threads have finished them
+// -- one bulk copy per chunk (contiguous in the tile and in HBM), issued by the chunk's first
+// thread once its warp's writes are fenced -- rather than one copy of the whole tile after a CTA
+// barrier, so that the early chunks' stores overlap the slowest chunk's last rows.  Called by
+// every thread of the CTA once it has written the last of its chunk's rows (no thread writes
+// another chunk's rows after that); the issuing thread waits until its copy has read shared
+// memory.
+template <typename S>
+__device__ __forceinline__ void store_chunk(S *og, const S *tile, int m, int k, int c) {
+    fence_async_smem();
+    __syncwarp();
+    if (c == 0) {
+        bulk_s2g(og + (size_t)k * m * kSZ, tile + (size_t)k * m * kSZ, (uint32_t)((size_t)m * kSZ * sizeof(S)));
+        bulk_commit();
+        bulk_wait_read();
+    }
+}
+
 // The finished tile (in shared memory) to HBM.  og: the first element of this CTA's lines of
 // the group; y0: the group's first row in the [rows][32] view; x0: its first line.
 template <typename Tr, int V>
 __device__ __forceinline__ void store_tile(const DevOp &op, const TileMaps &tm, const typename Tr::S *tile,
                                            typename Tr::S *og, int x0, int y0, int k, int c) {
     using S = typename Tr::S;
-    if (kBulkStore<Tr>) {
+    if constexpr (kBulkStore<Tr> && Tr::W == kSZ) {
+        store_chunk<S>(og, tile, op.m, k, c);
+    } else if (kBulkStore<Tr>) {
         fence_async_smem();   // this thread's tile writes are visible to the bulk store
         __syncthreads();
         if (threadIdx.x == 0) {
-            if constexpr (Tr::W == kSZ) {
-                bulk_s2g(og, tile, (uint32_t)tile_bytes_of(op.n, sizeof(S)));
-            } else {
-                for (int r = 0; r < op.n; r += tm.box_rows)
-                    tma_store_2d(&tm.out, x0, y0 + r, tile + (size_t)r * Tr::W);
-            }
+            for (int r = 0; r < op.n; r += tm.box_rows)
+                tma_store_2d(&tm.out, x0, y0 + r, tile + (size_t)r * Tr::W);
             bulk_commit();
             bulk_wait_read();   // shared memory must stay valid until the copy has read it
         }
@@ -1578,16 +1594,14 @@ __global__ void __launch_bounds__(kMaxResidentP * 32) k_resident_ilv(const __gri
     }
     group_sweep<Tr, 1, 0>(op, tile, xs, ends, k, c, hb, ha, unsafe);
     S *og = static_cast<S *>(ma.out[o]) + gofs;
-    if (kBulkStore<Tr>) {
+    if constexpr (kBulkStore<Tr> && W == kSZ) {
+        store_chunk<S>(og, tile, m, k, c);
+    } else if (kBulkStore<Tr>) {
         fence_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
-            if constexpr (W == kSZ) {
-                bulk_s2g(og, tile, (uint32_t)tile_bytes_of(n, sizeof(S)));
-            } else {
-                for (int r = 0; r < n; r += mm.box_rows)
-                    tma_store_2d(&mm.out[o], x0, y0 + r, tile + (size_t)r * W);
-            }
+            for (int r = 0; r < n; r += mm.box_rows)
+                tma_store_2d(&mm.out[o], x0, y0 + r, tile + (size_t)r * W);
             bulk_commit();
             bulk_wait_read();
         }
