@@ -133,25 +133,30 @@ __device__ __forceinline__ T stencil(const DevOp &op, int J, const T (&w)[kTaps]
         // the row's form (DevOp::edge_form; FP64: the taps as written), as in the resident sweep
         const int form = (sizeof(T) == 8) ? 0 : op.edge_form[e];
         T s = T(0);
+        // FP32: the plan's float copies of the taps (a conversion would issue on the FP64 pipe)
         if (form == 2) {
             T a[kTaps - 1];
 #pragma unroll
             for (int o = 0; o < kTaps - 1; ++o) a[o] = w[o + 1] - w[o];
 #pragma unroll
-            for (int k = 1; k <= 5; ++k) s += T(op.edge_dd[e][k - 1]) * (a[k] - a[k - 1]);
+            for (int k = 1; k <= 5; ++k)
+                s += (sizeof(T) == 4 ? T(op.edge_dd32[e][k - 1]) : T(op.edge_dd[e][k - 1])) * (a[k] - a[k - 1]);
         } else {
 #pragma unroll
-            for (int o = 0; o < kTaps; ++o) s += T(op.edge[e][o]) * (form == 1 ? w[o] - w[3] : w[o]);
+            for (int o = 0; o < kTaps; ++o)
+                s += (sizeof(T) == 4 ? T(op.edge_pf[e][o][0]) : T(op.edge[e][o])) * (form == 1 ? w[o] - w[3] : w[o]);
         }
         return s;
     }
     // uniform interior rows: taps at offsets 0, +1, +2 and the form of op.symmetric
-    const T t0 = T(op.tap[3]), t1 = T(op.tap[4]), t2 = T(op.tap[5]);
+    const T t0 = sizeof(T) == 4 ? T(op.tap32[3]) : T(op.tap[3]);
+    const T t1 = sizeof(T) == 4 ? T(op.tap32[4]) : T(op.tap[4]);
+    const T t2 = sizeof(T) == 4 ? T(op.tap32[5]) : T(op.tap[5]);
     switch (op.symmetric) {
     case 1:
     case 4:   // symmetric (filter, second derivative); FP32: second differences and the tap sum
         if constexpr (sizeof(T) == 4)
-            return T(op.tapsum) * w[3] + t1 * ((w[4] - w[3]) - (w[3] - w[2])) + t2 * ((w[5] - w[3]) - (w[3] - w[1]));
+            return T(op.tapsum32) * w[3] + t1 * ((w[4] - w[3]) - (w[3] - w[2])) + t2 * ((w[5] - w[3]) - (w[3] - w[1]));
         else
             return t0 * w[3] + t1 * (w[4] + w[2]) + t2 * (w[5] + w[1]);
     case 2: return t1 * (w[3] + w[4]) + t2 * (w[2] + w[5]);              // nodes -> mid-points

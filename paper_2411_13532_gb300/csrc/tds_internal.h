@@ -105,6 +105,9 @@ struct DevOp {
     double red_den_inv;   // 1/(1 + v.q)
     double tap[kTaps];                 // interior stencil taps, offsets -3..3
     double tapsum;                     // symmetric taps: t0 + 2 t1 + 2 t2 (0 for a second derivative)
+    // the same taps, tap sum and second-difference weights rounded to float once on the host (FP32
+    // sweeps read them without a conversion, which would issue on the FP64 pipe)
+    float tap32[kTaps], tapsum32, edge_dd32[2 * kEdgeRows][5];
     double edge[2 * kEdgeRows][kTaps]; // closed lines: rows 0..3 then n-4..n-1
     float edge_pf[2 * kEdgeRows][kTaps][2]; // the same taps as float pairs (hi, lo): FP32 sweeps
                                             // evaluate closure rows with e64 in pair arithmetic

@@ -319,6 +319,10 @@ static tds_status build_operator(const tds_plan *p, int P, int m, const LineOper
     // sum on the centre value -- exactly zero for a second derivative, so nothing cancels there
     const bool sym = (op.symmetric == 1 || op.symmetric == 4);
     op.tapsum = (op.symmetric == 4) ? 0.0 : op.tap[3] + 2.0 * (op.tap[4] + op.tap[5]);
+    op.tapsum32 = (float)op.tapsum;
+    for (int o = 0; o < kTaps; ++o) op.tap32[o] = (float)op.tap[o];
+    for (int e = 0; e < 2 * kEdgeRows; ++e)
+        for (int k = 0; k < 5; ++k) op.edge_dd32[e][k] = (float)op.edge_dd[e][k];
 
     // interior forward records with f folded in (FP32 records: the tap sum in place of t0 for
     // symmetric taps), and the cut-off rows of pi and s^a

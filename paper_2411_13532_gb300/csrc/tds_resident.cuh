@@ -77,8 +77,23 @@ struct TrNative {
     static __device__ __forceinline__ void st_mid(S *p, const Pack<A, V> &v) { stv<T, V>(p, v); }
     template <int V>
     static __device__ __forceinline__ void st_out(const DevOp &, S *p, const Pack<A, V> &v) { stv<T, V>(p, v); }
-    static __device__ __forceinline__ A tap(const DevOp &op, int i) { return A(op.tap[i]); }
-    static __device__ __forceinline__ A edge(const DevOp &op, int e, int o) { return A(op.edge[e][o]); }
+    // FP32: the plan's float copies (the FP64 -> FP32 conversion issues on the FP64 pipe)
+    static __device__ __forceinline__ A tap(const DevOp &op, int i) {
+        if constexpr (sizeof(T) == 4) return op.tap32[i];
+        else return op.tap[i];
+    }
+    static __device__ __forceinline__ A tapsum(const DevOp &op) {
+        if constexpr (sizeof(T) == 4) return op.tapsum32;
+        else return op.tapsum;
+    }
+    static __device__ __forceinline__ A edge(const DevOp &op, int e, int o) {
+        if constexpr (sizeof(T) == 4) return op.edge_pf[e][o][0];
+        else return op.edge[e][o];
+    }
+    static __device__ __forceinline__ A edge_dd(const DevOp &op, int e, int k) {
+        if constexpr (sizeof(T) == 4) return op.edge_dd32[e][k];
+        else return op.edge_dd[e][k];
+    }
     static __device__ __forceinline__ void fwd(const DevOp &op, int cls, int j, A &f, A &r, A &pi) {
         const size_t i = (size_t)cls * op.m + j;
         if constexpr (sizeof(T) == 4) {
@@ -193,7 +208,9 @@ struct TrSplit {
         for (int i = 0; i < V; ++i) p[i] = df_join(v.v[i]);
     }
     static __device__ __forceinline__ A tap(const DevOp &op, int i) { return DF(op.tap[i]); }
+    static __device__ __forceinline__ A tapsum(const DevOp &op) { return DF(op.tapsum); }
     static __device__ __forceinline__ A edge(const DevOp &op, int e, int o) { return DF(op.edge[e][o]); }
+    static __device__ __forceinline__ A edge_dd(const DevOp &op, int e, int k) { return DF(op.edge_dd[e][k]); }
     static __device__ __forceinline__ void fwd(const DevOp &op, int cls, int j, A &f, A &r, A &pi) {
         const float4 *q = reinterpret_cast<const float4 *>(op.fwdd) + 2 * ((size_t)cls * op.m + j);
         const float4 a = __ldg(q);
@@ -332,7 +349,7 @@ __device__ __forceinline__ void estencil(const DevOp &op, int e, const Pack<type
 #pragma unroll
             for (int o = 0; o < kTaps - 1; ++o) a[o] = w[o + 1].v[i] - w[o].v[i];
 #pragma unroll
-            for (int k = 1; k <= 5; ++k) s[i] = mad(Tr::from_d(op.edge_dd[e][k - 1]), a[k] - a[k - 1], s[i]);
+            for (int k = 1; k <= 5; ++k) s[i] = mad(Tr::edge_dd(op, e, k - 1), a[k] - a[k - 1], s[i]);
         }
     } else {                  // form 1: sum_o c_o (v[J+o] - v[J]); form 0: sum_o c_o v[J+o]
 #pragma unroll
@@ -716,7 +733,7 @@ __device__ __forceinline__ void sweep_interior(const DevOp &op, int cls, typenam
         return;
     }
     const int m = op.m;
-    const A t0 = (FORM == kSymD) ? Tr::from_d(op.tapsum) : Tr::tap(op, 3), t1 = Tr::tap(op, 4), t2 = Tr::tap(op, 5);
+    const A t0 = (FORM == kSymD) ? Tr::tapsum(op) : Tr::tap(op, 3), t1 = Tr::tap(op, 4), t2 = Tr::tap(op, 5);
     const int jm = (je < m - 2) ? je : m - 2;
     const int jp = FWD ? warp_jpi<Tr>(op, cls) : 0;
     if (FWD) {
@@ -1121,7 +1138,7 @@ __device__ __forceinline__ void adjoint_fold(const DevOp &op, typename Tr::S *ro
                                              Pack<typename Tr::A, V> &Ssum, Ends64<V> &ex) {
     using A = typename Tr::A;
     const int m = op.m, P = op.P;
-    const A t0 = (FORM == kSymD) ? Tr::from_d(op.tapsum) : Tr::tap(op, 3), t1 = Tr::tap(op, 4), t2 = Tr::tap(op, 5);
+    const A t0 = (FORM == kSymD) ? Tr::tapsum(op) : Tr::tap(op, 3), t1 = Tr::tap(op, 4), t2 = Tr::tap(op, 5);
     auto emit = [&](int r, const Pack<A, V> (&v)[5]) {
         A sv[V];
         istencil<A, V, FORM>(t0, t1, t2, v, sv);
