@@ -162,6 +162,9 @@ struct tds_plan {
     // thomas_ratio = A[0][n-1] / gamma, thomas_inv_den = 1 / (1 + v.z) (Sherman-Morrison)
     void *thomas_mem;
     double thomas_ratio, thomas_inv_den;
+    // the four rows at each end of a closed line for FP32 sweeps with e64 (rows 0..3, n-4..n-1):
+    // {f, c', f a} of each row as float pairs (hi, lo)
+    float thomas_end_pf[2 * tds::kEdgeRows][3][2];
     void *dmem;            // one device allocation holding every array of both operators
     void *hmem;            // host copies (reduced coefficients)
 };

@@ -613,6 +613,17 @@ static tds_status build_thomas(tds_plan *p, const LineOperator &L, const DevOp &
     p->thomas_mem = d;
     p->thomas_ratio = ratio;
     p->thomas_inv_den = inv_den;
+    if (n >= 2 * kEdgeRows) {
+        for (int t = 0; t < 2 * kEdgeRows; ++t) {
+            const int j = (t < kEdgeRows) ? t : n - 2 * kEdgeRows + t;
+            const double v[3] = {f[j], cp[j], f[j] * a[j]};
+            for (int q = 0; q < 3; ++q) {
+                const float hi = (float)v[q];
+                p->thomas_end_pf[t][q][0] = hi;
+                p->thomas_end_pf[t][q][1] = (float)(v[q] - (double)hi);
+            }
+        }
+    }
     return TDS_OK;
 }
 

@@ -14,10 +14,14 @@
 // read once (cyclic lines: once more each).  FP32 plans run every step in FP32, except where a
 // closed line's closure makes its ends ill-conditioned (DevOp::e64: an FP32 rounding at row 1 or
 // n-2 reaches the end row multiplied by about 100 for f''_0 + 11 f''_1 = ...): there the four
-// rows at each end run both passes in FP64 -- right-hand sides from the exact FP32 inputs with
-// the taps as written, forward steps with the FP64 records, forward values kept in registers for
-// the backward steps -- and only their final values are rounded to FP32.
+// rows at each end run both passes in float-pair arithmetic (about 48 bits, on the FP32 pipes) --
+// right-hand sides from the exact FP32 inputs with the taps as pairs, forward steps with the
+// planner's pair records, forward values kept in registers for the backward steps -- and only
+// their final values are rounded to FP32.
+#include <cstring>
+
 #include "tds_device.cuh"
+#include "tds_df.cuh"
 
 namespace tds {
 namespace {
@@ -27,8 +31,8 @@ struct ThomasArgs {
     const void *rec;   // [n] {f t0 (FP32 symmetric taps: f tapsum), f t1, f t2, f a}
     const void *fc;    // [n] {f, c'}
     const void *z;     // [n] z = A'^{-1} u (cyclic lines), else null
-    const double *rec64, *fc64;   // the FP64 records (the FP64 end rows of FP32 sweeps)
     double ratio, inv_den;
+    float end_pf[2 * kEdgeRows][3][2];   // {f, c', f a} of the end rows as pairs (E64)
 };
 
 // Interior forms (window w[i] = v[J - 3 + i]), the coefficients folded with f:
@@ -54,7 +58,25 @@ template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
 
-// E64: FP32 sweep of a closed line with the four rows at each end in FP64 (see the header).
+// sum_o c_o w_o over the taps of closure row e, c_o as float pairs, w_o floats (exact in a pair)
+__device__ __forceinline__ DF edge_sum_pf(const DevOp &op, int e, const float (&w)[kTaps]) {
+    float sh = 0.0f, se = 0.0f;
+#pragma unroll
+    for (int o = 0; o < kTaps; ++o) {
+        const float ch = op.edge_pf[e][o][0], cl = op.edge_pf[e][o][1];
+        const float p = __fmul_rn(ch, w[o]);
+        float err = __fmaf_rn(ch, w[o], -p);
+        err = __fmaf_rn(cl, w[o], err);
+        const DF t = df_two(sh, p);
+        sh = t.h;
+        se = __fadd_rn(se, __fadd_rn(t.l, err));
+    }
+    return df_two(sh, se);
+}
+
+__device__ __forceinline__ float df_round(DF x) { return __fadd_rn(x.h, x.l); }
+
+// E64: FP32 sweep of a closed line with the four rows at each end in float pairs (see the header).
 template <typename T, int FORM, bool CYC, bool E64>
 __global__ void __launch_bounds__(128) k_thomas(const __grid_constant__ ThomasArgs ta, const T *__restrict__ in,
                                                 T *__restrict__ out) {
@@ -87,29 +109,32 @@ __global__ void __launch_bounds__(128) k_thomas(const __grid_constant__ ThomasAr
         const T f = __ldg(&fc[j].x);
         return fma(-g, d, f * stencil<T>(op, j, w));
     };
-    // a closure row in FP64: the taps as written on the (exact) inputs, then the FP64 records
-    auto edge_row64 = [&](int j, double d) {
-        const int e = (j < kEdgeRows) ? j : kEdgeRows + j - (n - kEdgeRows);
-        double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-        for (int o = 0; o < kTaps; o += 2) {
-            s0 = ::fma(op.edge[e][o], (double)w[o], s0);
-            if (o + 1 < kTaps) s1 = ::fma(op.edge[e][o + 1], (double)w[o + 1], s1);
+    // a closure row in pairs: d = f s - (f a) d with the taps on the (exact) inputs; t indexes the
+    // end rows' pair records (0..3: rows 0..3, 4..7: rows n-4..n-1)
+    auto edge_row_pf = [&](int t, int j, DF d) {
+        if constexpr (E64) {
+            const int e = (j < kEdgeRows) ? j : kEdgeRows + j - (n - kEdgeRows);
+            const DF sum = edge_sum_pf(op, e, w);
+            const DF f = df_make(ta.end_pf[t][0][0], ta.end_pf[t][0][1]);
+            const DF g = df_make(ta.end_pf[t][2][0], ta.end_pf[t][2][1]);
+            return dot2(f, sum, -g, d);
+        } else {
+            return d;
         }
-        return ::fma(-__ldg(ta.rec64 + 4 * j + 3), d, __ldg(ta.fc64 + 2 * j) * (s0 + s1));
     };
+    auto cprime = [&](int t) { return df_make(ta.end_pf[t][1][0], ta.end_pf[t][1][1]); };
     const int e = CYC ? 0 : kEdgeRows;
     T d = T(0);
-    double dh[E64 ? kEdgeRows : 1], dt[E64 ? kEdgeRows : 1];   // FP64 forward values of the end rows
+    DF dh[E64 ? kEdgeRows : 1], dt[E64 ? kEdgeRows : 1];   // forward values of the end rows
     if constexpr (E64) {
-        double x = 0.0;
+        DF x = df_make(0.0f, 0.0f);
 #pragma unroll
         for (int j = 0; j < kEdgeRows; ++j) {
-            x = edge_row64(j, x);
+            x = edge_row_pf(j, j, x);
             dh[j] = x;
             slide(j);
         }
-        d = T(x);
+        d = df_round(x);
     } else {
         for (int j = 0; j < e; ++j) {
             d = edge_row(j, d);
@@ -126,34 +151,34 @@ __global__ void __launch_bounds__(128) k_thomas(const __grid_constant__ ThomasAr
     }
     T y;
     if constexpr (E64) {
-        // the last rows: forward in FP64 from d_{n-5}, then their backward steps in FP64
-        double x = (n > 2 * kEdgeRows) ? (double)d : dh[kEdgeRows - 1];
+        // the last rows: forward in pairs from d_{n-5}, then their backward steps in pairs
+        DF x = (n > 2 * kEdgeRows) ? df_make(d, 0.0f) : dh[kEdgeRows - 1];
 #pragma unroll
         for (int t = 0; t < kEdgeRows; ++t) {
-            x = edge_row64(n - kEdgeRows + t, x);
+            x = edge_row_pf(kEdgeRows + t, n - kEdgeRows + t, x);
             dt[t] = x;
             slide(n - kEdgeRows + t);
         }
-        dst[(size_t)(n - 1) * kSZ] = T(x);
+        dst[(size_t)(n - 1) * kSZ] = df_round(x);
 #pragma unroll
         for (int t = kEdgeRows - 2; t >= 0; --t) {
             const int j = n - kEdgeRows + t;
-            x = ::fma(-__ldg(ta.fc64 + 2 * j + 1), x, dt[t]);
-            dst[(size_t)j * kSZ] = T(x);
+            x = mad(-cprime(kEdgeRows + t), x, dt[t]);
+            dst[(size_t)j * kSZ] = df_round(x);
         }
         // interior rows in FP32, in place
-        y = T(x);
+        y = df_round(x);
 #pragma unroll 4
         for (int j = n - kEdgeRows - 1; j >= kEdgeRows; --j) {
             y = fma(-__ldg(&fc[j].y), y, dst[(size_t)j * kSZ]);
             dst[(size_t)j * kSZ] = y;
         }
-        // the first rows in FP64 from their forward values in registers
-        x = (n > 2 * kEdgeRows) ? (double)y : x;
+        // the first rows in pairs from their forward values in registers
+        x = (n > 2 * kEdgeRows) ? df_make(y, 0.0f) : x;
 #pragma unroll
         for (int j = kEdgeRows - 1; j >= 0; --j) {
-            x = ::fma(-__ldg(ta.fc64 + 2 * j + 1), x, dh[j]);
-            dst[(size_t)j * kSZ] = T(x);
+            x = mad(-cprime(j), x, dh[j]);
+            dst[(size_t)j * kSZ] = df_round(x);
         }
     } else {
         for (int j = n - e; j < n; ++j) {
@@ -206,8 +231,7 @@ tds_status launch_thomas(const tds_plan *p, const void *in, void *out, cudaStrea
     ta.ratio = p->thomas_ratio;
     ta.inv_den = p->thomas_inv_den;
     const double *r64 = reinterpret_cast<const double *>(b);
-    ta.rec64 = r64;
-    ta.fc64 = r64 + 4 * n;
+    std::memcpy(ta.end_pf, p->thomas_end_pf, sizeof(ta.end_pf));
     if (p->dtype == TDS_F64) {
         ta.rec = r64;
         ta.fc = r64 + 4 * n;
