@@ -795,3 +795,29 @@ def test_closed_adjoint_fold_forms(dtype, kind, fold, monkeypatch):
                 plan = tds.Plan(shape, "x", kind, "closed", P=P, h=h, dtype=TORCH[dtype], variant=variant)
             mx, rms = rel_errors(from_device_layout(plan.adjoint(x), "x", shape), ref)
             assert mx <= TOL[dtype], (P, variant, mx, rms)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("lanes", ["2", "4"])
+@pytest.mark.parametrize("bc", ["periodic", "closed"])
+def test_lines_per_thread_every_point(dtype, lanes, bc, monkeypatch):
+    """Two or four lines per thread in the whole-group resident kernels (TDS_RESIDENT_LANES, read at
+    plan creation; four lines for FP32 only): every point of the derivatives and their adjoints
+    against the oracle, with chunks in the first, interior and last positions."""
+    if dtype == "f64" and lanes == "4":
+        pytest.skip("four lines per thread are FP32 only")
+    monkeypatch.setenv("TDS_RESIDENT_LANES", lanes)
+    shape = (4, 64, 128)
+    cart = np.random.default_rng(43).uniform(-1, 1, shape)
+    if dtype == "f32":
+        cart = cart.astype(np.float32).astype(np.float64)
+    h = oracle.grid_spacing(128, bc)
+    x = to_device_layout(cart, "x", dtype)
+    for order in (1, 2):
+        for adjoint in (False, True):
+            ref = (oracle.deriv_adjoint if adjoint else oracle.deriv)(cart, "x", order, bc, h)
+            for P in (1, 2, 4):
+                plan = tds.Plan(shape, "x", order, bc, P=P, h=h, dtype=TORCH[dtype], variant="resident", width=32)
+                y = plan.adjoint(x) if adjoint else plan.deriv(x)
+                mx, rms = rel_errors(from_device_layout(y, "x", shape), ref)
+                assert mx <= TOL[dtype], (order, adjoint, P, mx, rms)
