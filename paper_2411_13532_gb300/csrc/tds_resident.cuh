@@ -178,8 +178,10 @@ struct TrSplit {
     static constexpr int W = W_;
     static constexpr bool kE64 = true;   // closed lines with a high end gain: closure rows in FP64 (Ends64)
     static constexpr bool kDF = true;
-    static __device__ __forceinline__ A from_d(double x) { return DF(x); }
-    static __device__ __forceinline__ double to_d(A x) { return static_cast<double>(x); }
+    // by integer operations (tds_df.cuh): the chunk-end values cross to and from the FP64 reduced
+    // system without FP64-pipe conversions
+    static __device__ __forceinline__ A from_d(double x) { return df_split(x); }
+    static __device__ __forceinline__ double to_d(A x) { return df_join(x); }
     template <int V>
     static __device__ __forceinline__ Pack<A, V> ld_in(const DevOp &, const S *p, int &) {
         Pack<A, V> r;
