@@ -642,7 +642,11 @@ tds_status build_plan(tds_plan *p) {
     // adjoint on that partition (forward form, see build_operator)
     int sg = 0;
     {
-        const int cap = (p->dtype == TDS_F64) ? 128 : 256;
+        int cap = (p->dtype == TDS_F64) ? 128 : 256;
+        if (const char *e = std::getenv("TDS_SEG_ROWS")) {   // longest segment (tuning)
+            const int v = std::atoi(e);
+            if (v >= 64 && v <= 4096) cap = v;
+        }
         for (int d = (p->m < cap ? p->m : cap); d >= 64; --d)
             if (p->m % d == 0) { sg = d; break; }
     }
