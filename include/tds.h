@@ -93,7 +93,8 @@ typedef struct tds_plan tds_plan;
  *   P     : chunks per line (the emulated ranks); n % P == 0, m = n/P >= 4.
  *   h     : grid spacing (> 0).
  *   dtype : storage and sweep precision.  TDS_F32 keeps the reduced chunk-end system and the
- *           Sherman-Morrison correction in FP64.
+ *           Sherman-Morrison correction in FP64; on closed lines whose closure magnifies end-row
+ *           rounding (the second derivative's), its four rows at each end run in float pairs.
  *   sz    : group size SZ; must be 32.
  *   mode  : TDS_REDUCED_EXACT solves the full 2P-unknown chunk-end system;
  *           TDS_REDUCED_PAPER_DROP drops the two sub-machine-epsilon couplings per chunk
