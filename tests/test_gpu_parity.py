@@ -821,3 +821,24 @@ def test_lines_per_thread_every_point(dtype, lanes, bc, monkeypatch):
                 y = plan.adjoint(x) if adjoint else plan.deriv(x)
                 mx, rms = rel_errors(from_device_layout(y, "x", shape), ref)
                 assert mx <= TOL[dtype], (order, adjoint, P, mx, rms)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("rows", ["64", "512"])
+def test_segment_length_knob_every_point(dtype, rows, monkeypatch):
+    """TDS_SEG_ROWS (the longest segment of SEGMENTED plans, read at plan creation) changes the
+    internal partition only: every point of long lines against the oracle, both boundaries."""
+    monkeypatch.setenv("TDS_SEG_ROWS", rows)
+    shape = (1, 32, 4096)
+    cart = np.random.default_rng(47).uniform(-1, 1, shape)
+    if dtype == "f32":
+        cart = cart.astype(np.float32).astype(np.float64)
+    x = to_device_layout(cart, "x", dtype)
+    for bc in ("periodic", "closed"):
+        h = oracle.grid_spacing(4096, bc)
+        ref = oracle.deriv(cart, "x", 1, bc, h)
+        for P in (1, 4):
+            plan = tds.Plan(shape, "x", 1, bc, P=P, h=h, dtype=TORCH[dtype], variant="segmented")
+            assert plan.variant == "segmented"
+            mx, rms = rel_errors(from_device_layout(plan.deriv(x), "x", shape), ref)
+            assert mx <= TOL[dtype], (bc, P, mx, rms)
